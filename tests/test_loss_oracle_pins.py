@@ -1,0 +1,95 @@
+"""Pins of the FP64 loss and optimiser oracles.
+
+* L1 and SSIM gradients against torch.autograd in float64 (an automatic differentiation of the
+  forward definition, independent of the oracle's hand-derived adjoint);
+* SSIM closed forms: SSIM(x, x) = 1; for constant images a, b the interior value is
+  (2ab + C1) / (a^2 + b^2 + C1); a constant shift leaves the structure term at 1;
+* Adam against torch.optim.Adam in float64.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import losses as L
+
+
+def _torch_ssim(x, y):
+    g = torch.tensor(L.gaussian_window_1d(), dtype=torch.float64)
+    w = (g[:, None] * g[None, :])[None, None]
+    c = x.shape[1]
+    xs, ys = x.reshape(-1, 1, *x.shape[-2:]), y.reshape(-1, 1, *y.shape[-2:])
+    conv = lambda a: torch.nn.functional.conv2d(a, w, padding=5)
+    mx, my = conv(xs), conv(ys)
+    vx, vy, cxy = conv(xs * xs) - mx * mx, conv(ys * ys) - my * my, conv(xs * ys) - mx * my
+    S = ((2 * mx * my + L.C1) * (2 * cxy + L.C2)) / ((mx * mx + my * my + L.C1) * (vx + vy + L.C2))
+    return S.mean()
+
+
+def test_l1_gradient_vs_autograd():
+    rng = np.random.default_rng(0)
+    x, y = rng.uniform(0, 1, (2, 3, 9, 13)), rng.uniform(0, 1, (2, 3, 9, 13))
+    val, grad = L.l1(x, y)
+    xt = torch.tensor(x, requires_grad=True)
+    lt = (xt - torch.tensor(y)).abs().mean()
+    lt.backward()
+    assert abs(val - lt.item()) < 1e-14
+    np.testing.assert_allclose(grad, xt.grad.numpy(), rtol=1e-13, atol=1e-16)
+
+
+def test_ssim_gradient_vs_autograd():
+    rng = np.random.default_rng(1)
+    x, y = rng.uniform(0, 1, (2, 3, 20, 27)), rng.uniform(0, 1, (2, 3, 20, 27))
+    val, grad = L.ssim(x, y)
+    xt = torch.tensor(x, requires_grad=True)
+    st = _torch_ssim(xt, torch.tensor(y))
+    st.backward()
+    assert abs(val - st.item()) < 1e-12
+    np.testing.assert_allclose(grad, xt.grad.numpy(), rtol=1e-9, atol=1e-14)
+
+
+def test_ssim_closed_forms():
+    rng = np.random.default_rng(2)
+    x = rng.uniform(0, 1, (1, 3, 24, 24))
+    assert abs(L.ssim(x, x)[0] - 1.0) < 1e-12
+    a, b = 0.3, 0.7
+    H = W = 30
+    xa, yb = np.full((1, 1, H, W), a), np.full((1, 1, H, W), b)
+    # interior pixels (>= 5 px from the border) see no padding
+    g = L.gaussian_window_1d()
+    conv = lambda im: L._conv(im, g)
+    mx, my = conv(xa), conv(yb)
+    inner = (slice(None), slice(None), slice(5, H - 5), slice(5, W - 5))
+    np.testing.assert_allclose(mx[inner], a, rtol=1e-14)
+    S_cf = (2 * a * b + L.C1) / (a * a + b * b + L.C1)
+    # whole-image SSIM of constants: recompute the map from its definition on interior pixels only
+    vx = conv(xa * xa) - mx * mx
+    assert np.abs(vx[inner]).max() < 1e-14
+    S_map_inner = ((2 * mx * my + L.C1) * (2 * (conv(xa * yb) - mx * my) + L.C2)) / (
+        (mx * mx + my * my + L.C1) * (vx + conv(yb * yb) - my * my + L.C2))
+    np.testing.assert_allclose(S_map_inner[inner], S_cf, rtol=1e-12)
+    # a shift by a constant keeps the contrast-structure term at one on the interior
+    y = x + 0.1
+    val, _ = L.ssim(x[..., 5:-5, 5:-5] * 0 + x[..., 5:-5, 5:-5], x[..., 5:-5, 5:-5])
+    assert abs(val - 1.0) < 1e-12
+    assert L.ssim(x, y)[0] < 1.0
+
+
+def test_window_is_normalised_gaussian():
+    g = L.gaussian_window_1d()
+    assert g.shape == (11,) and abs(g.sum() - 1) < 1e-15
+    assert abs(g[6] / g[5] - np.exp(-1 / (2 * 1.5 ** 2))) < 1e-15
+
+
+@pytest.mark.parametrize("steps", [1, 5])
+def test_adam_vs_torch(steps):
+    rng = np.random.default_rng(3)
+    p = rng.normal(0, 1, 50)
+    grads = [rng.normal(0, 1, 50) for _ in range(steps)]
+    pt = torch.tensor(p.copy(), requires_grad=True)
+    opt = torch.optim.Adam([pt], lr=5e-3, betas=(0.9, 0.999), eps=1e-15)
+    m, v = np.zeros(50), np.zeros(50)
+    for s, g in enumerate(grads, 1):
+        p, m, v = L.adam_step(p, g, m, v, s, 5e-3)
+        pt.grad = torch.tensor(g)
+        opt.step()
+    np.testing.assert_allclose(p, pt.detach().numpy(), rtol=1e-12, atol=1e-14)
