@@ -1,0 +1,256 @@
+/*
+ * gs.h -- C ABI of libgs, a differentiable 3D Gaussian Splatting rasterizer for NVIDIA GB300
+ * (sm_103a), forward and backward, with SE(3) pose gradients, batched over many views of many
+ * scenes (agents' submaps), plus the fused losses and the in-kernel Adam step of the mapping loop.
+ *
+ * What it computes.  MAGS-SLAM optimises each agent's Gaussian submap against a sliding window of
+ * keyframes through "differentiably rendered RGB and depth" (Sec. III-A, mapping loss Eq. 4) and,
+ * after fusion, refines Gaussians together with per-keyframe pose deltas (Sec. III-D, refinement
+ * loss Eq. 23).  Keyframe poses are world-to-camera (Sec. III-B, lifting relation Eq. 15); a
+ * Gaussian carries a centre, per-axis scale, rotation, opacity and colour, with covariance
+ * R diag(s)^2 R^T (Eq. 19).  The paper cites the 3DGS rasterizer for the rendering itself and fixes
+ * none of its internals; the readings this library implements are:
+ *   - EWA projection with 0.3 px dilation, radius = ceil(3 sqrt(lambda_max)), near-plane cull;
+ *   - 16x16 pixel tiles, one 64-bit key (global tile << 32 | float bits of camera depth) per
+ *     (view, Gaussian, touched tile), stably sorted (ties: ascending flattened (view, Gaussian));
+ *   - per pixel (sample at x + 0.5, y + 0.5), front to back: sigma = 1/2 d^T conic d,
+ *     alpha = min(alpha_max, o exp(-sigma)), skip alpha < alpha_min, stop before blending when
+ *     T (1 - alpha) < t_min; outputs RGB (+ T_final bg), unnormalised depth, alpha = 1 - T_final;
+ *   - culling, binning and every skip / stop decision in FP32 with a fixed operation order and a
+ *     library-defined FP32 exponential (Cody-Waite reduction, degree-7 Taylor), so that any other
+ *     implementation of the same decision chain takes the same branches bit for bit.
+ *
+ * Conventions.
+ *   - Every function returns int: GS_OK (0) or a negative GS_ERR_* code; no exceptions cross the
+ *     ABI.  gs_error_string() names a code.
+ *   - Every data pointer is a DEVICE pointer owned by the caller (except where marked "host").
+ *     The library allocates no device memory in any call: scratch lives in a caller-allocated
+ *     workspace of gs_workspace_size() bytes (256-byte aligned), initialised by gs_workspace_init().
+ *   - Every call is ordered on the caller's CUDA stream (`stream`, a cudaStream_t; NULL = the legacy
+ *     default stream) and none synchronises the host, except gs_check_status().  The sequence
+ *     project -> bin_sort -> render_fwd -> loss -> render_bwd -> pose_grad -> adam contains no host
+ *     synchronisation and may be captured in a CUDA graph.
+ *   - Data-dependent failures (key capacity exceeded, a bounded wait that timed out) are recorded in
+ *     a status block inside the workspace; gs_check_status() synchronises the stream and reports
+ *     the first one.  Argument errors are reported immediately and launch nothing.
+ *   - Arrays are row-major float32 unless stated.  N = rows of the concatenated Gaussian arrays of
+ *     all scenes; V = views; P = number of (view, Gaussian) pairs = sum over views of the Gaussian
+ *     count of the view's scene; images are [V, 3, H, W] (planar RGB) and [V, H, W].
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = -1,   /* a pointer, size or parameter is out of range            */
+    GS_ERR_CAPACITY = -2,      /* more duplicated keys than key_capacity (required K kept) */
+    GS_ERR_TIMEOUT = -3,       /* a bounded device-side wait gave up                      */
+    GS_ERR_CUDA = -4,          /* a CUDA launch or runtime call failed                     */
+    GS_ERR_DEVICE_FAULT = -5,  /* a device-side consistency check failed                   */
+};
+
+#define GS_MAX_VIEWS 1024
+
+/* Pinhole camera with world-to-camera pose p_c = R p_w + t (R row-major); camera x right,
+ * y down, z forward.  Intrinsics in pixels.  64 bytes. */
+typedef struct gs_camera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+} gs_camera;
+
+/* Rasterizer constants.  gs_default_params() gives tile 16x16, near 0.2, dilation 0.3,
+ * radius_sigmas 3, alpha_max 0.99, alpha_min 1/255 (float division), t_min 1e-4, bg 0.
+ * Supported tiles: 16x16, 16x8, 32x16. */
+typedef struct gs_params {
+    int32_t tile_w, tile_h;
+    float near_plane;
+    float dilation;
+    float radius_sigmas;
+    float alpha_max;
+    float alpha_min;
+    float t_min;
+    float bg[3];
+} gs_params;
+
+/* One rendering problem: V views of one or more scenes (agents' submaps) whose Gaussians are
+ * concatenated row-wise.  View v renders rows [view_gauss_begin[v], +view_gauss_count[v]).
+ * All views share width x height (the agents share one camera model, Sec. V). */
+typedef struct gs_problem {
+    int32_t num_views;                 /* V, 1..GS_MAX_VIEWS                          */
+    int32_t width, height;             /* image size, pixels                          */
+    int32_t reserved;
+    int64_t num_gaussians;             /* N                                           */
+    const int64_t *view_gauss_begin;   /* host [V]                                    */
+    const int64_t *view_gauss_count;   /* host [V]                                    */
+    const gs_camera *cameras;          /* device [V]                                  */
+    int64_t key_capacity;              /* max duplicated keys K the workspace holds   */
+    gs_params params;
+} gs_problem;
+
+/* Gaussian parameters, device, [N,3] means, [N,3] log-scales (natural log of the per-axis
+ * standard deviation), [N,4] quaternions (w,x,y,z; normalised internally), [N] opacities already
+ * in (0,1), [N,3] RGB colours. */
+typedef struct gs_gaussians {
+    const float *means, *log_scales, *quats, *opacities, *colors;
+} gs_gaussians;
+
+/* Forward outputs (device): rgb [V,3,H,W], depth [V,H,W] (sum of z alpha T, background 0),
+ * alpha [V,H,W] = 1 - T_final, final_T [V,H,W], last_idx [V,H,W] int32 = 1 + position (within
+ * the pixel's tile list) of the last blended Gaussian, 0 if none.  final_T and last_idx are what
+ * the backward pass needs; rgb, depth, alpha may be NULL. */
+typedef struct gs_image {
+    float *rgb, *depth, *alpha, *final_T;
+    int32_t *last_idx;
+} gs_image;
+
+/* Upstream gradients (device): dL/drgb [V,3,H,W], dL/ddepth [V,H,W], dL/dalpha [V,H,W]; NULL = 0. */
+typedef struct gs_image_grad {
+    const float *d_rgb, *d_depth, *d_alpha;
+} gs_image_grad;
+
+/* Gaussian gradients (device), same shapes as gs_gaussians; ACCUMULATED (+=), so the caller
+ * zeroes them (or lets gs_adam_step do it) before a backward pass. */
+typedef struct gs_grads {
+    float *means, *log_scales, *quats, *opacities, *colors;
+} gs_grads;
+
+/* Device pointers into an initialised workspace, for inspection and tests.  Sizes: proj [P,12]
+ * float (mean_x, mean_y, conic_A, conic_B | conic_C, opacity, depth, radius | r, g, b, unused);
+ * tiles_touched [P] uint32 (inclusive prefix sums after gs_bin_sort); sorted_keys [K] uint64;
+ * sorted_vals [K] uint32 (flattened pair index p = pair_offset[v] + i); tile_ranges [G,2] uint32
+ * with G = V * ceil(W/tile_w) * ceil(H/tile_h); grad2d [P,12] float (dL/d mean_x, mean_y,
+ * conic A, B, C, opacity, depth, r, g, b, 0, 0); num_keys -> uint32 K. */
+typedef struct gs_ws_view {
+    float *proj;
+    uint32_t *tiles_touched;
+    uint64_t *sorted_keys;
+    uint32_t *sorted_vals;
+    uint32_t *tile_ranges;
+    float *grad2d;
+    uint32_t *num_keys;
+    int64_t num_pairs;                 /* P */
+    int64_t num_tiles;                 /* G */
+    int32_t sort_passes;               /* 8-bit LSD passes of the onesweep sort */
+    int32_t reserved;
+} gs_ws_view;
+
+/* Statistics of the last calls, read by gs_read_stats (synchronises the stream). */
+typedef struct gs_stats {
+    int64_t num_keys;                  /* K of the last gs_bin_sort                           */
+    int64_t fwd_pairs;                 /* (pixel, list entry) pairs evaluated by the forward  */
+    int64_t bwd_pairs;                 /* (pixel, list entry) pairs walked by the backward    */
+} gs_stats;
+
+const char *gs_error_string(int code);
+
+/* Library version and the device architecture it was compiled for (e.g. 1030 = sm_103a). */
+int gs_version(int *major, int *minor, int *arch);
+
+void gs_default_params(gs_params *out);
+
+/* Workspace bytes for a problem (host only, no CUDA call). */
+int gs_workspace_size(const gs_problem *pb, size_t *bytes);
+
+/* Writes the per-view tables into the workspace and clears its status block.  Call once after
+ * allocating the workspace and again whenever view_gauss_begin / view_gauss_count change. */
+int gs_workspace_init(const gs_problem *pb, void *ws, void *stream);
+
+/* Fills *out with device pointers into the workspace (host only). */
+int gs_workspace_view(const gs_problem *pb, void *ws, gs_ws_view *out);
+
+/* Synchronises `stream`, then returns the first recorded device status (GS_OK,
+ * GS_ERR_CAPACITY with *required_keys = K needed, or GS_ERR_TIMEOUT) and clears it.
+ * required_keys may be NULL. */
+int gs_check_status(const gs_problem *pb, void *ws, void *stream, int64_t *required_keys);
+
+/* Synchronises `stream` and reads the statistics counters. */
+int gs_read_stats(const gs_problem *pb, void *ws, void *stream, gs_stats *out);
+
+/* EWA projection of every (view, Gaussian) pair (Eq. 19 covariance form, world-to-camera poses
+ * of Eq. 15): camera transform, 2-D conic with dilation, radius, tile rectangle, touched-tile
+ * count; writes proj and tiles_touched in the workspace. */
+int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stream);
+
+/* Tile binning: inclusive scan of tiles_touched, one (tile|depth) key per touched tile, stable
+ * onesweep LSD radix sort (8-bit digits, decoupled look-back with bounded waits), per-tile
+ * [start, end) ranges.  K > key_capacity records GS_ERR_CAPACITY (keys beyond capacity dropped). */
+int gs_bin_sort(const gs_problem *pb, void *ws, void *stream);
+
+/* Front-to-back compositing of every (view, tile) of the problem in one persistent launch.
+ * g supplies nothing here but is kept for symmetry (colours were captured by gs_project). */
+int gs_render_fwd(const gs_problem *pb, void *ws, const gs_image *out, void *stream);
+
+/* Adjoint of the compositing, back to front from final_T and last_idx (no per-pixel lists),
+ * followed by the projection adjoint: accumulates dL/d(means, log_scales, quats, opacities,
+ * colors) into `grads` (+=) and leaves per-view pose partial sums in the workspace. */
+int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const gs_image *fwd,
+                  const gs_image_grad *dimg, const gs_grads *grads, void *stream);
+
+/* dL/d xi for each view, xi = (rho, phi) the left perturbation T <- Exp(xi) T of the world-to-camera
+ * pose at xi = 0 (the per-keyframe pose delta of Sec. III-D): pose_grad [V,6] (rho_x, rho_y, rho_z,
+ * phi_x, phi_y, phi_z), overwritten, summed deterministically from the partials of gs_render_bwd. */
+int gs_pose_grad(const gs_problem *pb, void *ws, float *pose_grad, void *stream);
+
+/* Photometric + depth L1 terms of the mapping loss (Eq. 4): L = w_rgb mean|rgb - rgb_t| +
+ * w_depth mean|depth - depth_t| over `views` views of width x height.  Writes d_rgb [V,3,H,W],
+ * d_depth [V,H,W] (d_depth / depth / depth_t may be NULL when w_depth = 0) and writes L to
+ * *loss (device double, overwritten).  sign(0) = 0. */
+int gs_loss_l1(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
+               const float *depth, const float *depth_t, float w_rgb, float w_depth,
+               float *d_rgb, float *d_depth, double *loss, void *stream);
+
+/* L = w_l1 mean|rgb - rgb_t| + w_ssim (1 - SSIM(rgb, rgb_t)) (Eq. 23's photometric and
+ * structural terms): 11x11 Gaussian window, sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2,
+ * mean over views, channels, pixels.  Writes d_rgb and writes L to *loss (overwritten).
+ * `scratch` is a device buffer of gs_ssim_scratch_size() bytes, 256-byte aligned. */
+size_t gs_ssim_scratch_size(int32_t views, int32_t width, int32_t height);
+int gs_loss_l1_ssim(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
+                    float w_l1, float w_ssim, float *d_rgb, double *loss, void *scratch, void *stream);
+
+/* One bias-corrected Adam step over all Gaussian parameters (beta1 0.9, beta2 0.999, eps 1e-15)
+ * with per-group learning rates lr[5] = {means, log_scales, quats, opacity_logits, colors}.
+ * The opacity group steps logit(o): its gradient is dL/do * o (1 - o), and `opacities` is
+ * rewritten as sigmoid(logit).  `step` is a device int32 incremented by the kernel (bias
+ * correction uses the incremented value).  Moments m, v are [N,14] each (layout: means 3,
+ * log_scales 3, quats 4, logit 1, colors 3).  If zero_grads != 0 the gradients are cleared. */
+typedef struct gs_adam_state {
+    float *means, *log_scales, *quats, *opacity_logits, *opacities, *colors;
+    float *m, *v;
+    int32_t *step;
+} gs_adam_state;
+int gs_adam_step(int64_t n, const gs_adam_state *st, const gs_grads *grads, const float lr[5],
+                 int32_t zero_grads, void *stream);
+
+/* Zeroes the five gradient arrays of n Gaussians (stream-ordered memsets). */
+int gs_grads_zero(int64_t n, const gs_grads *grads, void *stream);
+
+/* Number of kernels this library has launched in the calling process since it was loaded
+ * (host-side counter; graph replays are not counted). */
+int64_t gs_launch_count(void);
+
+/* ---- test hooks (no counterpart in the paper; they exist to check the library itself) ---- */
+
+/* y_spec[i] = the library's FP32 decision-chain exponential of x[i]; y_cuda[i] = CUDA's expf(x[i])
+ * (either output may be NULL).  n elements, device arrays. */
+int gs_debug_expf(const float *x, float *y_spec, float *y_cuda, int64_t n, void *stream);
+
+/* Bounded-wait check of the decoupled look-back: runs the inclusive scan over n ones in `scratch`
+ * (device, gs_debug_scan_scratch_size(n) bytes) with partition `silent_partition` never
+ * publishing its count (-1: normal run) and a short spin limit (about a millisecond), then
+ * synchronises and returns the recorded status: GS_ERR_TIMEOUT when a successor gave up waiting,
+ * GS_OK otherwise.  *total receives the scan total (n on a normal run). */
+size_t gs_debug_scan_scratch_size(int64_t n);
+int gs_debug_scan_timeout(void *scratch, int64_t n, int32_t silent_partition, void *stream, int64_t *total);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H_ */

@@ -1,0 +1,464 @@
+// gs_api.cu -- the C ABI of libgs: argument validation, workspace layout, stage launches.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <vector>
+
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+int device_sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!cache[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int tile_ok(int tw, int th) {
+    return (tw == 16 && th == 16) || (tw == 16 && th == 8) || (tw == 32 && th == 16);
+}
+
+int compute_layout(const gs_problem *pb, Layout *L) {
+    if (!pb || !L) return GS_ERR_INVALID_ARG;
+    const gs_params &p = pb->params;
+    if (pb->num_views < 1 || pb->num_views > GS_MAX_VIEWS) return GS_ERR_INVALID_ARG;
+    if (pb->width < 1 || pb->height < 1 || pb->width > 16384 || pb->height > 16384) return GS_ERR_INVALID_ARG;
+    if (!tile_ok(p.tile_w, p.tile_h)) return GS_ERR_INVALID_ARG;
+    if (!pb->view_gauss_begin || !pb->view_gauss_count || pb->num_gaussians < 0) return GS_ERR_INVALID_ARG;
+    if (pb->key_capacity < 1 || pb->key_capacity >= (1LL << 30)) return GS_ERR_INVALID_ARG;
+    if (!(p.alpha_max > 0.f && p.alpha_max < 1.f) || !(p.t_min > 0.f && p.t_min < 1.f) || !(p.alpha_min >= 0.f) ||
+        !(p.dilation >= 0.f) || !(p.radius_sigmas > 0.f) || !(p.near_plane > 0.f))
+        return GS_ERR_INVALID_ARG;
+    std::memset(L, 0, sizeof(*L));
+    L->V = pb->num_views;
+    L->W = pb->width;
+    L->H = pb->height;
+    L->tw = p.tile_w;
+    L->th = p.tile_h;
+    L->Tx = (L->W + L->tw - 1) / L->tw;
+    L->Ty = (L->H + L->th - 1) / L->th;
+    L->G = (long long)L->V * L->Tx * L->Ty;
+    L->N = pb->num_gaussians;
+    L->cap = pb->key_capacity;
+    long long P = 0, maxc = 0;
+    for (int v = 0; v < L->V; ++v) {
+        const long long b = pb->view_gauss_begin[v], c = pb->view_gauss_count[v];
+        if (b < 0 || c < 0 || b + c > L->N) return GS_ERR_INVALID_ARG;
+        P += c;
+        maxc = std::max(maxc, c);
+    }
+    if (P >= 0xffffffffLL) return GS_ERR_INVALID_ARG;   // pair indices are 32-bit
+    L->P = P;
+    L->max_count = maxc;
+    L->max_chunks = std::max<long long>(1, (maxc + kChunk - 1) / kChunk);
+    int gbits = 0;
+    while ((1LL << gbits) < L->G) ++gbits;
+    L->passes = (32 + gbits + 7) / 8;
+    if (L->passes > kMaxPasses) return GS_ERR_INVALID_ARG;
+    L->scan_parts = std::max<long long>(1, (P + kScanTile - 1) / kScanTile);
+    L->sort_parts = std::max<long long>(1, (L->cap + kSortTile - 1) / kSortTile);
+    long long chunks_total = 0;
+    for (int v = 0; v < L->V; ++v) chunks_total += (pb->view_gauss_count[v] + kChunk - 1) / kChunk;
+    size_t o = 0;
+    L->o_status = o; o = align256(o + sizeof(DevStatus));
+    L->o_views = o; o = align256(o + sizeof(ViewEntry) * L->V);
+    L->o_proj = o; o = align256(o + sizeof(float) * 12 * (size_t)std::max<long long>(P, 1));
+    L->o_touched = o; o = align256(o + sizeof(uint32_t) * (size_t)std::max<long long>(P, 1) + 64);
+    L->o_scan_state = o; o = align256(o + sizeof(unsigned long long) * L->scan_parts);
+    for (int k = 0; k < 2; ++k) { L->o_keys[k] = o; o = align256(o + sizeof(uint64_t) * (size_t)L->cap); }
+    for (int k = 0; k < 2; ++k) { L->o_vals[k] = o; o = align256(o + sizeof(uint32_t) * (size_t)L->cap); }
+    L->o_hist = o; o = align256(o + sizeof(uint32_t) * kMaxPasses * 256);
+    L->o_sort_state = o; o = align256(o + sizeof(uint32_t) * 256 * (size_t)L->sort_parts * L->passes);
+    L->o_ranges = o; o = align256(o + sizeof(uint32_t) * 2 * (size_t)L->G);
+    L->o_g2d = o; o = align256(o + sizeof(float) * 12 * (size_t)std::max<long long>(P, 1));
+    L->o_pose_part = o; o = align256(o + sizeof(float) * 8 * (size_t)std::max<long long>(chunks_total, 1));
+    L->total = o;
+    return GS_OK;
+}
+
+static int ws_ok(const void *ws) { return ws && ((uintptr_t)ws & 255) == 0; }
+
+}  // namespace gs
+
+using namespace gs;
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+const char *gs_error_string(int code) {
+    switch (code) {
+    case GS_OK: return "ok";
+    case GS_ERR_INVALID_ARG: return "invalid argument";
+    case GS_ERR_CAPACITY: return "key capacity exceeded";
+    case GS_ERR_TIMEOUT: return "bounded device wait timed out";
+    case GS_ERR_CUDA: return "CUDA error";
+    case GS_ERR_DEVICE_FAULT: return "device consistency check failed";
+    default: return "unknown error";
+    }
+}
+
+int gs_version(int *major, int *minor, int *arch) {
+    if (major) *major = 1;
+    if (minor) *minor = 0;
+#ifdef GS_ARCH
+    if (arch) *arch = GS_ARCH;
+#else
+    if (arch) *arch = 0;
+#endif
+    return GS_OK;
+}
+
+void gs_default_params(gs_params *out) {
+    if (!out) return;
+    out->tile_w = 16;
+    out->tile_h = 16;
+    out->near_plane = 0.2f;
+    out->dilation = 0.3f;
+    out->radius_sigmas = 3.0f;
+    out->alpha_max = 0.99f;
+    out->alpha_min = 1.0f / 255.0f;
+    out->t_min = 1e-4f;
+    out->bg[0] = out->bg[1] = out->bg[2] = 0.0f;
+}
+
+int gs_workspace_size(const gs_problem *pb, size_t *bytes) {
+    Layout L;
+    int rc = compute_layout(pb, &L);
+    if (rc) return rc;
+    if (!bytes) return GS_ERR_INVALID_ARG;
+    *bytes = L.total;
+    return GS_OK;
+}
+
+__global__ void k_write_views(ViewEntry *dst, int first, int n, ViewEntry e0, ViewEntry e1, ViewEntry e2,
+                              ViewEntry e3, ViewEntry e4, ViewEntry e5, ViewEntry e6, ViewEntry e7) {
+    const ViewEntry es[8] = {e0, e1, e2, e3, e4, e5, e6, e7};
+    if ((int)threadIdx.x < n) dst[first + threadIdx.x] = es[threadIdx.x];
+}
+
+int gs_workspace_init(const gs_problem *pb, void *ws, void *stream) {
+    Layout L;
+    int rc = compute_layout(pb, &L);
+    if (rc) return rc;
+    if (!ws_ok(ws)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<ViewEntry> ve(L.V);
+    long long pair = 0, chunk = 0;
+    for (int v = 0; v < L.V; ++v) {
+        ve[v].gauss_begin = pb->view_gauss_begin[v];
+        ve[v].count = pb->view_gauss_count[v];
+        ve[v].pair_off = pair;
+        ve[v].chunk_off = chunk;
+        pair += ve[v].count;
+        chunk += (ve[v].count + kChunk - 1) / kChunk;
+    }
+    if (cudaMemsetAsync(ws_ptr<void>(ws, L.o_status), 0, sizeof(DevStatus), s) != cudaSuccess) return GS_ERR_CUDA;
+    ViewEntry *dst = ws_ptr<ViewEntry>(ws, L.o_views);
+    for (int v0 = 0; v0 < L.V; v0 += 8) {
+        ViewEntry e[8];
+        std::memset(e, 0, sizeof(e));
+        const int n = std::min(8, L.V - v0);
+        for (int k = 0; k < n; ++k) e[k] = ve[v0 + k];
+        k_write_views<<<1, 8, 0, s>>>(dst, v0, n, e[0], e[1], e[2], e[3], e[4], e[5], e[6], e[7]);
+        count_launches(1);
+    }
+    return check_launch();
+}
+
+int gs_workspace_view(const gs_problem *pb, void *ws, gs_ws_view *out) {
+    Layout L;
+    int rc = compute_layout(pb, &L);
+    if (rc) return rc;
+    if (!ws_ok(ws) || !out) return GS_ERR_INVALID_ARG;
+    out->proj = ws_ptr<float>(ws, L.o_proj);
+    out->tiles_touched = ws_ptr<uint32_t>(ws, L.o_touched);
+    out->sorted_keys = ws_ptr<uint64_t>(ws, L.o_keys[L.passes & 1]);
+    out->sorted_vals = ws_ptr<uint32_t>(ws, L.o_vals[L.passes & 1]);
+    out->tile_ranges = ws_ptr<uint32_t>(ws, L.o_ranges);
+    out->grad2d = ws_ptr<float>(ws, L.o_g2d);
+    out->num_keys = reinterpret_cast<uint32_t *>(&ws_ptr<DevStatus>(ws, L.o_status)->num_keys);
+    out->num_pairs = L.P;
+    out->num_tiles = L.G;
+    out->sort_passes = L.passes;
+    out->reserved = 0;
+    return GS_OK;
+}
+
+int gs_check_status(const gs_problem *pb, void *ws, void *stream, int64_t *required_keys) {
+    Layout L;
+    int rc = compute_layout(pb, &L);
+    if (rc) return rc;
+    if (!ws_ok(ws)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevStatus h;
+    DevStatus *d = ws_ptr<DevStatus>(ws, L.o_status);
+    if (cudaMemcpyAsync(&h, d, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GS_ERR_CUDA;
+    if (required_keys) *required_keys = (int64_t)h.required_keys;
+    if (h.code != 0) {
+        int32_t zero[2] = {0, 0};
+        if (cudaMemcpyAsync(d, zero, sizeof(zero), cudaMemcpyHostToDevice, s) != cudaSuccess) return GS_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return GS_ERR_CUDA;
+    }
+    return h.code;
+}
+
+int gs_read_stats(const gs_problem *pb, void *ws, void *stream, gs_stats *out) {
+    Layout L;
+    int rc = compute_layout(pb, &L);
+    if (rc) return rc;
+    if (!ws_ok(ws) || !out) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevStatus h;
+    if (cudaMemcpyAsync(&h, ws_ptr<DevStatus>(ws, L.o_status), sizeof(DevStatus), cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+        return GS_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GS_ERR_CUDA;
+    out->num_keys = (int64_t)h.num_keys;
+    out->fwd_pairs = (int64_t)h.fwd_pairs;
+    out->bwd_pairs = (int64_t)h.bwd_pairs;
+    return GS_OK;
+}
+
+int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stream) {
+    Layout L;
+    int rc = compute_layout(pb, &L);
+    if (rc) return rc;
+    if (!ws_ok(ws) || !g || !pb->cameras) return GS_ERR_INVALID_ARG;
+    if (L.N > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacities || !g->colors)) return GS_ERR_INVALID_ARG;
+    if (((uintptr_t)g->quats & 15) != 0) return GS_ERR_INVALID_ARG;
+    if (L.P == 0) return GS_OK;
+    ProjArgs a;
+    a.views = ws_ptr<ViewEntry>(ws, L.o_views);
+    a.cams = pb->cameras;
+    a.means = g->means; a.log_scales = g->log_scales; a.quats = g->quats;
+    a.opacities = g->opacities; a.colors = g->colors;
+    a.proj = ws_ptr<float4>(ws, L.o_proj);
+    a.touched = ws_ptr<uint32_t>(ws, L.o_touched);
+    a.W = L.W; a.H = L.H;
+    a.tw = (float)L.tw; a.th = (float)L.th; a.Tx = (float)L.Tx; a.Ty = (float)L.Ty;
+    a.near_plane = pb->params.near_plane; a.dil = pb->params.dilation; a.sigmas = pb->params.radius_sigmas;
+    launch_project(L, a, (cudaStream_t)stream);
+    return check_launch();
+}
+
+static BinArgs make_bin_args(const Layout &L, void *ws) {
+    BinArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.views = ws_ptr<ViewEntry>(ws, L.o_views);
+    a.touched = ws_ptr<uint32_t>(ws, L.o_touched);
+    a.scan_state = ws_ptr<unsigned long long>(ws, L.o_scan_state);
+    a.proj = ws_ptr<float4>(ws, L.o_proj);
+    a.g2d = ws_ptr<float4>(ws, L.o_g2d);
+    for (int k = 0; k < 2; ++k) {
+        a.keys[k] = ws_ptr<uint64_t>(ws, L.o_keys[k]);
+        a.vals[k] = ws_ptr<uint32_t>(ws, L.o_vals[k]);
+    }
+    a.hist = ws_ptr<uint32_t>(ws, L.o_hist);
+    a.sort_state = ws_ptr<uint32_t>(ws, L.o_sort_state);
+    a.ranges = ws_ptr<uint32_t>(ws, L.o_ranges);
+    a.st = ws_ptr<DevStatus>(ws, L.o_status);
+    a.V = L.V; a.Tx = L.Tx; a.Ty = L.Ty; a.passes = L.passes;
+    a.tw = (float)L.tw; a.th = (float)L.th;
+    a.P = L.P; a.cap = L.cap; a.sort_parts = L.sort_parts; a.max_chunks = L.max_chunks; a.G = L.G;
+    a.fault_scan_part = -1;
+    a.spin_limit = kSpinLimit;
+    return a;
+}
+
+int gs_bin_sort(const gs_problem *pb, void *ws, void *stream) {
+    Layout L;
+    int rc = compute_layout(pb, &L);
+    if (rc) return rc;
+    if (!ws_ok(ws)) return GS_ERR_INVALID_ARG;
+    BinArgs a = make_bin_args(L, ws);
+    return run_bin_sort(a, (cudaStream_t)stream);
+}
+
+int gs_render_fwd(const gs_problem *pb, void *ws, const gs_image *out, void *stream) {
+    Layout L;
+    int rc = compute_layout(pb, &L);
+    if (rc) return rc;
+    if (!ws_ok(ws) || !out || !out->final_T || !out->last_idx) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    FwdArgs a;
+    a.proj = ws_ptr<const float4>(ws, L.o_proj);
+    a.vals = ws_ptr<const uint32_t>(ws, L.o_vals[L.passes & 1]);
+    a.ranges = ws_ptr<const uint32_t>(ws, L.o_ranges);
+    a.rgb = out->rgb; a.depth = out->depth; a.alpha = out->alpha; a.finalT = out->final_T; a.last = out->last_idx;
+    a.st = ws_ptr<DevStatus>(ws, L.o_status);
+    a.W = L.W; a.H = L.H; a.Tx = L.Tx; a.Ty = L.Ty; a.G = L.G; a.P = std::max<long long>(L.P, 1);
+    const gs_params &p = pb->params;
+    a.amax = p.alpha_max; a.amin = p.alpha_min; a.tmin = p.t_min;
+    a.bg0 = p.bg[0]; a.bg1 = p.bg[1]; a.bg2 = p.bg[2];
+    return launch_render_fwd(L.tw, L.th, a, s);
+}
+
+int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const gs_image *fwd,
+                  const gs_image_grad *dimg, const gs_grads *grads, void *stream) {
+    Layout L;
+    int rc = compute_layout(pb, &L);
+    if (rc) return rc;
+    if (!ws_ok(ws) || !g || !fwd || !fwd->final_T || !fwd->last_idx || !dimg || !grads || !pb->cameras)
+        return GS_ERR_INVALID_ARG;
+    if (L.N > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacities || !grads->colors))
+        return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    BwdArgs a;
+    a.proj = ws_ptr<const float4>(ws, L.o_proj);
+    a.vals = ws_ptr<const uint32_t>(ws, L.o_vals[L.passes & 1]);
+    a.ranges = ws_ptr<const uint32_t>(ws, L.o_ranges);
+    a.finalT = fwd->final_T; a.last = fwd->last_idx;
+    a.d_rgb = dimg->d_rgb; a.d_depth = dimg->d_depth; a.d_alpha = dimg->d_alpha;
+    a.g2d = ws_ptr<float>(ws, L.o_g2d);
+    a.st = ws_ptr<DevStatus>(ws, L.o_status);
+    a.W = L.W; a.H = L.H; a.Tx = L.Tx; a.Ty = L.Ty; a.G = L.G; a.P = std::max<long long>(L.P, 1);
+    const gs_params &p = pb->params;
+    a.amax = p.alpha_max; a.amin = p.alpha_min;
+    a.bg0 = p.bg[0]; a.bg1 = p.bg[1]; a.bg2 = p.bg[2];
+    rc = launch_render_bwd(L.tw, L.th, a, s);
+    if (rc) return rc;
+    if (L.P == 0) return GS_OK;
+    ProjBwdArgs b;
+    b.views = ws_ptr<ViewEntry>(ws, L.o_views);
+    b.cams = pb->cameras;
+    b.means = g->means; b.log_scales = g->log_scales; b.quats = g->quats;
+    b.touched_incl = ws_ptr<const uint32_t>(ws, L.o_touched);
+    b.g2d = ws_ptr<const float4>(ws, L.o_g2d);
+    b.g_means = grads->means; b.g_ls = grads->log_scales; b.g_quats = grads->quats;
+    b.g_op = grads->opacities; b.g_col = grads->colors;
+    b.pose_part = ws_ptr<float>(ws, L.o_pose_part);
+    b.W = L.W; b.H = L.H;
+    b.dil = p.dilation;
+    launch_project_bwd(L, b, s);
+    return check_launch();
+}
+
+int gs_pose_grad(const gs_problem *pb, void *ws, float *pose_grad, void *stream) {
+    Layout L;
+    int rc = compute_layout(pb, &L);
+    if (rc) return rc;
+    if (!ws_ok(ws) || !pose_grad) return GS_ERR_INVALID_ARG;
+    launch_pose_reduce(L, ws_ptr<ViewEntry>(ws, L.o_views), ws_ptr<float>(ws, L.o_pose_part), pose_grad,
+                       (cudaStream_t)stream);
+    return check_launch();
+}
+
+int gs_loss_l1(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
+               const float *depth, const float *depth_t, float w_rgb, float w_depth, float *d_rgb, float *d_depth,
+               double *loss, void *stream) {
+    if (views < 1 || width < 1 || height < 1 || !rgb || !rgb_t || !d_rgb || !loss) return GS_ERR_INVALID_ARG;
+    if (w_depth != 0.f && (!depth || !depth_t || !d_depth)) return GS_ERR_INVALID_ARG;
+    return launch_loss_l1(views, width, height, rgb, rgb_t, depth, depth_t, w_rgb, w_depth, d_rgb, d_depth, loss,
+                          (cudaStream_t)stream);
+}
+
+size_t gs_ssim_scratch_size(int32_t views, int32_t width, int32_t height) {
+    if (views < 1 || width < 1 || height < 1) return 0;
+    return ssim_scratch_bytes(views, width, height);
+}
+
+int gs_loss_l1_ssim(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t, float w_l1,
+                    float w_ssim, float *d_rgb, double *loss, void *scratch, void *stream) {
+    if (views < 1 || width < 1 || height < 1 || !rgb || !rgb_t || !d_rgb || !loss || !ws_ok(scratch))
+        return GS_ERR_INVALID_ARG;
+    return launch_loss_l1_ssim(views, width, height, rgb, rgb_t, w_l1, w_ssim, d_rgb, loss, scratch,
+                               (cudaStream_t)stream);
+}
+
+int gs_adam_step(int64_t n, const gs_adam_state *st, const gs_grads *grads, const float lr[5], int32_t zero_grads,
+                 void *stream) {
+    if (n < 0 || !st || !grads || !lr || !st->step || !st->m || !st->v) return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!st->means || !st->log_scales || !st->quats || !st->opacity_logits || !st->opacities ||
+                  !st->colors || !grads->means || !grads->log_scales || !grads->quats || !grads->opacities ||
+                  !grads->colors))
+        return GS_ERR_INVALID_ARG;
+    return launch_adam(n, *st, *grads, lr, zero_grads, (cudaStream_t)stream);
+}
+
+__global__ void k_debug_expf(const float *x, float *ys, float *yc, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = x[i];
+        if (ys) ys[i] = spec_expf(v);
+        if (yc) yc[i] = expf(v);
+    }
+}
+
+int gs_grads_zero(int64_t n, const gs_grads *g, void *stream) {
+    if (n < 0 || !g) return GS_ERR_INVALID_ARG;
+    if (n == 0) return GS_OK;
+    if (!g->means || !g->log_scales || !g->quats || !g->opacities || !g->colors) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t sz[5] = {12, 12, 16, 4, 12};
+    float *p[5] = {g->means, g->log_scales, g->quats, g->opacities, g->colors};
+    for (int k = 0; k < 5; ++k)
+        if (cudaMemsetAsync(p[k], 0, sz[k] * (size_t)n, s) != cudaSuccess) return GS_ERR_CUDA;
+    return GS_OK;
+}
+
+int64_t gs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int gs_debug_expf(const float *x, float *y_spec, float *y_cuda, int64_t n, void *stream) {
+    if (!x || n < 0) return GS_ERR_INVALID_ARG;
+    if (n == 0) return GS_OK;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 4096);
+    k_debug_expf<<<grid, 256, 0, (cudaStream_t)stream>>>(x, y_spec, y_cuda, n);
+    count_launches(1);
+    return check_launch();
+}
+
+__global__ void k_fill_ones(uint32_t *p, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = 1u;
+}
+
+size_t gs_debug_scan_scratch_size(int64_t n) {
+    if (n < 1) return 0;
+    const long long parts = (n + kScanTile - 1) / kScanTile;
+    return align256(sizeof(DevStatus)) + align256(sizeof(uint32_t) * (size_t)n) +
+           align256(sizeof(unsigned long long) * (size_t)parts);
+}
+
+int gs_debug_scan_timeout(void *scratch, int64_t n, int32_t silent_partition, void *stream, int64_t *total) {
+    if (!ws_ok(scratch) || n < 1 || n > (1LL << 28)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    BinArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.st = ws_ptr<DevStatus>(scratch, 0);
+    a.touched = ws_ptr<uint32_t>(scratch, align256(sizeof(DevStatus)));
+    a.scan_state = ws_ptr<unsigned long long>(scratch, align256(sizeof(DevStatus)) + align256(sizeof(uint32_t) * (size_t)n));
+    a.P = n;
+    a.cap = (1LL << 30) - 1;
+    a.fault_scan_part = silent_partition;
+    a.spin_limit = 1ull << 14;
+    if (cudaMemsetAsync(a.st, 0, sizeof(DevStatus), s) != cudaSuccess) return GS_ERR_CUDA;
+    k_fill_ones<<<64, 256, 0, s>>>(a.touched, n);
+    count_launches(1);
+    int rc = run_scan_only(a, s);
+    if (rc) return rc;
+    DevStatus h;
+    if (cudaMemcpyAsync(&h, a.st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GS_ERR_CUDA;
+    if (total) *total = (int64_t)h.num_keys;
+    return h.code;
+}
+
+}  // extern "C"

@@ -1,0 +1,242 @@
+// gs_internal.cuh -- shared device helpers of libgs (sm_103a).
+//
+// The FP32 decision chain (culling, tile rectangle, depth key, sigma, alpha, transmittance) is
+// written with explicit round-to-nearest intrinsics (__fmul_rn, __fadd_rn, __fsub_rn, __fmaf_rn,
+// __fdiv_rn, __fsqrt_rn): the compiler never contracts or reorders them, so every branch is taken
+// exactly as the operation sequence below prescribes, whatever the -fmad setting of the
+// translation unit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr int kMaxPasses = 8;          // 8-bit digits of a 64-bit key
+constexpr int kSortThreads = 256;
+constexpr int kSortIPT = 16;
+constexpr int kSortTile = kSortThreads * kSortIPT;   // keys per onesweep partition
+constexpr int kScanThreads = 256;
+constexpr int kScanIPT = 16;
+constexpr int kScanTile = kScanThreads * kScanIPT;
+constexpr int kChunk = 256;            // (view, Gaussian) pairs per projection block
+constexpr unsigned long long kSpinLimit = 1ull << 21;  // bounded waits (x ~100 ns sleep)
+
+// counters inside the status block (zeroed by the call that uses them)
+enum Counter { kCtrScan = 0, kCtrSort0 = 1, kCtrFwd = 12, kCtrBwd = 13, kNumCounters = 32 };
+
+struct DevStatus {
+    int32_t code;                 // first recorded GS_ERR_* (0 = none)
+    int32_t where;                // stage tag of that error
+    unsigned long long required_keys;
+    unsigned long long num_keys;  // K written by the scan
+    unsigned long long fwd_pairs;
+    unsigned long long bwd_pairs;
+    uint32_t ctr[kNumCounters];
+};
+
+struct ViewEntry {                // per-view table in the workspace (32 bytes)
+    long long gauss_begin;
+    long long count;
+    long long pair_off;
+    long long chunk_off;
+};
+
+struct Layout {
+    int V, W, H, tw, th, Tx, Ty, passes;
+    long long G, P, N, cap, max_count, max_chunks;
+    long long scan_parts, sort_parts;
+    size_t o_status, o_views, o_proj, o_touched, o_scan_state, o_keys[2], o_vals[2], o_hist,
+        o_sort_state, o_ranges, o_g2d, o_pose_part, total;
+};
+
+// ------------------------------------------------------------------------------------------
+// error recording (first error wins)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void record_error(DevStatus *st, int code, int where) {
+    if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
+}
+
+// ------------------------------------------------------------------------------------------
+// FP32 decision-chain arithmetic
+// ------------------------------------------------------------------------------------------
+namespace fp {
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+}  // namespace fp
+
+// e^x in FP32: x = k ln2 + r with k = rint(x log2 e) and a two-part ln2 (hi has 16 significant
+// bits so k*hi is exact for |k| < 256), e^r by the degree-7 Taylor polynomial in Horner form with
+// fused multiply-adds, then 2^k through the exponent field.  x <= -87 gives 0, x > 88 gives +inf.
+__device__ __forceinline__ float spec_expf(float x) {
+    if (!(x > -87.0f)) return 0.0f;
+    if (x > 88.0f) return __int_as_float(0x7f800000);
+    const float kLog2e = 0x1.715476p+0f;
+    const float kLn2Hi = 0x1.62e4p-1f;
+    const float kLn2Lo = 0x1.7f7d1cp-20f;
+    float kf = rintf(fp::mul(x, kLog2e));
+    float r = fp::fma(-kf, kLn2Hi, x);
+    r = fp::fma(-kf, kLn2Lo, r);
+    float p = 0x1.a01a02p-13f;              // 1/7!
+    p = fp::fma(p, r, 0x1.6c16c2p-10f);     // 1/6!
+    p = fp::fma(p, r, 0x1.111112p-7f);      // 1/5!
+    p = fp::fma(p, r, 0x1.555556p-5f);      // 1/4!
+    p = fp::fma(p, r, 0x1.555556p-3f);      // 1/3!
+    p = fp::fma(p, r, 0.5f);
+    p = fp::fma(p, r, 1.0f);
+    p = fp::fma(p, r, 1.0f);
+    int k = (int)kf;
+    return fp::mul(p, __int_as_float((k + 127) << 23));
+}
+
+struct SpecProj {
+    float mx, my, A, B, C, z, rf;
+    int x0, x1, y0, y1;
+    bool visible;
+};
+
+// Tile rectangle of the bounding square [m - r, m + r] (x1, y1 exclusive), clamped to the grid.
+__device__ __forceinline__ void spec_rect(float mx, float my, float rf, float tw, float th, float Tx, float Ty,
+                                          int &x0, int &x1, int &y0, int &y1) {
+    float fx0 = fminf(fmaxf(floorf(fp::div(fp::sub(mx, rf), tw)), 0.0f), Tx);
+    float fx1 = fminf(fmaxf(fp::add(floorf(fp::div(fp::add(mx, rf), tw)), 1.0f), 0.0f), Tx);
+    float fy0 = fminf(fmaxf(floorf(fp::div(fp::sub(my, rf), th)), 0.0f), Ty);
+    float fy1 = fminf(fmaxf(fp::add(floorf(fp::div(fp::add(my, rf), th)), 1.0f), 0.0f), Ty);
+    x0 = (int)fx0; x1 = (int)fx1; y0 = (int)fy0; y1 = (int)fy1;
+}
+
+// EWA projection of one Gaussian into one view (the FP32 decision chain).
+//   p_c = R mu + t; unit quaternion -> rotation Rq; M = Rq diag(exp(l));
+//   J = [[fx/z, 0, -fx tx/z], [0, fy/z, -fy ty/z]] with tx, ty = x/z, y/z clamped to
+//   +-0.65 W/fx, +-0.65 H/fy; U = (J R) M; Sigma_2 = U U^T + dilation I; conic = Sigma_2^-1;
+//   mean2D = (fx x/z + cx, fy y/z + cy); radius = ceil(sigmas sqrt(lambda_max)).
+__device__ __forceinline__ SpecProj spec_project(const float *R, const float *t, float fx, float fy, float cx,
+                                                 float cy, int W, int H, float tw, float th, float Tx, float Ty,
+                                                 float near_plane, float dil, float sigmas, float m0, float m1,
+                                                 float m2, float l0, float l1, float l2, float qw, float qx,
+                                                 float qy, float qz) {
+    using namespace fp;
+    SpecProj o;
+    o.visible = false;
+    o.mx = o.my = o.A = o.B = o.C = o.rf = 0.0f;
+    o.x0 = o.x1 = o.y0 = o.y1 = 0;
+    float xc = fma(R[0], m0, fma(R[1], m1, fma(R[2], m2, t[0])));
+    float yc = fma(R[3], m0, fma(R[4], m1, fma(R[5], m2, t[1])));
+    float zc = fma(R[6], m0, fma(R[7], m1, fma(R[8], m2, t[2])));
+    o.z = zc;
+    if (!(zc > near_plane)) return o;
+    float n2 = fma(qw, qw, fma(qx, qx, fma(qy, qy, mul(qz, qz))));
+    if (!(n2 > 0.0f)) return o;
+    float inv = div(1.0f, sqrt(n2));
+    float w = mul(qw, inv), x = mul(qx, inv), y = mul(qy, inv), z = mul(qz, inv);
+    float xx = mul(x, x), yy = mul(y, y), zz = mul(z, z);
+    float xy = mul(x, y), xz = mul(x, z), yz = mul(y, z);
+    float wx = mul(w, x), wy = mul(w, y), wz = mul(w, z);
+    float Rq[9];
+    Rq[0] = sub(1.0f, mul(2.0f, add(yy, zz)));
+    Rq[1] = mul(2.0f, sub(xy, wz));
+    Rq[2] = mul(2.0f, add(xz, wy));
+    Rq[3] = mul(2.0f, add(xy, wz));
+    Rq[4] = sub(1.0f, mul(2.0f, add(xx, zz)));
+    Rq[5] = mul(2.0f, sub(yz, wx));
+    Rq[6] = mul(2.0f, sub(xz, wy));
+    Rq[7] = mul(2.0f, add(yz, wx));
+    Rq[8] = sub(1.0f, mul(2.0f, add(xx, yy)));
+    float s0 = spec_expf(l0), s1 = spec_expf(l1), s2 = spec_expf(l2);
+    float M[9];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        M[3 * j + 0] = mul(Rq[3 * j + 0], s0);
+        M[3 * j + 1] = mul(Rq[3 * j + 1], s1);
+        M[3 * j + 2] = mul(Rq[3 * j + 2], s2);
+    }
+    float iz = div(1.0f, zc);
+    float limx = div(mul(0.65f, (float)W), fx);
+    float limy = div(mul(0.65f, (float)H), fy);
+    float ux = mul(xc, iz), uy = mul(yc, iz);
+    float tx = fminf(limx, fmaxf(-limx, ux));
+    float ty = fminf(limy, fmaxf(-limy, uy));
+    float J00 = mul(fx, iz), J11 = mul(fy, iz);
+    float J02 = -mul(mul(fx, tx), iz), J12 = -mul(mul(fy, ty), iz);
+    float Wm[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Wm[k] = fma(J00, R[k], mul(J02, R[6 + k]));
+        Wm[3 + k] = fma(J11, R[3 + k], mul(J12, R[6 + k]));
+    }
+    float U[6];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            U[3 * r + k] = fma(Wm[3 * r], M[k], fma(Wm[3 * r + 1], M[3 + k], mul(Wm[3 * r + 2], M[6 + k])));
+    float a = add(fma(U[0], U[0], fma(U[1], U[1], mul(U[2], U[2]))), dil);
+    float b = fma(U[0], U[3], fma(U[1], U[4], mul(U[2], U[5])));
+    float c = add(fma(U[3], U[3], fma(U[4], U[4], mul(U[5], U[5]))), dil);
+    float det = fma(a, c, -mul(b, b));
+    if (!(det > 0.0f)) return o;
+    o.A = div(c, det);
+    o.B = div(-b, det);
+    o.C = div(a, det);
+    o.mx = fma(fx, ux, cx);
+    o.my = fma(fy, uy, cy);
+    float mid = mul(0.5f, add(a, c));
+    float disc = fma(mid, mid, -det);
+    float lam = add(mid, sqrt(fmaxf(0.0f, disc)));
+    o.rf = ceilf(mul(sigmas, sqrt(lam)));
+    spec_rect(o.mx, o.my, o.rf, tw, th, Tx, Ty, o.x0, o.x1, o.y0, o.y1);
+    o.visible = (o.x1 > o.x0) && (o.y1 > o.y0);
+    return o;
+}
+
+// sigma = 1/2 (A dx^2 + C dy^2) + B dx dy with d = pixel - mean2D (decision chain order).
+__device__ __forceinline__ float spec_sigma(float A, float B, float C, float dx, float dy) {
+    float q = fp::fma(fp::mul(A, dx), dx, fp::mul(fp::mul(C, dy), dy));
+    return fp::fma(fp::mul(B, dx), dy, fp::mul(0.5f, q));
+}
+
+// ------------------------------------------------------------------------------------------
+// relaxed device-scope loads / stores for decoupled look-back
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+int compute_layout(const gs_problem *pb, Layout *L);
+void count_launches(int n);
+int device_sm_count();
+int check_launch();
+
+template <class T>
+__host__ __device__ inline T *ws_ptr(void *ws, size_t off) {
+    return reinterpret_cast<T *>(static_cast<char *>(ws) + off);
+}
+
+}  // namespace gs

@@ -1,0 +1,102 @@
+// gs_kernels.cuh -- kernel argument blocks and host launchers of libgs.
+#pragma once
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+// ---------------- projection ----------------
+struct ProjArgs {
+    const ViewEntry *views;
+    const gs_camera *cams;
+    const float *means, *log_scales, *quats, *opacities, *colors;
+    float4 *proj;               // [P,3] float4
+    uint32_t *touched;          // [P]
+    int W, H;
+    float tw, th, Tx, Ty;
+    float near_plane, dil, sigmas;
+};
+
+struct ProjBwdArgs {
+    const ViewEntry *views;
+    const gs_camera *cams;
+    const float *means, *log_scales, *quats;
+    const uint32_t *touched_incl;   // inclusive prefix sums (nonzero increment = visible)
+    const float4 *g2d;              // [P,3] float4
+    float *g_means, *g_ls, *g_quats, *g_op, *g_col;
+    float *pose_part;               // [chunks, 8]
+    int W, H;
+    float dil;
+};
+
+void launch_project(const Layout &L, const ProjArgs &a, cudaStream_t s);
+void launch_project_bwd(const Layout &L, const ProjBwdArgs &a, cudaStream_t s);
+void launch_pose_reduce(const Layout &L, const ViewEntry *views, const float *part, float *out, cudaStream_t s);
+
+// ---------------- binning ----------------
+struct BinArgs {
+    const ViewEntry *views;
+    uint32_t *touched;                 // in: counts; out: inclusive prefix sums
+    unsigned long long *scan_state;
+    const float4 *proj;
+    float4 *g2d;
+    uint64_t *keys[2];
+    uint32_t *vals[2];
+    uint32_t *hist;                    // [kMaxPasses][256]
+    uint32_t *sort_state;              // [passes][sort_parts][256]
+    uint32_t *ranges;                  // [G,2]
+    DevStatus *st;
+    int V, Tx, Ty, passes;
+    float tw, th;
+    long long P, cap, sort_parts, max_chunks, G;
+    int fault_scan_part;               // -1 normally; >= 0: that scan partition never publishes
+    unsigned long long spin_limit;
+};
+
+// runs scan -> emit -> histogram -> digit scan -> onesweep passes -> ranges; the sorted keys end
+// in keys[passes % 2]
+int run_bin_sort(const BinArgs &a, cudaStream_t s);
+// scan alone (used by the bounded-wait test entry point)
+int run_scan_only(const BinArgs &a, cudaStream_t s);
+
+// ---------------- rendering ----------------
+struct FwdArgs {
+    const float4 *proj;
+    const uint32_t *vals;
+    const uint32_t *ranges;
+    float *rgb, *depth, *alpha, *finalT;
+    int32_t *last;
+    DevStatus *st;
+    int W, H, Tx, Ty;
+    long long G, P;
+    float amax, amin, tmin, bg0, bg1, bg2;
+};
+
+struct BwdArgs {
+    const float4 *proj;
+    const uint32_t *vals;
+    const uint32_t *ranges;
+    const float *finalT;
+    const int32_t *last;
+    const float *d_rgb, *d_depth, *d_alpha;
+    float *g2d;                        // [P,12]
+    DevStatus *st;
+    int W, H, Tx, Ty;
+    long long G, P;
+    float amax, amin, bg0, bg1, bg2;
+};
+
+int launch_render_fwd(int tw, int th, const FwdArgs &a, cudaStream_t s);
+int launch_render_bwd(int tw, int th, const BwdArgs &a, cudaStream_t s);
+
+// ---------------- losses / optimiser ----------------
+int launch_loss_l1(int V, int W, int H, const float *rgb, const float *rgb_t, const float *depth,
+                   const float *depth_t, float w_rgb, float w_depth, float *d_rgb, float *d_depth, double *loss,
+                   cudaStream_t s);
+size_t ssim_scratch_bytes(int V, int W, int H);
+int launch_loss_l1_ssim(int V, int W, int H, const float *rgb, const float *rgb_t, float w_l1, float w_ssim,
+                        float *d_rgb, double *loss, void *scratch, cudaStream_t s);
+int launch_adam(long long n, const gs_adam_state &st, const gs_grads &g, const float lr[5], int zero_grads,
+                cudaStream_t s);
+
+}  // namespace gs

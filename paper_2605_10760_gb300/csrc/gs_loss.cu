@@ -1,0 +1,310 @@
+// gs_loss.cu -- loss terms of the mapping / refinement objectives and the Adam step.
+//
+// L1 (Eq. 4's photometric and depth terms): one pass per pixel producing the loss and its
+// gradient.  SSIM (Eq. 23's structural term): two tiled passes with an 11-tap separable Gaussian
+// (sigma 1.5, zero padding) in shared memory:
+//   pass 1 blurs x, y, x^2, y^2, xy and writes the per-pixel derivatives of the SSIM map with
+//          respect to mu_x, E[x^2] and E[xy];
+//   pass 2 blurs those three maps (the adjoint of a zero-padded symmetric blur is the same blur)
+//          and combines dSSIM/dx = blur(dS/dmu_x) + 2 x blur(dS/dE[x^2]) + y blur(dS/dE[xy]),
+//          fused with the L1 gradient.
+// Adam: one thread per Gaussian, 14 parameters, bias-corrected, opacity through its logit.
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+__device__ __forceinline__ float sgnf(float d) { return d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f); }
+
+__device__ __forceinline__ void block_add_double(double v, double *out) {
+    __shared__ double s_part[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_part[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double w = lane < (int)(blockDim.x >> 5) ? s_part[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0 && w != 0.0) atomicAdd(out, w);
+    }
+}
+
+__global__ void k_l1(long long HWn, int V, const float *rgb, const float *rgb_t, const float *depth,
+                     const float *depth_t, float sc_rgb, float sc_d, float *d_rgb, float *d_depth, double *loss) {
+    double acc = 0.0;
+    const long long total = (long long)V * HWn;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long v = i / HWn, p = i - v * HWn;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long idx = (3 * v + c) * HWn + p;
+            const float d = rgb[idx] - rgb_t[idx];
+            acc += (double)fabsf(d) * sc_rgb;
+            d_rgb[idx] = sgnf(d) * sc_rgb;
+        }
+        if (depth && d_depth) {
+            const float d = depth[i] - depth_t[i];
+            acc += (double)fabsf(d) * sc_d;
+            d_depth[i] = sgnf(d) * sc_d;
+        }
+    }
+    block_add_double(acc, loss);
+}
+
+int launch_loss_l1(int V, int W, int H, const float *rgb, const float *rgb_t, const float *depth,
+                   const float *depth_t, float w_rgb, float w_depth, float *d_rgb, float *d_depth, double *loss,
+                   cudaStream_t s) {
+    const long long HWn = (long long)W * H;
+    const float sc_rgb = (float)((double)w_rgb / (3.0 * V * HWn));
+    const float sc_d = (float)((double)w_depth / ((double)V * HWn));
+    const bool use_d = depth && depth_t && d_depth && w_depth != 0.f;
+    const long long total = (long long)V * HWn;
+    const int grid = (int)std::min<long long>((total + 255) / 256, (long long)device_sm_count() * 8);
+    if (cudaMemsetAsync(loss, 0, sizeof(double), s) != cudaSuccess) return GS_ERR_CUDA;
+    k_l1<<<std::max(grid, 1), 256, 0, s>>>(HWn, V, rgb, rgb_t, use_d ? depth : nullptr, depth_t, sc_rgb, sc_d,
+                                             d_rgb, use_d ? d_depth : nullptr, loss);
+    count_launches(1);
+    return check_launch();
+}
+
+// ------------------------------------------------------------------------------------------
+// SSIM
+// ------------------------------------------------------------------------------------------
+constexpr int kSB = 32;            // output tile
+constexpr int kR = 5;              // window radius
+constexpr int kSI = kSB + 2 * kR;  // input tile with halo
+constexpr float kC1 = 0.0001f, kC2 = 0.0009f;
+
+struct SsimTaps {
+    float w[11];
+};
+
+static SsimTaps make_taps() {
+    SsimTaps t;
+    double g[11], sum = 0.0;
+    for (int k = 0; k < 11; ++k) {
+        const double d = k - 5;
+        g[k] = exp(-d * d / (2.0 * 1.5 * 1.5));
+        sum += g[k];
+    }
+    for (int k = 0; k < 11; ++k) t.w[k] = (float)(g[k] / sum);
+    return t;
+}
+
+// pass 1: per image plane (view * 3 + channel), tile (bx, by)
+__global__ void __launch_bounds__(256) k_ssim1(int W, int H, const float *x, const float *y, SsimTaps tp,
+                                               float inv_n, float *dmu, float *dexx, float *dexy, double *ssim_sum) {
+    __shared__ float sx[kSI][kSI], sy[kSI][kSI];
+    __shared__ float h[5][kSI][kSB];
+    const long long plane = blockIdx.z;
+    const float *xp = x + plane * (long long)W * H;
+    const float *yp = y + plane * (long long)W * H;
+    const int x0 = blockIdx.x * kSB - kR, y0 = blockIdx.y * kSB - kR;
+    for (int i = threadIdx.x; i < kSI * kSI; i += 256) {
+        const int r = i / kSI, c = i % kSI;
+        const int gx = x0 + c, gy = y0 + r;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        sx[r][c] = in ? xp[(long long)gy * W + gx] : 0.f;
+        sy[r][c] = in ? yp[(long long)gy * W + gx] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSI * kSB; i += 256) {
+        const int r = i / kSB, c = i % kSB;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const float xv = sx[r][c + k], yv = sy[r][c + k], w = tp.w[k];
+            a0 += w * xv;
+            a1 += w * yv;
+            a2 += w * xv * xv;
+            a3 += w * yv * yv;
+            a4 += w * xv * yv;
+        }
+        h[0][r][c] = a0; h[1][r][c] = a1; h[2][r][c] = a2; h[3][r][c] = a3; h[4][r][c] = a4;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < kSB * kSB; i += 256) {
+        const int r = i / kSB, c = i % kSB;
+        const int gx = blockIdx.x * kSB + c, gy = blockIdx.y * kSB + r;
+        if (gx >= W || gy >= H) continue;
+        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const float w = tp.w[k];
+            mx += w * h[0][r + k][c];
+            my += w * h[1][r + k][c];
+            exx += w * h[2][r + k][c];
+            eyy += w * h[3][r + k][c];
+            exy += w * h[4][r + k][c];
+        }
+        const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
+        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
+        const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+        const float iB = 1.f / (B1 * B2);
+        const float S = A1 * A2 * iB;
+        acc += (double)S;
+        const long long o = plane * (long long)W * H + (long long)gy * W + gx;
+        dmu[o] = inv_n * ((2.f * my * A2 - 2.f * my * A1) * iB - S * (2.f * mx / B1 - 2.f * mx / B2));
+        dexx[o] = inv_n * (-S / B2);
+        dexy[o] = inv_n * (2.f * A1 * iB);
+    }
+    block_add_double(acc, ssim_sum);
+}
+
+// pass 2: blur the three derivative maps and combine with the L1 gradient
+__global__ void __launch_bounds__(256) k_ssim2(int W, int H, const float *x, const float *y, SsimTaps tp,
+                                               const float *dmu, const float *dexx, const float *dexy, float l1_scale,
+                                               float w_ssim, float *d_rgb) {
+    __shared__ float s[3][kSI][kSI];
+    __shared__ float h[3][kSI][kSB];
+    const long long plane = blockIdx.z;
+    const long long off = plane * (long long)W * H;
+    const int x0 = blockIdx.x * kSB - kR, y0 = blockIdx.y * kSB - kR;
+    for (int i = threadIdx.x; i < kSI * kSI; i += 256) {
+        const int r = i / kSI, c = i % kSI;
+        const int gx = x0 + c, gy = y0 + r;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const long long o = off + (long long)gy * W + gx;
+        s[0][r][c] = in ? dmu[o] : 0.f;
+        s[1][r][c] = in ? dexx[o] : 0.f;
+        s[2][r][c] = in ? dexy[o] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSI * kSB; i += 256) {
+        const int r = i / kSB, c = i % kSB;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const float w = tp.w[k];
+            a0 += w * s[0][r][c + k];
+            a1 += w * s[1][r][c + k];
+            a2 += w * s[2][r][c + k];
+        }
+        h[0][r][c] = a0; h[1][r][c] = a1; h[2][r][c] = a2;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSB * kSB; i += 256) {
+        const int r = i / kSB, c = i % kSB;
+        const int gx = blockIdx.x * kSB + c, gy = blockIdx.y * kSB + r;
+        if (gx >= W || gy >= H) continue;
+        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const float w = tp.w[k];
+            b0 += w * h[0][r + k][c];
+            b1 += w * h[1][r + k][c];
+            b2 += w * h[2][r + k][c];
+        }
+        const long long o = off + (long long)gy * W + gx;
+        const float xv = x[o], yv = y[o];
+        const float gs = b0 + 2.f * xv * b1 + yv * b2;
+        d_rgb[o] = l1_scale * sgnf(xv - yv) - w_ssim * gs;
+    }
+}
+
+__global__ void k_l1_sum(long long n, const float *x, const float *y, double *out) {
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += (double)fabsf(x[i] - y[i]);
+    block_add_double(acc, out);
+}
+
+__global__ void k_ssim_finish(double *scratch_sums, float w_l1, float w_ssim, double inv_n, double *loss) {
+    // scratch_sums[0] = sum |x - y|, scratch_sums[1] = sum of the SSIM map
+    *loss = w_l1 * scratch_sums[0] * inv_n + w_ssim * (1.0 - scratch_sums[1] * inv_n);
+}
+
+size_t ssim_scratch_bytes(int V, int W, int H) {
+    return 256 + 3 * sizeof(float) * (size_t)V * 3 * W * H;
+}
+
+int launch_loss_l1_ssim(int V, int W, int H, const float *rgb, const float *rgb_t, float w_l1, float w_ssim,
+                        float *d_rgb, double *loss, void *scratch, cudaStream_t s) {
+    static const SsimTaps taps = make_taps();
+    const long long plane = (long long)W * H, n = 3LL * V * plane;
+    double *sums = reinterpret_cast<double *>(scratch);
+    float *dmu = reinterpret_cast<float *>(static_cast<char *>(scratch) + 256);
+    float *dexx = dmu + n, *dexy = dexx + n;
+    if (cudaMemsetAsync(sums, 0, 2 * sizeof(double), s) != cudaSuccess) return GS_ERR_CUDA;
+    dim3 grid((W + kSB - 1) / kSB, (H + kSB - 1) / kSB, 3 * V);
+    const float inv_n = (float)(1.0 / (double)n);
+    k_l1_sum<<<device_sm_count() * 4, 256, 0, s>>>(n, rgb, rgb_t, sums);
+    k_ssim1<<<grid, 256, 0, s>>>(W, H, rgb, rgb_t, taps, inv_n, dmu, dexx, dexy, sums + 1);
+    k_ssim2<<<grid, 256, 0, s>>>(W, H, rgb, rgb_t, taps, dmu, dexx, dexy, w_l1 * inv_n, w_ssim, d_rgb);
+    k_ssim_finish<<<1, 1, 0, s>>>(sums, w_l1, w_ssim, 1.0 / (double)n, loss);
+    count_launches(4);
+    return check_launch();
+}
+
+// ------------------------------------------------------------------------------------------
+// Adam
+// ------------------------------------------------------------------------------------------
+struct AdamArgs {
+    long long n;
+    float *p[5];            // means, log_scales, quats, opacity_logits, colors
+    float *opac;            // activated opacity (rewritten)
+    float *g[5];            // grads: means, log_scales, quats, opacities (w.r.t. o), colors
+    float *m, *v;
+    const int32_t *step;
+    float lr[5];
+    int zero;
+};
+
+__global__ void __launch_bounds__(256) k_adam(AdamArgs a) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int t = *a.step + 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-15f;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    const int dims[5] = {3, 3, 4, 1, 3};
+    int col = 0;
+    float *m = a.m + 14 * i, *v = a.v + 14 * i;
+#pragma unroll
+    for (int grp = 0; grp < 5; ++grp) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            if (d >= dims[grp]) break;
+            const long long idx = i * dims[grp] + d;
+            float gr = a.g[grp][idx];
+            if (grp == 3) {
+                const float o = a.opac[i];
+                gr *= o * (1.f - o);
+            }
+            const float mm = b1 * m[col] + (1.f - b1) * gr;
+            const float vv = b2 * v[col] + (1.f - b2) * gr * gr;
+            m[col] = mm;
+            v[col] = vv;
+            const float upd = a.lr[grp] * (mm / c1) / (sqrtf(vv / c2) + eps);
+            const float np = a.p[grp][idx] - upd;
+            a.p[grp][idx] = np;
+            if (grp == 3) a.opac[i] = 1.f / (1.f + __expf(-np));
+            if (a.zero) a.g[grp][idx] = 0.f;
+            ++col;
+        }
+    }
+}
+
+__global__ void k_step_inc(int32_t *step) { *step += 1; }
+
+int launch_adam(long long n, const gs_adam_state &st, const gs_grads &g, const float lr[5], int zero_grads,
+                cudaStream_t s) {
+    AdamArgs a;
+    a.n = n;
+    a.p[0] = st.means; a.p[1] = st.log_scales; a.p[2] = st.quats; a.p[3] = st.opacity_logits; a.p[4] = st.colors;
+    a.opac = st.opacities;
+    a.g[0] = g.means; a.g[1] = g.log_scales; a.g[2] = g.quats; a.g[3] = g.opacities; a.g[4] = g.colors;
+    a.m = st.m;
+    a.v = st.v;
+    a.step = st.step;
+    for (int k = 0; k < 5; ++k) a.lr[k] = lr[k];
+    a.zero = zero_grads;
+    if (n > 0) {
+        k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
+        count_launches(1);
+    }
+    k_step_inc<<<1, 1, 0, s>>>(st.step);
+    count_launches(1);
+    return check_launch();
+}
+
+}  // namespace gs

@@ -1,0 +1,243 @@
+// gs_project.cu -- EWA projection of (view, Gaussian) pairs and its adjoint.
+//
+// Forward: the FP32 decision chain of gs_internal.cuh; one thread per pair, grid (chunk, view).
+// Backward: the chain rule through the same projection in FP32 value arithmetic, accumulating
+// dL/d(mean, log-scale, quaternion, opacity, colour) with atomics (several views of one scene add
+// into the same Gaussian) and the per-view SE(3) pose gradient as one partial sum per block.
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+
+
+__global__ void __launch_bounds__(kChunk) k_project(ProjArgs a) {
+    const int v = blockIdx.y;
+    __shared__ ViewEntry s_ve;
+    __shared__ float s_cam[16];
+    if (threadIdx.x == 0) s_ve = a.views[v];
+    if (threadIdx.x < 16) s_cam[threadIdx.x] = reinterpret_cast<const float *>(a.cams + v)[threadIdx.x];
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (i >= s_ve.count) return;
+    const long long gi = s_ve.gauss_begin + i;
+    const long long f = s_ve.pair_off + i;
+    const float *mu = a.means + 3 * gi;
+    const float *ls = a.log_scales + 3 * gi;
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(a.quats) + gi);
+    SpecProj o = spec_project(s_cam, s_cam + 9, s_cam[12], s_cam[13], s_cam[14], s_cam[15], a.W, a.H, a.tw, a.th,
+                              a.Tx, a.Ty, a.near_plane, a.dil, a.sigmas, __ldg(mu), __ldg(mu + 1), __ldg(mu + 2),
+                              __ldg(ls), __ldg(ls + 1), __ldg(ls + 2), q.x, q.y, q.z, q.w);
+    uint32_t cnt = 0;
+    if (o.visible) {
+        cnt = (uint32_t)((o.x1 - o.x0) * (o.y1 - o.y0));
+        const float *col = a.colors + 3 * gi;
+        float4 *rec = a.proj + 3 * f;
+        rec[0] = make_float4(o.mx, o.my, o.A, o.B);
+        rec[1] = make_float4(o.C, __ldg(a.opacities + gi), o.z, o.rf);
+        rec[2] = make_float4(__ldg(col), __ldg(col + 1), __ldg(col + 2), 0.0f);
+    }
+    a.touched[f] = cnt;
+}
+
+void launch_project(const Layout &L, const ProjArgs &a, cudaStream_t s) {
+    dim3 grid((unsigned)L.max_chunks, (unsigned)L.V);
+    k_project<<<grid, kChunk, 0, s>>>(a);
+    count_launches(1);
+}
+
+// ------------------------------------------------------------------------------------------
+// projection adjoint
+// ------------------------------------------------------------------------------------------
+
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__global__ void __launch_bounds__(kChunk) k_project_bwd(ProjBwdArgs a) {
+    const int v = blockIdx.y;
+    __shared__ ViewEntry s_ve;
+    __shared__ float s_cam[16];
+    __shared__ float s_red[kChunk / 32][6];
+    if (threadIdx.x == 0) s_ve = a.views[v];
+    if (threadIdx.x < 16) s_cam[threadIdx.x] = reinterpret_cast<const float *>(a.cams + v)[threadIdx.x];
+    __syncthreads();
+    if ((long long)blockIdx.x * kChunk >= s_ve.count) return;   // whole block idle: no partial slot
+    const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
+    float pose[6] = {0, 0, 0, 0, 0, 0};
+    if (i < s_ve.count) {
+        const long long f = s_ve.pair_off + i;
+        const uint32_t prev = f > 0 ? a.touched_incl[f - 1] : 0u;
+        if (a.touched_incl[f] != prev) {
+            const long long gi = s_ve.gauss_begin + i;
+            const float *R = s_cam, *t = s_cam + 9;
+            const float fx = s_cam[12], fy = s_cam[13];
+            const float4 g0 = a.g2d[3 * f], g1 = a.g2d[3 * f + 1], g2 = a.g2d[3 * f + 2];
+            const float gmx = g0.x, gmy = g0.y, gA = g0.z, gB = g0.w, gC = g1.x, gop = g1.y, gz = g1.z;
+            atomicAdd(a.g_op + gi, gop);
+            atomicAdd(a.g_col + 3 * gi, g1.w);
+            atomicAdd(a.g_col + 3 * gi + 1, g2.x);
+            atomicAdd(a.g_col + 3 * gi + 2, g2.y);
+            const float m0 = a.means[3 * gi], m1 = a.means[3 * gi + 1], m2 = a.means[3 * gi + 2];
+            // camera-space centre exactly as in the forward decision chain
+            const float xc = fp::fma(R[0], m0, fp::fma(R[1], m1, fp::fma(R[2], m2, t[0])));
+            const float yc = fp::fma(R[3], m0, fp::fma(R[4], m1, fp::fma(R[5], m2, t[1])));
+            const float zc = fp::fma(R[6], m0, fp::fma(R[7], m1, fp::fma(R[8], m2, t[2])));
+            const float4 qr = reinterpret_cast<const float4 *>(a.quats)[gi];
+            const float qn = sqrtf(qr.x * qr.x + qr.y * qr.y + qr.z * qr.z + qr.w * qr.w);
+            const float w = qr.x / qn, x = qr.y / qn, y = qr.z / qn, z = qr.w / qn;
+            float Rq[9];
+            Rq[0] = 1.f - 2.f * (y * y + z * z); Rq[1] = 2.f * (x * y - w * z);       Rq[2] = 2.f * (x * z + w * y);
+            Rq[3] = 2.f * (x * y + w * z);       Rq[4] = 1.f - 2.f * (x * x + z * z); Rq[5] = 2.f * (y * z - w * x);
+            Rq[6] = 2.f * (x * z - w * y);       Rq[7] = 2.f * (y * z + w * x);       Rq[8] = 1.f - 2.f * (x * x + y * y);
+            float s[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s[k] = spec_expf(a.log_scales[3 * gi + k]);
+            float M[9];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) M[3 * j + k] = Rq[3 * j + k] * s[k];
+            // clamp decisions as in the forward decision chain
+            const float izs = fp::div(1.0f, zc);
+            const float limx = fp::div(fp::mul(0.65f, (float)a.W), fx);
+            const float limy = fp::div(fp::mul(0.65f, (float)a.H), fy);
+            const float uxs = fp::mul(xc, izs), uys = fp::mul(yc, izs);
+            const bool clx = (uxs < -limx) || (uxs > limx);
+            const bool cly = (uys < -limy) || (uys > limy);
+            const float iz = 1.0f / zc;
+            const float ux = xc * iz, uy = yc * iz;
+            const float tx = fminf(limx, fmaxf(-limx, ux)), ty = fminf(limy, fmaxf(-limy, uy));
+            const float J00 = fx * iz, J11 = fy * iz, J02 = -fx * tx * iz, J12 = -fy * ty * iz;
+            float Wm[6];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                Wm[k] = J00 * R[k] + J02 * R[6 + k];
+                Wm[3 + k] = J11 * R[3 + k] + J12 * R[6 + k];
+            }
+            float U[6];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    U[3 * r + k] = Wm[3 * r] * M[k] + Wm[3 * r + 1] * M[3 + k] + Wm[3 * r + 2] * M[6 + k];
+            float gpc0 = gmx * fx * iz, gpc1 = gmy * fy * iz;
+            float gpc2 = -(gmx * fx * xc + gmy * fy * yc) * iz * iz + gz;
+            // conic adjoint
+            const float a_ = U[0] * U[0] + U[1] * U[1] + U[2] * U[2] + a.dil;
+            const float b_ = U[0] * U[3] + U[1] * U[4] + U[2] * U[5];
+            const float c_ = U[3] * U[3] + U[4] * U[4] + U[5] * U[5] + a.dil;
+            const float det = a_ * c_ - b_ * b_;
+            const float id = 1.0f / det, id2 = id * id;
+            const float ga = gA * (-c_ * c_ * id2) + gB * (b_ * c_ * id2) + gC * (id - a_ * c_ * id2);
+            const float gb = gA * (2.f * b_ * c_ * id2) + gB * (-id - 2.f * b_ * b_ * id2) + gC * (2.f * a_ * b_ * id2);
+            const float gc = gA * (id - a_ * c_ * id2) + gB * (a_ * b_ * id2) + gC * (-a_ * a_ * id2);
+            float gU[6];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gU[k] = 2.f * ga * U[k] + gb * U[3 + k];
+                gU[3 + k] = 2.f * gc * U[3 + k] + gb * U[k];
+            }
+            float gW[6], gM[9];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                gW[j] = gU[0] * M[3 * j] + gU[1] * M[3 * j + 1] + gU[2] * M[3 * j + 2];
+                gW[3 + j] = gU[3] * M[3 * j] + gU[4] * M[3 * j + 1] + gU[5] * M[3 * j + 2];
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gM[3 * j + k] = Wm[j] * gU[k] + Wm[3 + j] * gU[3 + k];
+            float gRq[9], gs[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    gRq[3 * j + k] = gM[3 * j + k] * s[k];
+                    gs[k] += gM[3 * j + k] * Rq[3 * j + k];
+                }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) atomicAdd(a.g_ls + 3 * gi + k, gs[k] * s[k]);
+            float gq[4];
+            gq[0] = 2.f * (-z * gRq[1] + y * gRq[2] + z * gRq[3] - x * gRq[5] - y * gRq[6] + x * gRq[7]);
+            gq[1] = 2.f * (y * gRq[1] + z * gRq[2] + y * gRq[3] - w * gRq[5] + z * gRq[6] + w * gRq[7]) -
+                    4.f * x * (gRq[4] + gRq[8]);
+            gq[2] = 2.f * (x * gRq[1] + w * gRq[2] + x * gRq[3] + z * gRq[5] - w * gRq[6] + z * gRq[7]) -
+                    4.f * y * (gRq[0] + gRq[8]);
+            gq[3] = 2.f * (-w * gRq[1] + x * gRq[2] + w * gRq[3] + y * gRq[5] + x * gRq[6] + y * gRq[7]) -
+                    4.f * z * (gRq[0] + gRq[4]);
+            const float dq = gq[0] * w + gq[1] * x + gq[2] * y + gq[3] * z;
+            const float qv[4] = {w, x, y, z};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(a.g_quats + 4 * gi + k, (gq[k] - qv[k] * dq) / qn);
+            float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f, gR[9];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gJ00 += gW[k] * R[k];
+                gJ02 += gW[k] * R[6 + k];
+                gJ11 += gW[3 + k] * R[3 + k];
+                gJ12 += gW[3 + k] * R[6 + k];
+                gR[k] = gW[k] * J00;
+                gR[3 + k] = gW[3 + k] * J11;
+                gR[6 + k] = gW[k] * J02 + gW[3 + k] * J12;
+            }
+            gpc2 += -(gJ00 * fx + gJ11 * fy) * iz * iz + (gJ02 * fx * tx + gJ12 * fy * ty) * iz * iz;
+            const float gtx = -gJ02 * fx * iz, gty = -gJ12 * fy * iz;
+            if (!clx) { gpc0 += gtx * iz; gpc2 -= gtx * xc * iz * iz; }
+            if (!cly) { gpc1 += gty * iz; gpc2 -= gty * yc * iz * iz; }
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                atomicAdd(a.g_means + 3 * gi + k, R[k] * gpc0 + R[3 + k] * gpc1 + R[6 + k] * gpc2);
+            // pose: d p_c = rho + phi x p_c, d R = [phi]x R
+            float N[9];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) N[3 * j + m] = gR[3 * j] * R[3 * m] + gR[3 * j + 1] * R[3 * m + 1] +
+                                                          gR[3 * j + 2] * R[3 * m + 2];
+            pose[0] = gpc0; pose[1] = gpc1; pose[2] = gpc2;
+            pose[3] = yc * gpc2 - zc * gpc1 + N[7] - N[5];
+            pose[4] = zc * gpc0 - xc * gpc2 + N[2] - N[6];
+            pose[5] = xc * gpc1 - yc * gpc0 + N[3] - N[1];
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        float r = warp_sum(pose[k]);
+        if (lane == 0) s_red[warp][k] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float r = 0.f;
+#pragma unroll
+        for (int wi = 0; wi < kChunk / 32; ++wi) r += s_red[wi][threadIdx.x];
+        a.pose_part[(s_ve.chunk_off + blockIdx.x) * 8 + threadIdx.x] = r;
+    }
+}
+
+void launch_project_bwd(const Layout &L, const ProjBwdArgs &a, cudaStream_t s) {
+    dim3 grid((unsigned)L.max_chunks, (unsigned)L.V);
+    k_project_bwd<<<grid, kChunk, 0, s>>>(a);
+    count_launches(1);
+}
+
+// deterministic per-view sum of the pose partials: one warp per (view, component)
+__global__ void k_pose_reduce(const ViewEntry *views, const float *pose_part, float *out) {
+    const int v = blockIdx.x, k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const ViewEntry ve = views[v];
+    const long long chunks = (ve.count + kChunk - 1) / kChunk;
+    float acc = 0.f;
+    for (long long c = lane; c < chunks; c += 32) acc += pose_part[(ve.chunk_off + c) * 8 + k];
+    acc = warp_sum(acc);
+    if (lane == 0) out[6 * v + k] = acc;
+}
+
+void launch_pose_reduce(const Layout &L, const ViewEntry *views, const float *part, float *out, cudaStream_t s) {
+    k_pose_reduce<<<L.V, 6 * 32, 0, s>>>(views, part, out);
+    count_launches(1);
+}
+
+}  // namespace gs

@@ -1,0 +1,449 @@
+// gs_sort.cu -- tile binning: key emission and a hand-written onesweep LSD radix sort.
+//
+// Pipeline (all stream-ordered, no host synchronisation, K read from device memory):
+//   1. k_scan      single-pass inclusive scan of tiles_touched with decoupled look-back;
+//                  the last partition writes K and flags K > capacity;
+//   2. k_emit      one key (global tile << 32 | float bits of depth) per touched tile, tiles in
+//                  row-major order, value = flattened (view, Gaussian) index; also clears that
+//                  pair's backward accumulator;
+//   3. k_hist      digit histograms of every 8-bit pass in one read of the keys;
+//   4. k_digit_scan exclusive scan of each pass's 256 digit counts;
+//   5. k_onesweep  one launch per pass: each CTA claims the next partition of 4096 keys, ranks them
+//                  stably (warp match_any + per-warp digit counters), publishes its digit counts,
+//                  looks back over its predecessors' counts (bounded spins) and scatters through
+//                  shared memory so that each digit run is written contiguously;
+//   6. k_ranges    [start, end) of every global tile in the sorted keys.
+// Depth is positive (z > near > 0), so its float bit pattern orders like its value, and the sort is
+// stable, so equal keys keep the emission order (ascending flattened index).
+#include "gs_kernels.cuh"
+
+namespace gs {
+
+constexpr unsigned long long kFlagAgg64 = 1ull << 62, kFlagInc64 = 2ull << 62, kVal64 = (1ull << 62) - 1;
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kVal = (1u << 30) - 1;
+
+// ------------------------------------------------------------------------------------------
+// 1. inclusive scan with decoupled look-back
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanThreads) k_scan(BinArgs a) {
+    __shared__ uint32_t s_part;
+    __shared__ unsigned long long s_wsum[kScanThreads / 32];
+    __shared__ unsigned long long s_prefix;
+    const long long nparts = (a.P + kScanTile - 1) / kScanTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_part = atomicAdd(&a.st->ctr[kCtrScan], 1u);
+        __syncthreads();
+        const long long part = s_part;
+        if (part >= nparts) break;
+        const long long base = part * kScanTile + (long long)threadIdx.x * kScanIPT;
+        uint32_t x[kScanIPT];
+        if (base + kScanIPT <= a.P) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.touched + base);
+#pragma unroll
+            for (int q = 0; q < kScanIPT / 4; ++q) {
+                uint4 u = src[q];
+                x[4 * q] = u.x; x[4 * q + 1] = u.y; x[4 * q + 2] = u.z; x[4 * q + 3] = u.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanIPT; ++k) x[k] = (base + k < a.P) ? a.touched[base + k] : 0u;
+        }
+        unsigned long long tsum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanIPT; ++k) tsum += x[k];
+        // block exclusive scan of the per-thread sums
+        unsigned long long incl = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = lane < kScanThreads / 32 ? s_wsum[lane] : 0ull;
+            unsigned long long wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            if (lane < kScanThreads / 32) s_wsum[lane] = wi - w;   // exclusive warp offsets
+            if (lane == kScanThreads / 32 - 1) {
+                // lane 7 holds the block total: publish and look back
+                const unsigned long long total = wi;
+                unsigned long long prefix = 0;
+                const bool silent = (part == a.fault_scan_part);
+                if (part == 0) {
+                    if (!silent) st_relaxed_u64(a.scan_state, kFlagInc64 | total);
+                } else {
+                    if (!silent) st_relaxed_u64(a.scan_state + part, kFlagAgg64 | total);
+                    long long j = part - 1;
+                    unsigned long long spins = 0;
+                    bool timed_out = false;
+                    while (j >= 0) {
+                        unsigned long long w2 = ld_relaxed_u64(a.scan_state + j);
+                        unsigned long long fl = w2 & ~kVal64;
+                        if (fl == 0) {
+                            if (++spins > a.spin_limit) { timed_out = true; break; }
+                            __nanosleep(100);
+                            continue;
+                        }
+                        prefix += w2 & kVal64;
+                        if (fl == kFlagInc64) break;
+                        --j;
+                    }
+                    if (timed_out) record_error(a.st, GS_ERR_TIMEOUT, 1);
+                    if (!silent) st_relaxed_u64(a.scan_state + part, kFlagInc64 | ((prefix + total) & kVal64));
+                }
+                s_prefix = prefix;
+                if (part == nparts - 1) {
+                    const unsigned long long K = prefix + total;
+                    a.st->num_keys = K;
+                    if (K > (unsigned long long)a.cap) {
+                        a.st->required_keys = K;
+                        record_error(a.st, GS_ERR_CAPACITY, 2);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        unsigned long long run = s_prefix + s_wsum[warp] + (incl - tsum);
+        uint32_t y[kScanIPT];
+#pragma unroll
+        for (int k = 0; k < kScanIPT; ++k) {
+            run += x[k];
+            y[k] = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
+        }
+        if (base + kScanIPT <= a.P) {
+            uint4 *dst = reinterpret_cast<uint4 *>(a.touched + base);
+#pragma unroll
+            for (int q = 0; q < kScanIPT / 4; ++q) dst[q] = make_uint4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanIPT; ++k)
+                if (base + k < a.P) a.touched[base + k] = y[k];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// 2. key emission
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kChunk) k_emit(BinArgs a) {
+    const int v = blockIdx.y;
+    __shared__ ViewEntry s_ve;
+    if (threadIdx.x == 0) s_ve = a.views[v];
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
+    if (i >= s_ve.count) return;
+    const long long f = s_ve.pair_off + i;
+    const uint32_t end = a.touched[f];
+    const uint32_t start = f > 0 ? a.touched[f - 1] : 0u;
+    if (end == start) return;
+    const float4 r0 = a.proj[3 * f], r1 = a.proj[3 * f + 1];
+    int x0, x1, y0, y1;
+    spec_rect(r0.x, r0.y, r1.w, a.tw, a.th, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
+    const unsigned long long zbits = __float_as_uint(r1.z);
+    const unsigned long long gbase = (unsigned long long)v * a.Tx * a.Ty;
+    unsigned long long k = start;
+    uint64_t *keys = a.keys[0];
+    uint32_t *vals = a.vals[0];
+    for (int ty = y0; ty < y1; ++ty)
+        for (int tx = x0; tx < x1; ++tx) {
+            if (k < (unsigned long long)a.cap) {
+                keys[k] = ((gbase + (unsigned long long)(ty * a.Tx + tx)) << 32) | zbits;
+                vals[k] = (uint32_t)f;
+            }
+            ++k;
+        }
+    if (k != end) record_error(a.st, GS_ERR_DEVICE_FAULT, 3);
+    float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    a.g2d[3 * f] = z4;
+    a.g2d[3 * f + 1] = z4;
+    a.g2d[3 * f + 2] = z4;
+}
+
+// ------------------------------------------------------------------------------------------
+// 3./4. digit histograms
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_hist(BinArgs a) {
+    __shared__ uint32_t sh[kMaxPasses][256];
+    for (int i = threadIdx.x; i < kMaxPasses * 256; i += 256) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    const unsigned long long K = min(a.st->num_keys, (unsigned long long)a.cap);
+    const uint64_t *keys = a.keys[0];
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * 256; i0 < K; i0 += (unsigned long long)gridDim.x * 256) {
+        const unsigned long long i = i0 + threadIdx.x;
+        const bool valid = i < K;
+        const uint64_t key = valid ? keys[i] : 0ull;
+        for (int p = 0; p < a.passes; ++p) {
+            const uint32_t d = valid ? (uint32_t)((key >> (8 * p)) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&sh[p][d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.passes * 256; i += 256) {
+        uint32_t c = (&sh[0][0])[i];
+        if (c) atomicAdd(a.hist + i, c);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_digit_scan(uint32_t *hist) {
+    __shared__ uint32_t s_w[8];
+    uint32_t *h = hist + blockIdx.x * 256;
+    const uint32_t x = h[threadIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    uint32_t off = 0;
+    for (int w = 0; w < warp; ++w) off += s_w[w];
+    h[threadIdx.x] = off + incl - x;
+}
+
+// ------------------------------------------------------------------------------------------
+// 5. onesweep pass
+// ------------------------------------------------------------------------------------------
+struct SweepArgs {
+    const uint64_t *kin;
+    const uint32_t *vin;
+    uint64_t *kout;
+    uint32_t *vout;
+    const uint32_t *digit_off;   // [256] exclusive global digit starts of this pass
+    uint32_t *state;             // [parts][256]
+    uint32_t *ctr;
+    DevStatus *st;
+    long long cap;
+    int shift;
+    unsigned long long spin_limit;
+};
+
+constexpr int kSweepWarps = kSortThreads / 32;
+constexpr size_t kSweepDynSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(uint32_t));
+
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
+    extern __shared__ __align__(16) unsigned char sw_smem[];
+    uint64_t *s_keys = reinterpret_cast<uint64_t *>(sw_smem);
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kSortTile);
+    __shared__ uint32_t s_wcnt[kSweepWarps][256];
+    __shared__ uint32_t s_tstart[256];
+    __shared__ uint32_t s_gbase[256];
+    __shared__ uint32_t s_wsum[kSweepWarps];
+    __shared__ uint32_t s_part;
+    __shared__ int s_bad;
+    const unsigned long long Kll = min(a.st->num_keys, (unsigned long long)a.cap);
+    const uint32_t K = (uint32_t)Kll;
+    const uint32_t nparts = (K + kSortTile - 1) / kSortTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = lanemask_lt();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_part = atomicAdd(a.ctr, 1u);
+            s_bad = 0;
+        }
+#pragma unroll
+        for (int w = 0; w < kSweepWarps; ++w) s_wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        const uint32_t part = s_part;
+        if (part >= nparts) break;
+        const uint32_t base = part * kSortTile;
+        const uint32_t tile_n = min((uint32_t)kSortTile, K - base);
+        uint64_t k[kSortIPT];
+        uint32_t val[kSortIPT];
+        uint32_t rk[kSortIPT];
+#pragma unroll
+        for (int r = 0; r < kSortIPT; ++r) {
+            const uint32_t li = warp * (kSortIPT * 32) + r * 32 + lane;
+            const bool valid = li < tile_n;
+            k[r] = valid ? a.kin[base + li] : 0ull;
+            val[r] = valid ? a.vin[base + li] : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kSortIPT; ++r) {
+            const uint32_t li = warp * (kSortIPT * 32) + r * 32 + lane;
+            const uint32_t d = li < tile_n ? (uint32_t)((k[r] >> a.shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t c = d < 256u ? s_wcnt[warp][d] : 0u;
+            __syncwarp();
+            if (d < 256u && lane == __ffs(peers) - 1) s_wcnt[warp][d] = c + __popc(peers);
+            __syncwarp();
+            rk[r] = c + __popc(peers & lt_mask);
+        }
+        __syncthreads();
+        // thread d owns digit d
+        const int d = threadIdx.x;
+        uint32_t total = 0;
+#pragma unroll
+        for (int w = 0; w < kSweepWarps; ++w) {
+            const uint32_t c = s_wcnt[w][d];
+            s_wcnt[w][d] = total;
+            total += c;
+        }
+        uint32_t *my_state = a.state + (size_t)part * 256 + d;
+        if (part == 0) st_relaxed_u32(my_state, kFlagInc | total);
+        else st_relaxed_u32(my_state, kFlagAgg | total);
+        // exclusive scan of the digit totals inside the tile
+        uint32_t incl = total;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        // look back over the predecessors' counts of digit d
+        uint32_t excl = 0;
+        if (part > 0) {
+            int j = (int)part - 1;
+            unsigned long long spins = 0;
+            bool timed_out = false;
+            while (j >= 0) {
+                const uint32_t w = ld_relaxed_u32(a.state + (size_t)j * 256 + d);
+                const uint32_t fl = w & ~kVal;
+                if (fl == 0u) {
+                    if (++spins > a.spin_limit) { timed_out = true; break; }
+                    __nanosleep(64);
+                    continue;
+                }
+                excl += w & kVal;
+                if (fl == kFlagInc) break;
+                --j;
+            }
+            st_relaxed_u32(my_state, kFlagInc | ((excl + total) & kVal));
+            if (timed_out) {
+                s_bad = 1;
+                record_error(a.st, GS_ERR_TIMEOUT, 4);
+            }
+        }
+        __syncthreads();
+        uint32_t woff = 0;
+        for (int w = 0; w < warp; ++w) woff += s_wsum[w];
+        const uint32_t tstart = woff + incl - total;
+        s_tstart[d] = tstart;
+        s_gbase[d] = a.digit_off[d] + excl - tstart;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSortIPT; ++r) {
+            const uint32_t li = warp * (kSortIPT * 32) + r * 32 + lane;
+            if (li < tile_n) {
+                const uint32_t dd = (uint32_t)((k[r] >> a.shift) & 255u);
+                const uint32_t lp = s_tstart[dd] + s_wcnt[warp][dd] + rk[r];
+                s_keys[lp] = k[r];
+                s_vals[lp] = val[r];
+            }
+        }
+        __syncthreads();
+        if (!s_bad) {
+            for (uint32_t i = threadIdx.x; i < tile_n; i += kSortThreads) {
+                const uint64_t key = s_keys[i];
+                const uint32_t dd = (uint32_t)((key >> a.shift) & 255u);
+                const uint32_t gp = s_gbase[dd] + i;
+                if (gp < K) {
+                    a.kout[gp] = key;
+                    a.vout[gp] = s_vals[i];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// 6. tile ranges
+// ------------------------------------------------------------------------------------------
+__global__ void k_ranges(const uint64_t *keys, DevStatus *st, long long cap, long long G, uint32_t *ranges) {
+    const unsigned long long K = min(st->num_keys, (unsigned long long)cap);
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < K;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long g = keys[i] >> 32;
+        if (g >= (unsigned long long)G) {            // only after an earlier recorded failure
+            record_error(st, GS_ERR_DEVICE_FAULT, 5);
+            continue;
+        }
+        if (i == 0 || (keys[i - 1] >> 32) != g) ranges[2 * g] = (uint32_t)i;
+        if (i == K - 1 || (keys[i + 1] >> 32) != g) ranges[2 * g + 1] = (uint32_t)(i + 1);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// host driver
+// ------------------------------------------------------------------------------------------
+static int occupancy(const void *fn, int threads, size_t dyn) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, dyn) != cudaSuccess || b < 1) b = 1;
+    return b;
+}
+
+int run_scan_only(const BinArgs &a, cudaStream_t s) {
+    if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
+    const long long parts = (a.P + kScanTile - 1) / kScanTile;
+    if (parts > 0) {
+        if (cudaMemsetAsync(a.scan_state, 0, sizeof(unsigned long long) * parts, s) != cudaSuccess) return GS_ERR_CUDA;
+        static int occ = occupancy((const void *)k_scan, kScanThreads, 0);
+        long long grid = std::min<long long>(parts, (long long)device_sm_count() * occ);
+        k_scan<<<(unsigned)grid, kScanThreads, 0, s>>>(a);
+        count_launches(1);
+    } else {
+        // no pairs: K = 0
+        if (cudaMemsetAsync(&a.st->num_keys, 0, sizeof(unsigned long long), s) != cudaSuccess) return GS_ERR_CUDA;
+    }
+    return check_launch();
+}
+
+int run_bin_sort(const BinArgs &a, cudaStream_t s) {
+    // counters of the scan and of every sort pass
+    if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t) * (1 + kMaxPasses), s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    int rc = run_scan_only(a, s);
+    if (rc) return rc;
+    if (a.P > 0) {
+        dim3 grid((unsigned)a.max_chunks, (unsigned)a.V);
+        k_emit<<<grid, kChunk, 0, s>>>(a);
+        count_launches(1);
+    }
+    if (cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaMemsetAsync(a.sort_state, 0, sizeof(uint32_t) * 256 * (size_t)a.sort_parts * a.passes, s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    const int sms = device_sm_count();
+    k_hist<<<sms * 4, 256, 0, s>>>(a);
+    k_digit_scan<<<a.passes, 256, 0, s>>>(a.hist);
+    count_launches(2);
+    static bool attr = [] {
+        return cudaFuncSetAttribute((const void *)k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSweepDynSmem) == cudaSuccess;
+    }();
+    if (!attr) return GS_ERR_CUDA;
+    static int occ = occupancy((const void *)k_onesweep, kSortThreads, kSweepDynSmem);
+    const long long grid = std::max<long long>(1, std::min<long long>(a.sort_parts, (long long)sms * occ));
+    for (int p = 0; p < a.passes; ++p) {
+        SweepArgs sa;
+        sa.kin = a.keys[p & 1];
+        sa.vin = a.vals[p & 1];
+        sa.kout = a.keys[(p + 1) & 1];
+        sa.vout = a.vals[(p + 1) & 1];
+        sa.digit_off = a.hist + 256 * p;
+        sa.state = a.sort_state + (size_t)256 * a.sort_parts * p;
+        sa.ctr = &a.st->ctr[kCtrSort0 + p];
+        sa.st = a.st;
+        sa.cap = a.cap;
+        sa.shift = 8 * p;
+        sa.spin_limit = a.spin_limit;
+        k_onesweep<<<(unsigned)grid, kSortThreads, kSweepDynSmem, s>>>(sa);
+        count_launches(1);
+    }
+    if (cudaMemsetAsync(a.ranges, 0, sizeof(uint32_t) * 2 * (size_t)a.G, s) != cudaSuccess) return GS_ERR_CUDA;
+    k_ranges<<<sms * 8, 256, 0, s>>>(a.keys[a.passes & 1], a.st, a.cap, a.G, a.ranges);
+    count_launches(1);
+    return check_launch();
+}
+
+}  // namespace gs

@@ -1,0 +1,313 @@
+"""Torch-facing binding of libgs: a problem object owning the workspace, one function per C-ABI
+call, and a torch.autograd.Function.  Every computation runs in libgs; this module only passes
+device pointers (torch tensors are used as device memory and for the current CUDA stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def default_params(**over) -> L.gs_params:
+    p = L.gs_params()
+    L.load().gs_default_params(C.byref(p))
+    for k, v in over.items():
+        if k == "bg":
+            for i in range(3):
+                p.bg[i] = float(v[i])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+@dataclass
+class Gaussians:
+    """Device float32 tensors: means [N,3], log_scales [N,3], quats [N,4] (w,x,y,z), opacities [N],
+    colors [N,3]."""
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacities: torch.Tensor
+    colors: torch.Tensor
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda"):
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=torch.float32)
+        return cls(t(scene.means), t(scene.log_scales), t(scene.quats), t(scene.opacities), t(scene.colors))
+
+    def struct(self) -> L.gs_gaussians:
+        s = L.gs_gaussians()
+        s.means, s.log_scales, s.quats = self.means.data_ptr(), self.log_scales.data_ptr(), self.quats.data_ptr()
+        s.opacities, s.colors = self.opacities.data_ptr(), self.colors.data_ptr()
+        return s
+
+    @property
+    def n(self):
+        return int(self.means.shape[0])
+
+
+def zeros_like_grads(g: Gaussians) -> Gaussians:
+    return Gaussians(*[torch.zeros_like(getattr(g, k)) for k in ("means", "log_scales", "quats", "opacities",
+                                                                  "colors")])
+
+
+def cameras_tensor(cameras, device="cuda") -> torch.Tensor:
+    """[V,16] float32 device tensor (R row-major, t, fx, fy, cx, cy) from scenes.Camera objects."""
+    rows = np.stack([c.as_row() for c in cameras]).astype(np.float32)
+    return torch.from_numpy(rows).to(device)
+
+
+class Problem:
+    """V views of one or more scenes plus the libgs workspace that serves them.
+
+    view_gauss_begin / view_gauss_count: first row and row count of each view's scene in the
+    concatenated Gaussian arrays.  cameras: [V,16] device tensor.  The workspace is one device
+    byte tensor; key_capacity bounds the number of duplicated (tile, depth) keys.
+    """
+
+    def __init__(self, view_gauss_begin, view_gauss_count, num_gaussians, width, height, cameras=None,
+                 params: L.gs_params | None = None, key_capacity: int | None = None, device="cuda"):
+        self.lib = L.load()
+        self.device = torch.device(device)
+        self.vb = np.ascontiguousarray(view_gauss_begin, dtype=np.int64)
+        self.vc = np.ascontiguousarray(view_gauss_count, dtype=np.int64)
+        self.V = int(self.vb.shape[0])
+        self.W, self.H = int(width), int(height)
+        self.N = int(num_gaussians)
+        self.P = int(self.vc.sum())
+        self.params = params if params is not None else default_params()
+        if key_capacity is None:
+            key_capacity = int(min((1 << 30) - 1, max(1 << 20, 4 * self.P)))
+        self.cap = int(key_capacity)
+        self.cameras = cameras
+        self._pb = L.gs_problem()
+        self._sync_struct()
+        self._alloc()
+
+    # -- struct / workspace ------------------------------------------------------------------
+    def _sync_struct(self):
+        pb = self._pb
+        pb.num_views, pb.width, pb.height = self.V, self.W, self.H
+        pb.num_gaussians = self.N
+        pb.view_gauss_begin = self.vb.ctypes.data_as(C.POINTER(C.c_int64))
+        pb.view_gauss_count = self.vc.ctypes.data_as(C.POINTER(C.c_int64))
+        pb.cameras = None if self.cameras is None else self.cameras.data_ptr()
+        pb.key_capacity = self.cap
+        pb.params = self.params
+
+    @property
+    def pb(self):
+        self._sync_struct()
+        return C.byref(self._pb)
+
+    def _alloc(self):
+        n = C.c_size_t()
+        L.check(self.lib.gs_workspace_size(self.pb, C.byref(n)), "gs_workspace_size")
+        self.ws_bytes = int(n.value)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        L.check(self.lib.gs_workspace_init(self.pb, _ptr(self.ws), _stream()), "gs_workspace_init")
+
+    def set_capacity(self, cap: int):
+        self.cap = int(min((1 << 30) - 1, cap))
+        self._alloc()
+
+    def set_cameras(self, cameras: torch.Tensor):
+        assert cameras.dtype == torch.float32 and cameras.is_contiguous() and cameras.shape == (self.V, 16)
+        self.cameras = cameras
+
+    @property
+    def tiles(self):
+        tw, th = self.params.tile_w, self.params.tile_h
+        return -(-self.W // tw), -(-self.H // th)
+
+    # -- inspection ----------------------------------------------------------------------------
+    def workspace(self) -> dict:
+        """Tensors viewing the workspace (proj, tiles_touched, sorted keys/vals, ranges, grad2d, K)."""
+        v = L.gs_ws_view()
+        L.check(self.lib.gs_workspace_view(self.pb, _ptr(self.ws), C.byref(v)), "gs_workspace_view")
+        base = self.ws.data_ptr()
+
+        def sl(ptr, count, dtype):
+            off = ptr - base
+            nbytes = count * torch.empty((), dtype=dtype).element_size()
+            return self.ws[off:off + nbytes].view(dtype)
+
+        P, G = int(v.num_pairs), int(v.num_tiles)
+        return dict(proj=sl(v.proj, 12 * P, torch.float32).view(P, 12),
+                    tiles_touched=sl(v.tiles_touched, P, torch.int32),
+                    sorted_keys=sl(v.sorted_keys, self.cap, torch.int64),
+                    sorted_vals=sl(v.sorted_vals, self.cap, torch.int32),
+                    tile_ranges=sl(v.tile_ranges, 2 * G, torch.int32).view(G, 2),
+                    grad2d=sl(v.grad2d, 12 * P, torch.float32).view(P, 12),
+                    num_keys=sl(v.num_keys, 2, torch.int32), passes=int(v.sort_passes))
+
+    def check_status(self):
+        req = C.c_int64()
+        rc = self.lib.gs_check_status(self.pb, _ptr(self.ws), _stream(), C.byref(req))
+        return rc, int(req.value)
+
+    def stats(self) -> dict:
+        s = L.gs_stats()
+        L.check(self.lib.gs_read_stats(self.pb, _ptr(self.ws), _stream(), C.byref(s)), "gs_read_stats")
+        return dict(num_keys=int(s.num_keys), fwd_pairs=int(s.fwd_pairs), bwd_pairs=int(s.bwd_pairs))
+
+    # -- stages ----------------------------------------------------------------------------
+    def project(self, g: Gaussians):
+        gs_ = g.struct()
+        L.check(self.lib.gs_project(self.pb, C.byref(gs_), _ptr(self.ws), _stream()), "gs_project")
+
+    def bin_sort(self):
+        L.check(self.lib.gs_bin_sort(self.pb, _ptr(self.ws), _stream()), "gs_bin_sort")
+
+    def alloc_image(self) -> dict:
+        V, H, W = self.V, self.H, self.W
+        d = self.device
+        return dict(rgb=torch.empty(V, 3, H, W, device=d), depth=torch.empty(V, H, W, device=d),
+                    alpha=torch.empty(V, H, W, device=d), final_T=torch.empty(V, H, W, device=d),
+                    last_idx=torch.empty(V, H, W, dtype=torch.int32, device=d))
+
+    def render_fwd(self, img: dict | None = None) -> dict:
+        img = img if img is not None else self.alloc_image()
+        s = L.gs_image(_ptr(img.get("rgb")), _ptr(img.get("depth")), _ptr(img.get("alpha")),
+                       _ptr(img["final_T"]), _ptr(img["last_idx"]))
+        L.check(self.lib.gs_render_fwd(self.pb, _ptr(self.ws), C.byref(s), _stream()), "gs_render_fwd")
+        return img
+
+    def render_bwd(self, g: Gaussians, img: dict, d_rgb=None, d_depth=None, d_alpha=None,
+                   grads: Gaussians | None = None) -> Gaussians:
+        grads = grads if grads is not None else zeros_like_grads(g)
+        gs_ = g.struct()
+        fi = L.gs_image(None, None, None, _ptr(img["final_T"]), _ptr(img["last_idx"]))
+        di = L.gs_image_grad(_ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha))
+        go = L.gs_grads(*[getattr(grads, k).data_ptr() for k in ("means", "log_scales", "quats", "opacities",
+                                                                   "colors")])
+        L.check(self.lib.gs_render_bwd(self.pb, C.byref(gs_), _ptr(self.ws), C.byref(fi), C.byref(di), C.byref(go),
+                                       _stream()), "gs_render_bwd")
+        return grads
+
+    def pose_grad(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = out if out is not None else torch.empty(self.V, 6, device=self.device)
+        L.check(self.lib.gs_pose_grad(self.pb, _ptr(self.ws), _ptr(out), _stream()), "gs_pose_grad")
+        return out
+
+    def forward_checked(self, g: Gaussians, img: dict | None = None, max_retries: int = 2) -> dict:
+        """project + bin_sort + render_fwd, growing the key capacity when K exceeds it (syncs)."""
+        for _ in range(max_retries + 1):
+            self.project(g)
+            self.bin_sort()
+            rc, req = self.check_status()
+            if rc == L.GS_ERR_CAPACITY:
+                self.set_capacity(int(req * 1.25) + 1024)
+                continue
+            L.check(rc, "gs_bin_sort")
+            return self.render_fwd(img)
+        raise L.GsError(L.GS_ERR_CAPACITY, "forward_checked")
+
+
+# ------------------------------------------------------------------------------------------
+# losses and optimiser
+# ------------------------------------------------------------------------------------------
+
+def loss_l1(rgb, rgb_t, depth=None, depth_t=None, w_rgb=1.0, w_depth=0.0, d_rgb=None, d_depth=None, loss=None):
+    """Returns (loss [1] float64 device, d_rgb, d_depth)."""
+    V, _, H, W = rgb.shape
+    d_rgb = d_rgb if d_rgb is not None else torch.empty_like(rgb)
+    if w_depth != 0.0 and d_depth is None:
+        d_depth = torch.empty_like(depth)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float64, device=rgb.device)
+    L.check(L.load().gs_loss_l1(V, W, H, _ptr(rgb), _ptr(rgb_t), _ptr(depth), _ptr(depth_t), float(w_rgb),
+                                float(w_depth), _ptr(d_rgb), _ptr(d_depth) if w_depth != 0.0 else None, _ptr(loss),
+                                _stream()), "gs_loss_l1")
+    return loss, d_rgb, d_depth
+
+
+def ssim_scratch(V, H, W, device="cuda") -> torch.Tensor:
+    n = L.load().gs_ssim_scratch_size(V, W, H)
+    return torch.empty(int(n), dtype=torch.uint8, device=device)
+
+
+def loss_l1_ssim(rgb, rgb_t, w_l1=0.8, w_ssim=0.2, d_rgb=None, loss=None, scratch=None):
+    V, _, H, W = rgb.shape
+    d_rgb = d_rgb if d_rgb is not None else torch.empty_like(rgb)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float64, device=rgb.device)
+    scratch = scratch if scratch is not None else ssim_scratch(V, H, W, rgb.device)
+    L.check(L.load().gs_loss_l1_ssim(V, W, H, _ptr(rgb), _ptr(rgb_t), float(w_l1), float(w_ssim), _ptr(d_rgb),
+                                     _ptr(loss), _ptr(scratch), _stream()), "gs_loss_l1_ssim")
+    return loss, d_rgb
+
+
+class AdamState:
+    """Adam moments and parameter views for the in-kernel optimiser step.  Opacity is optimised
+    through its logit; `g.opacities` is rewritten as sigmoid(logit) by every step."""
+
+    def __init__(self, g: Gaussians, lr=(1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3)):
+        self.g = g
+        o = g.opacities.clamp(1e-6, 1 - 1e-6)
+        self.logits = torch.log(o / (1 - o)).contiguous()
+        n = g.n
+        self.m = torch.zeros(n, 14, device=g.means.device)
+        self.v = torch.zeros(n, 14, device=g.means.device)
+        self.step = torch.zeros(1, dtype=torch.int32, device=g.means.device)
+        self.lr = (C.c_float * 5)(*lr)
+
+    def apply(self, grads: Gaussians, zero_grads=True):
+        st = L.gs_adam_state(self.g.means.data_ptr(), self.g.log_scales.data_ptr(), self.g.quats.data_ptr(),
+                             self.logits.data_ptr(), self.g.opacities.data_ptr(), self.g.colors.data_ptr(),
+                             self.m.data_ptr(), self.v.data_ptr(), self.step.data_ptr())
+        go = L.gs_grads(*[getattr(grads, k).data_ptr() for k in ("means", "log_scales", "quats", "opacities",
+                                                                   "colors")])
+        L.check(L.load().gs_adam_step(self.g.n, C.byref(st), C.byref(go), self.lr, int(bool(zero_grads)),
+                                      _stream()), "gs_adam_step")
+
+
+# ------------------------------------------------------------------------------------------
+# autograd
+# ------------------------------------------------------------------------------------------
+
+class _Rasterize(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacities, colors, pose_delta, problem):
+        g = Gaussians(means.contiguous(), log_scales.contiguous(), quats.contiguous(), opacities.contiguous(),
+                      colors.contiguous())
+        img = problem.forward_checked(g)
+        ctx.problem = problem
+        ctx.g = g
+        ctx.save_for_backward(img["final_T"], img["last_idx"])
+        ctx.mark_non_differentiable(img["final_T"])
+        return img["rgb"], img["depth"], img["alpha"]
+
+    @staticmethod
+    def backward(ctx, d_rgb, d_depth, d_alpha):
+        final_T, last_idx = ctx.saved_tensors
+        pb = ctx.problem
+        img = dict(final_T=final_T, last_idx=last_idx)
+        c = lambda t: None if t is None else t.contiguous()
+        grads = pb.render_bwd(ctx.g, img, c(d_rgb), c(d_depth), c(d_alpha))
+        pose = pb.pose_grad()
+        return grads.means, grads.log_scales, grads.quats, grads.opacities, grads.colors, pose, None
+
+
+def rasterize(means, log_scales, quats, opacities, colors, problem: Problem, pose_delta=None):
+    """Render (rgb [V,3,H,W], depth [V,H,W], alpha [V,H,W]) of the problem's views.
+
+    Differentiable w.r.t. the five Gaussian tensors and w.r.t. `pose_delta` [V,6]: a zero-valued
+    leaf standing for the left perturbation Exp(xi) T of each world-to-camera pose (its gradient
+    is dL/dxi at xi = 0; the forward renders at the problem's cameras)."""
+    if pose_delta is None:
+        pose_delta = torch.zeros(problem.V, 6, device=means.device, requires_grad=False)
+    return _Rasterize.apply(means, log_scales, quats, opacities, colors, pose_delta, problem)

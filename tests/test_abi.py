@@ -1,0 +1,91 @@
+"""CPU-side checks of the C ABI: the library loads, exports every function include/gs.h declares,
+and validates arguments on the host (no GPU call is made by any of these)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2605_10760_gb300 import _lib as L
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return L.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = L.header_symbols()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_reports_sm103a(lib):
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    assert lib.gs_version(C.byref(a), C.byref(b), C.byref(c)) == 0
+    assert c.value == 1030
+
+
+def _problem(V=1, W=1200, H=680, N=500_000, cap=1 << 21, **par):
+    p = L.gs_params()
+    lib = L.load()
+    lib.gs_default_params(C.byref(p))
+    for k, v in par.items():
+        setattr(p, k, v)
+    vb = np.zeros(V, np.int64)
+    vc = np.full(V, N, np.int64)
+    pb = L.gs_problem()
+    pb.num_views, pb.width, pb.height, pb.num_gaussians = V, W, H, N
+    pb.view_gauss_begin = vb.ctypes.data_as(C.POINTER(C.c_int64))
+    pb.view_gauss_count = vc.ctypes.data_as(C.POINTER(C.c_int64))
+    pb.key_capacity = cap
+    pb.params = p
+    pb._keep = (vb, vc)
+    return pb
+
+
+def test_default_params(lib):
+    p = L.gs_params()
+    lib.gs_default_params(C.byref(p))
+    assert (p.tile_w, p.tile_h) == (16, 16)
+    assert p.alpha_max == np.float32(0.99) and p.alpha_min == np.float32(1) / np.float32(255)
+    assert p.t_min == np.float32(1e-4) and p.dilation == np.float32(0.3)
+
+
+def test_workspace_size_and_validation(lib):
+    n = C.c_size_t()
+    pb = _problem()
+    assert lib.gs_workspace_size(C.byref(pb), C.byref(n)) == 0
+    # proj + grad2d (48 B each per pair) + keys (2 x 12 B per key) dominate
+    assert 500_000 * 96 + (1 << 21) * 24 < n.value < 500_000 * 140 + (1 << 21) * 40
+    bad = [_problem(V=0), _problem(W=0), _problem(cap=0), _problem(cap=1 << 30), _problem(tile_w=8),
+           _problem(alpha_max=1.5), _problem(t_min=0.0), _problem(near_plane=0.0)]
+    for b in bad:
+        assert lib.gs_workspace_size(C.byref(b), C.byref(n)) == L.GS_ERR_INVALID_ARG
+    pb = _problem(V=2)
+    vc = np.array([10, 20], np.int64)
+    vb = np.array([0, 500_000 - 5], np.int64)       # second view overruns the arrays
+    pb.view_gauss_begin = vb.ctypes.data_as(C.POINTER(C.c_int64))
+    pb.view_gauss_count = vc.ctypes.data_as(C.POINTER(C.c_int64))
+    assert lib.gs_workspace_size(C.byref(pb), C.byref(n)) == L.GS_ERR_INVALID_ARG
+
+
+def test_sort_pass_count_follows_tile_bits(lib):
+    for V, passes in ((1, 6), (64, 7)):
+        pb = _problem(V=V, N=1000)
+        v = L.gs_ws_view()
+        # a fake 256-aligned non-null address: gs_workspace_view only does pointer arithmetic
+        assert lib.gs_workspace_view(C.byref(pb), C.c_void_p(1 << 20), C.byref(v)) == 0
+        assert v.sort_passes == passes and v.num_tiles == V * 75 * 43
+
+
+def test_calls_reject_bad_arguments_without_launching(lib):
+    pb = _problem()
+    assert lib.gs_project(C.byref(pb), None, C.c_void_p(1 << 20), None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_bin_sort(C.byref(pb), C.c_void_p(3), None) == L.GS_ERR_INVALID_ARG   # misaligned
+    assert lib.gs_render_fwd(C.byref(pb), C.c_void_p(1 << 20), None, None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_pose_grad(C.byref(pb), C.c_void_p(1 << 20), None, None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_loss_l1(0, 10, 10, None, None, None, None, 1.0, 0.0, None, None, None, None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_adam_step(-1, None, None, None, 0, None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_debug_scan_timeout(None, 10, 0, None, None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_error_string(L.GS_ERR_CAPACITY) == b"key capacity exceeded"

@@ -1,0 +1,78 @@
+"""GPU parity of the loss kernels and the in-kernel Adam step against the FP64 oracles."""
+import numpy as np
+import pytest
+
+from helpers import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import losses as OL  # noqa: E402
+from paper_2605_10760_gb300 import scenes as S  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_10760_gb300 import raster
+    raster.L.load()
+    return raster
+
+
+@pytest.mark.parametrize("V,H,W", [(1, 37, 53), (2, 68, 120), (1, 680, 1200)])
+def test_l1_rgb_depth(R, V, H, W):
+    rng = np.random.default_rng(V * H)
+    x = rng.uniform(0, 1, (V, 3, H, W)).astype(np.float32)
+    y = rng.uniform(0, 1, (V, 3, H, W)).astype(np.float32)
+    d = rng.uniform(0, 5, (V, H, W)).astype(np.float32)
+    dt = rng.uniform(0, 5, (V, H, W)).astype(np.float32)
+    x[0, 0, 0, :5] = y[0, 0, 0, :5]              # sign(0) = 0
+    t = lambda a: torch.from_numpy(a).cuda()
+    loss, d_rgb, d_d = R.loss_l1(t(x), t(y), t(d), t(dt), 1.0, 0.1)
+    L, gr, gd = OL.mapping_l1_loss(x, y, d, dt, 1.0, 0.1)
+    assert abs(loss.item() - L) <= 1e-6 * abs(L)
+    np.testing.assert_allclose(d_rgb.cpu().numpy(), gr, rtol=1e-6, atol=0)
+    np.testing.assert_allclose(d_d.cpu().numpy(), gd, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("V,H,W", [(1, 40, 45), (2, 70, 97), (1, 680, 1200)])
+def test_l1_ssim(R, V, H, W):
+    rng = np.random.default_rng(H + W)
+    y = S.smooth_image(W, H, seed=3)[None].repeat(V, 0)
+    x = np.clip(y + rng.normal(0, 0.05, y.shape), 0, 1).astype(np.float32)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    loss, d_rgb = R.loss_l1_ssim(t(x), t(y), 0.8, 0.2)
+    L, g = OL.l1_ssim_loss(x, y, 0.8, 0.2)
+    assert abs(loss.item() - L) <= 1e-5 * abs(L)
+    assert rel_l2(d_rgb.cpu().numpy(), g) <= 1e-4
+
+
+def test_adam_step_matches_oracle(R):
+    rng = np.random.default_rng(5)
+    n = 3000
+    sc = S.random_cloud(n, seed=9)
+    g = R.Gaussians.from_scene(sc)
+    st = R.AdamState(g, lr=(1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3))
+    ref = {k: getattr(sc, k).astype(np.float64) for k in ("means", "log_scales", "quats", "colors")}
+    o = sc.opacities.astype(np.float64)
+    ref["logit"] = np.log(o / (1 - o))
+    mom = {k: (np.zeros_like(v), np.zeros_like(v)) for k, v in ref.items()}
+    lrs = {"means": 1.6e-4, "log_scales": 5e-3, "quats": 1e-3, "logit": 5e-2, "colors": 2.5e-3}
+    for step in range(1, 4):
+        grads = {k: rng.normal(0, 1, getattr(sc, k).shape).astype(np.float32)
+                 for k in ("means", "log_scales", "quats", "opacities", "colors")}
+        gg = R.Gaussians(*[torch.from_numpy(grads[k]).cuda() for k in ("means", "log_scales", "quats", "opacities",
+                                                                          "colors")])
+        o_now = 1 / (1 + np.exp(-ref["logit"]))
+        st.apply(gg, zero_grads=True)
+        assert float(gg.means.abs().sum()) == 0.0
+        for k in ("means", "log_scales", "quats", "colors", "logit"):
+            gk = grads["opacities"].astype(np.float64) * o_now * (1 - o_now) if k == "logit" else grads[k]
+            ref[k], m, v = OL.adam_step(ref[k], gk.astype(np.float64), *mom[k], step, lrs[k])
+            mom[k] = (m, v)
+    for k in ("means", "log_scales", "quats", "colors"):
+        np.testing.assert_allclose(getattr(g, k).cpu().numpy(), ref[k], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(st.logits.cpu().numpy(), ref["logit"], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(g.opacities.cpu().numpy(), 1 / (1 + np.exp(-ref["logit"])), rtol=1e-5, atol=1e-6)
+    assert int(st.step.item()) == 3
