@@ -54,6 +54,7 @@ enum {
     GS_ERR_TIMEOUT = -3,       /* a bounded device-side wait gave up                      */
     GS_ERR_CUDA = -4,          /* a CUDA launch or runtime call failed                     */
     GS_ERR_DEVICE_FAULT = -5,  /* a device-side consistency check failed                   */
+    GS_ERR_TOO_LARGE = -6,     /* input larger than a fixed-size static scratch area holds   */
 };
 
 #define GS_MAX_VIEWS 1024
@@ -214,6 +215,29 @@ int gs_loss_l1(int32_t views, int32_t width, int32_t height, const float *rgb, c
 size_t gs_ssim_scratch_size(int32_t views, int32_t width, int32_t height);
 int gs_loss_l1_ssim(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
                     float w_l1, float w_ssim, float *d_rgb, double *loss, void *scratch, void *stream);
+
+/* The same loss and gradient as gs_loss_l1_ssim, for callers that cannot allocate device memory:
+ * for example a tracking / mapping front-end that claims a fixed device-memory budget at start-up
+ * and may not grow it afterwards, or a host program whose allocator belongs to another component
+ * (cudaMalloc can also stall every stream on the device, which a real-time loop cannot afford).
+ * The paper has no counterpart to this entry point; it exists only for such callers.
+ *
+ * Instead of a caller-provided scratch buffer it uses a fixed area inside the library: a static
+ * device array of 256 + 3 * 4 * GS_SSIM_NOALLOC_MAX_PLANE bytes (about 12 MiB) that every GPU which
+ * loads libgs keeps until the process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The caller still provides rgb, rgb_t, d_rgb and loss as for gs_loss_l1_ssim.
+ *  - Limit: width * height <= GS_SSIM_NOALLOC_MAX_PLANE pixels per image plane (any number of
+ *    views); larger images are rejected with GS_ERR_TOO_LARGE before anything is launched.
+ *  - Set-up: the first call on a device (with that device current) looks up the device address of
+ *    the static area; make that first call before any stream capture on that device.
+ *  - Sharing: every call on a device uses the same area and leaves its last contents there; the
+ *    call clears what must start at zero itself.  Calls whose executions overlap on the GPU (on
+ *    different streams, or from different host threads) race on the area and give wrong results:
+ *    order them on one stream or synchronise between them.
+ * The image planes are processed one after another, so it launches 2 kernels per plane plus 2. */
+#define GS_SSIM_NOALLOC_MAX_PLANE (1 << 20)
+int gs_loss_l1_ssim_noalloc(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
+                            float w_l1, float w_ssim, float *d_rgb, double *loss, void *stream);
 
 /* One bias-corrected Adam step over all Gaussian parameters (beta1 0.9, beta2 0.999, eps 1e-15)
  * with per-group learning rates lr[5] = {means, log_scales, quats, opacity_logits, colors}.

@@ -17,6 +17,8 @@ GS_ERR_CAPACITY = -2
 GS_ERR_TIMEOUT = -3
 GS_ERR_CUDA = -4
 GS_ERR_DEVICE_FAULT = -5
+GS_ERR_TOO_LARGE = -6
+GS_SSIM_NOALLOC_MAX_PLANE = 1 << 20
 GS_MAX_VIEWS = 1024
 
 
@@ -100,6 +102,8 @@ _SIGS = {
                              _P]),
     "gs_ssim_scratch_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
     "gs_loss_l1_ssim": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_float, C.c_float, _P, _P, _P, _P]),
+    "gs_loss_l1_ssim_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_float, C.c_float, _P, _P,
+                                          _P]),
     "gs_adam_step": (C.c_int, [C.c_int64, C.POINTER(gs_adam_state), C.POINTER(gs_grads),
                                C.POINTER(C.c_float), C.c_int32, _P]),
 "gs_grads_zero": (C.c_int, [C.c_int64, C.POINTER(gs_grads), _P]),

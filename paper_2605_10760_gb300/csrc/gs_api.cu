@@ -111,6 +111,7 @@ const char *gs_error_string(int code) {
     case GS_ERR_TIMEOUT: return "bounded device wait timed out";
     case GS_ERR_CUDA: return "CUDA error";
     case GS_ERR_DEVICE_FAULT: return "device consistency check failed";
+    case GS_ERR_TOO_LARGE: return "input larger than the static scratch area holds";
     default: return "unknown error";
     }
 }
@@ -382,6 +383,14 @@ int gs_loss_l1_ssim(int32_t views, int32_t width, int32_t height, const float *r
         return GS_ERR_INVALID_ARG;
     return launch_loss_l1_ssim(views, width, height, rgb, rgb_t, w_l1, w_ssim, d_rgb, loss, scratch,
                                (cudaStream_t)stream);
+}
+
+int gs_loss_l1_ssim_noalloc(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
+                            float w_l1, float w_ssim, float *d_rgb, double *loss, void *stream) {
+    if (views < 1 || width < 1 || height < 1 || !rgb || !rgb_t || !d_rgb || !loss) return GS_ERR_INVALID_ARG;
+    if ((long long)width * height > GS_SSIM_NOALLOC_MAX_PLANE) return GS_ERR_TOO_LARGE;
+    return launch_loss_l1_ssim_noalloc(views, width, height, rgb, rgb_t, w_l1, w_ssim, d_rgb, loss,
+                                       (cudaStream_t)stream);
 }
 
 int gs_adam_step(int64_t n, const gs_adam_state *st, const gs_grads *grads, const float lr[5], int32_t zero_grads,

@@ -96,6 +96,8 @@ int launch_loss_l1(int V, int W, int H, const float *rgb, const float *rgb_t, co
 size_t ssim_scratch_bytes(int V, int W, int H);
 int launch_loss_l1_ssim(int V, int W, int H, const float *rgb, const float *rgb_t, float w_l1, float w_ssim,
                         float *d_rgb, double *loss, void *scratch, cudaStream_t s);
+int launch_loss_l1_ssim_noalloc(int V, int W, int H, const float *rgb, const float *rgb_t, float w_l1,
+                                float w_ssim, float *d_rgb, double *loss, cudaStream_t s);
 int launch_adam(long long n, const gs_adam_state &st, const gs_grads &g, const float lr[5], int zero_grads,
                 cudaStream_t s);
 

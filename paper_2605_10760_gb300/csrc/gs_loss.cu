@@ -9,6 +9,8 @@
 //          and combines dSSIM/dx = blur(dS/dmu_x) + 2 x blur(dS/dE[x^2]) + y blur(dS/dE[xy]),
 //          fused with the L1 gradient.
 // Adam: one thread per Gaussian, 14 parameters, bias-corrected, opacity through its logit.
+#include <mutex>
+
 #include "gs_kernels.cuh"
 
 namespace gs {
@@ -233,6 +235,60 @@ int launch_loss_l1_ssim(int V, int W, int H, const float *rgb, const float *rgb_
     k_ssim2<<<grid, 256, 0, s>>>(W, H, rgb, rgb_t, taps, dmu, dexx, dexy, w_l1 * inv_n, w_ssim, d_rgb);
     k_ssim_finish<<<1, 1, 0, s>>>(sums, w_l1, w_ssim, 1.0 / (double)n, loss);
     count_launches(4);
+    return check_launch();
+}
+
+// ------------------------------------------------------------------------------------------
+// The loss above without a caller-provided scratch buffer (for callers that cannot allocate).
+// Its scratch is this file's static device array: two running sums (256 bytes) followed by the
+// three derivative maps of ONE image plane; planes are processed one after another on the
+// caller's stream, each reusing the maps.
+// ------------------------------------------------------------------------------------------
+constexpr long long kNoallocMaxPlane = GS_SSIM_NOALLOC_MAX_PLANE;
+constexpr size_t kNoallocBytes = 256 + 3 * sizeof(float) * (size_t)kNoallocMaxPlane;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[64];
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.  (On the
+// host the symbol names a host-side stand-in, never the device memory itself.)
+static int noalloc_scratch(void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return GS_ERR_CUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return GS_OK;
+}
+
+int launch_loss_l1_ssim_noalloc(int V, int W, int H, const float *rgb, const float *rgb_t, float w_l1,
+                                float w_ssim, float *d_rgb, double *loss, cudaStream_t s) {
+    const long long plane = (long long)W * H, n = 3LL * V * plane;
+    if (plane > kNoallocMaxPlane) return GS_ERR_TOO_LARGE;
+    static const SsimTaps taps = make_taps();
+    void *base = nullptr;
+    int rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    double *sums = reinterpret_cast<double *>(base);
+    float *dmu = reinterpret_cast<float *>(static_cast<char *>(base) + 256);
+    float *dexx = dmu + plane, *dexy = dexx + plane;
+    if (cudaMemsetAsync(sums, 0, 2 * sizeof(double), s) != cudaSuccess) return GS_ERR_CUDA;
+    const float inv_n = (float)(1.0 / (double)n);
+    k_l1_sum<<<device_sm_count() * 4, 256, 0, s>>>(n, rgb, rgb_t, sums);
+    dim3 grid((W + kSB - 1) / kSB, (H + kSB - 1) / kSB, 1);
+    for (long long p = 0; p < 3LL * V; ++p) {
+        const long long off = p * plane;
+        k_ssim1<<<grid, 256, 0, s>>>(W, H, rgb + off, rgb_t + off, taps, inv_n, dmu, dexx, dexy, sums + 1);
+        k_ssim2<<<grid, 256, 0, s>>>(W, H, rgb + off, rgb_t + off, taps, dmu, dexx, dexy, w_l1 * inv_n, w_ssim,
+                                     d_rgb + off);
+    }
+    k_ssim_finish<<<1, 1, 0, s>>>(sums, w_l1, w_ssim, 1.0 / (double)n, loss);
+    count_launches((int)(2 + 6LL * V));
     return check_launch();
 }
 
