@@ -5,7 +5,7 @@
  *
  * What it computes.  MAGS-SLAM optimises each agent's Gaussian submap against a sliding window of
  * keyframes through "differentiably rendered RGB and depth" (Sec. III-A, mapping loss Eq. 4) and,
- * after fusion, refines Gaussians together with per-keyframe pose deltas (Sec. III-D, refinement
+ * after fusion, refines Gaussians together with per-keyframe pose deltas (Sec. III-C, refinement
  * loss Eq. 23).  Keyframe poses are world-to-camera (Sec. III-B, lifting relation Eq. 15); a
  * Gaussian carries a centre, per-axis scale, rotation, opacity and colour, with covariance
  * R diag(s)^2 R^T (Eq. 19).  The paper cites the 3DGS rasterizer for the rendering itself and fixes
@@ -83,7 +83,7 @@ typedef struct gs_params {
 
 /* One rendering problem: V views of one or more scenes (agents' submaps) whose Gaussians are
  * concatenated row-wise.  View v renders rows [view_gauss_begin[v], +view_gauss_count[v]).
- * All views share width x height (the agents share one camera model, Sec. V). */
+ * All views share width x height (the agents share one camera model, Sec. VI). */
 typedef struct gs_problem {
     int32_t num_views;                 /* V, 1..GS_MAX_VIEWS                          */
     int32_t width, height;             /* image size, pixels                          */
@@ -196,7 +196,7 @@ int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const g
                   const gs_image_grad *dimg, const gs_grads *grads, void *stream);
 
 /* dL/d xi for each view, xi = (rho, phi) the left perturbation T <- Exp(xi) T of the world-to-camera
- * pose at xi = 0 (the per-keyframe pose delta of Sec. III-D): pose_grad [V,6] (rho_x, rho_y, rho_z,
+ * pose at xi = 0 (the per-keyframe pose delta of Sec. III-C): pose_grad [V,6] (rho_x, rho_y, rho_z,
  * phi_x, phi_y, phi_z), overwritten, summed deterministically from the partials of gs_render_bwd. */
 int gs_pose_grad(const gs_problem *pb, void *ws, float *pose_grad, void *stream);
 

@@ -1,9 +1,9 @@
 /*
  * gs_oracle.c -- plain, slow CPU oracle of the differentiable 3D Gaussian Splatting rasterizer
  * that MAGS-SLAM's per-agent mapping (Sec. III-A, Eq. 4) and joint pose-Gaussian refinement
- * (Sec. III-D, Eq. 23) optimise through: render RGB, depth and alpha of anisotropic Gaussians
+ * (Sec. III-C, Eq. 23) optimise through: render RGB, depth and alpha of anisotropic Gaussians
  * seen from world-to-camera poses (Sec. III-B, Eq. 15), and differentiate a loss with respect to
- * every Gaussian parameter and to a per-view pose delta (Sec. III-D, "per-keyframe pose deltas").
+ * every Gaussian parameter and to a per-view pose delta (Sec. III-C, "per-keyframe pose deltas").
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links or calls this file; it exists so
  * that the CUDA library can be checked against an independent, obviously-correct computation.

@@ -8,7 +8,7 @@ TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU baseline).
   sigma 1.5 normalised to sum 1, zero padding of 5 pixels, C1 = 0.01^2, C2 = 0.03^2 (data range 1),
   averaged over views, channels and pixels.  The paper gives only the weight lambda = 0.2.
 * Adam with bias correction, as the per-agent optimiser (Sec. III-A, "optimized ... by gradient
-  descent"; Sec. III-D, refinement "at half the per-agent learning rate").
+  descent"; Sec. III-C, refinement "at half the per-agent learning rate").
 """
 from __future__ import annotations
 

@@ -1,7 +1,7 @@
 """Graph-captured mapping loop and the tile/launch autotuner.
 
 One mapping iteration (Sec. III-A: a submap optimised against its keyframe window by gradient
-descent; Sec. III-D: the refinement loss of Eq. 23 with its SSIM term) is
+descent; Sec. III-C: the refinement loss of Eq. 23 with its SSIM term) is
 
     gs_project -> gs_bin_sort -> gs_render_fwd -> gs_loss_l1_ssim -> gs_render_bwd -> gs_pose_grad
     -> gs_adam_step (which also clears the gradients for the next iteration)

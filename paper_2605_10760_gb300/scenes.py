@@ -6,7 +6,7 @@ the CPU oracle may take their inputs from it.
 
 Scene shapes follow the paper's workloads:
 
-* the camera model of the ReplicaMultiagent Plus renders (Sec. V, "Rendered
+* the camera model of the ReplicaMultiagent Plus renders (Sec. VI, "Rendered
   modalities"): 1200x680 pixels with a 90 degree horizontal field of view,
   hence fx = fy = 600, cx = 600, cy = 340; all agents share one camera model;
 * Gaussians carry a centre, per-axis scale, rotation, opacity and RGB colour
