@@ -149,24 +149,52 @@ class Pipeline:
                                                                               "opacities", "colors")])
         self.R.L.check(self.R.L.load().gs_grads_zero(self.g.n, C.byref(gg), self.R._stream()), "gs_grads_zero")
 
-    def step(self, ev=None):
+    def stages(self):
         R, pb = self.R, self.pb
-        rec = (lambda i: ev[i].record()) if ev else (lambda i: None)
-        rec(0)
-        pb.project(self.g)
-        rec(1)
-        pb.bin_sort()
-        rec(2)
-        pb.render_fwd(self.img)
-        rec(3)
-        R.loss_l1(self.img["rgb"], self.rgb_t, self.img["depth"], self.depth_t, 1.0, 0.1, self.d_rgb, self.d_depth,
-                  self.loss)
-        rec(4)
-        self.zero_grads()
-        pb.render_bwd(self.g, self.img, self.d_rgb, self.d_depth, None, self.grads)
-        rec(5)
-        pb.pose_grad(self.pose)
-        rec(6)
+        return [
+            lambda: pb.project(self.g),
+            lambda: pb.bin_sort(),
+            lambda: pb.render_fwd(self.img),
+            lambda: R.loss_l1(self.img["rgb"], self.rgb_t, self.img["depth"], self.depth_t, 1.0, 0.1, self.d_rgb,
+                              self.d_depth, self.loss),
+            lambda: (self.zero_grads(), pb.render_bwd(self.g, self.img, self.d_rgb, self.d_depth, None, self.grads)),
+            lambda: pb.pose_grad(self.pose),
+        ]
+
+    def step(self, ev=None):
+        """Eager: every stage's libgs calls issued from the host."""
+        for i, fn in enumerate(self.stages()):
+            if ev:
+                ev[i].record()
+            fn()
+        if ev:
+            ev[len(STAGES)].record()
+
+    def capture(self):
+        """Capture each stage as its own CUDA graph (after one eager warm-up step), so a step is six
+        graph launches with events between them."""
+        torch = self.torch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graphs = []
+        for fn in self.stages():
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr):
+                fn()
+            self.graphs.append(gr)
+        torch.cuda.synchronize()
+
+    def step_graph(self, ev=None):
+        for i, gr in enumerate(self.graphs):
+            if ev:
+                ev[i].record()
+            gr.replay()
+        if ev:
+            ev[len(STAGES)].record()
 
 
 STAGES = ["project", "bin_sort", "render_fwd", "loss", "render_bwd", "pose_grad"]
@@ -176,23 +204,46 @@ def l2_flush(buf):
     buf.zero_()
 
 
-def time_steps(pipe, steps, warmup, flush_buf, torch):
+def rank_views(S, wl, rank, world):
+    """Weak scaling: with N ranks every rank renders its own camera of the room (N cameras drawn
+    from one seed), so per-GPU work is fixed as N grows; a single process renders camera 0."""
+    if world > 1:
+        wl.cameras = S.room_cameras(wl.scene, world, seed=11)
+        wl.scene_of_view = np.zeros(world, np.int32)
+        return [rank]
+    return [0]
+
+
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value (timing only; no data-path collective)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_steps(pipe, steps, warmup, flush_buf, torch, graphs=True, barrier=None):
+    run = pipe.step_graph if graphs else pipe.step
     for _ in range(warmup):
-        pipe.step()
+        run()
     torch.cuda.synchronize()
     rc, _ = pipe.pb.check_status()
     if rc != 0:
         raise RuntimeError("device status %d during warm-up" % rc)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(steps)]
     with Clocks() as clk:
+        if barrier:
+            barrier()
         torch.cuda.synchronize()
         clk.mark_start()
         for i in range(steps):
             l2_flush(flush_buf)
-            pipe.step(evs[i])
+            run(evs[i])
         torch.cuda.synchronize()
+        if barrier:
+            barrier()
         clk.mark_end()
-    step_ms = [e[0].elapsed_time(e[6]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[len(STAGES)]) for e in evs]
     stage_ms = {s: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, s in enumerate(STAGES)}
     return step_ms, stage_ms, clk.summary()
 
@@ -264,6 +315,72 @@ def batched_speedup(R, S, torch, flush_buf, reps=3):
             "status": rc1}
 
 
+def mapping_graph(R, S, torch, iters=100, reps=2):
+    """room1m: 1M-Gaussian room, 8 views; `iters` mapping iterations (project, bin + sort, forward,
+    0.8 L1 + 0.2 (1 - SSIM), backward, pose gradient, Adam) captured in one CUDA graph; the tile
+    shape is picked first by the autotuner."""
+    from paper_2605_10760_gb300 import mapping as M
+    wl = S.workload("room1m")
+    V, H, W = len(wl.cameras), wl.height, wl.width
+    cams = R.cameras_tensor(wl.cameras)
+    tgt = torch.from_numpy(np.stack([S.smooth_image(W, H, 300 + v) for v in range(V)])).cuda()
+    g0 = R.Gaussians.from_scene(wl.scene)
+
+    def make(params):
+        return R.Problem(np.zeros(V, np.int64), np.full(V, wl.scene.n, np.int64), wl.scene.n, W, H, cams,
+                         params=params)
+
+    tw, th, _, table = M.autotune(make, g0, tgt, iters=3, reps=2, cache_key="room1m_8views")
+    pb = make(R.default_params(tile_w=tw, tile_h=th))
+    loop = M.MappingLoop(pb, g0, tgt)
+    loop.capture(iters)
+    loop.replay()
+    torch.cuda.synchronize()
+    rc0, _ = pb.check_status()
+    times = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        loop.replay()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    rc, req = pb.check_status()
+    ms_iter = statistics.median(times) / iters
+    return {"workload": "room1m: 1M-Gaussian room, 8 views 1200x680, 0.8 L1 + 0.2 (1-SSIM), Adam, "
+                        "%d iterations per CUDA graph" % iters,
+            "tile": [tw, th], "autotune": table, "ms_per_iteration": ms_iter,
+            "iterations_per_s": 1e3 / ms_iter, "views_per_s": V * 1e3 / ms_iter,
+            "loss_after": float(loop.loss.item()), "status": rc or rc0, "required_keys": req}
+
+
+def fused_map(R, S, torch, steps=3):
+    """floor4m: 16 agents' submaps merged into 4M Gaussians (multi-room floor), 64 views in one
+    batched problem, forward + backward with per-view pose gradients."""
+    wl = S.workload("floor4m")
+    V = len(wl.cameras)
+    pipe = Pipeline(R, S, wl, list(range(V)))
+    pipe.step()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        pipe.step()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    rc, _ = pipe.pb.check_status()
+    st = pipe.pb.stats()
+    ms = statistics.median(times)
+    out = {"workload": "floor4m: 4M Gaussians (16 submaps), 64 views 1200x680", "views": V, "ms_per_step": ms,
+           "views_per_s": V * 1e3 / ms, "keys": st["num_keys"], "fwd_pairs": st["fwd_pairs"],
+           "bwd_pairs": st["bwd_pairs"], "status": rc, "workspace_gb": pipe.pb.ws_bytes / 1e9}
+    del pipe
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle as it stands, timed on this host's cores on the same workload."""
     from oracle import losses as OL
@@ -333,6 +450,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the graph-loop and 4M/64-view measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -349,23 +467,20 @@ def main():
     from paper_2605_10760_gb300 import scenes as S
     R.L.load()
     wl = S.workload("room500k")
-    if world > 1:   # each rank its own camera in the room (weak scaling)
-        wl.cameras = S.room_cameras(wl.scene, world, seed=11)
-    pipe = Pipeline(R, S, wl, [rank if world > 1 else 0])
+    pipe = Pipeline(R, S, wl, rank_views(S, wl, rank, world))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     launches0 = R.L.load().gs_launch_count()
     pipe.step()
     torch.cuda.synchronize()
     launches_per_step = R.L.load().gs_launch_count() - launches0
     stats = pipe.pb.stats()
-    if world > 1:
-        dist.barrier()
-    step_ms, stage_ms, clocks = time_steps(pipe, args.steps, args.warmup, flush, torch)
+    pipe.capture()
+    eager_ms, eager_stage_ms, _ = time_steps(pipe, max(5, args.steps // 3), 2, flush, torch, graphs=False)
+    barrier = dist.barrier if world > 1 else None
+    step_ms, stage_ms, clocks = time_steps(pipe, args.steps, args.warmup, flush, torch, graphs=True, barrier=barrier)
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, "cuda")
     rc, _ = pipe.pb.check_status()
     ms = total_ms / args.steps
     value = world * pipe.V / (ms / 1e3)
@@ -398,6 +513,8 @@ def main():
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_note": "of %s" % peaks["src"]}
     batched = None if args.no_batched else batched_speedup(R, S, torch, flush)
+    graph_loop = None if args.no_extra else mapping_graph(R, S, torch)
+    fused = None if args.no_extra else fused_map(R, S, torch)
     cpu = None if args.no_cpu else cpu_baseline()
     line = {
         "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
@@ -408,12 +525,17 @@ def main():
                    "keys": K, "fwd_pairs": stats["fwd_pairs"], "bwd_pairs": stats["bwd_pairs"],
                    "status": rc},
         "stages_ms": stage_ms,
+        "timing": "each stage replayed as its own CUDA graph, events between stages; eager (host-issued) "
+                  "step for comparison in eager_ms_per_step",
+        "eager_ms_per_step": statistics.mean(eager_ms), "eager_stages_ms": eager_stage_ms,
         "roofline": roof,
         "e2e": {"value": world * pipe.V / (e2e_ms / 1e3), "unit": "views/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches_per_step * args.steps,
         "launches_per_step": launches_per_step,
         "batched": batched,
+        "mapping_graph": graph_loop,
+        "fused_map": fused,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }

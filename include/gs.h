@@ -124,7 +124,7 @@ typedef struct gs_grads {
 } gs_grads;
 
 /* Device pointers into an initialised workspace, for inspection and tests.  Sizes: proj [P,12]
- * float (mean_x, mean_y, conic_A, conic_B | conic_C, opacity, depth, radius | r, g, b, unused);
+ * float (mean_x, mean_y, conic_A, conic_B | conic_C, opacity, depth, radius | r, g, b, sigma_cut);
  * tiles_touched [P] uint32 (inclusive prefix sums after gs_bin_sort); sorted_keys [K] uint64;
  * sorted_vals [K] uint32 (flattened pair index p = pair_offset[v] + i); tile_ranges [G,2] uint32
  * with G = V * ceil(W/tile_w) * ceil(H/tile_h); grad2d [P,12] float (dL/d mean_x, mean_y,

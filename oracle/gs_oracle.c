@@ -506,6 +506,17 @@ int64_t og_forward(const og_ctx *c, double *rgb, double *depth, double *alpha, d
 /* 4. backward compositing: per (view, Gaussian) gradients of the 2-D quantities               */
 /* g2d [VN,10] = dL/d(mean_x, mean_y, conic_A, conic_B, conic_C, opacity, depth, r, g, b).      */
 /* ------------------------------------------------------------------------------------------ */
+#define OG_ACC(dst, val)                 \
+    do {                                 \
+        double v_ = (val);               \
+        if (shared_acc) {                \
+            _Pragma("omp atomic")        \
+            (dst) += v_;                 \
+        } else {                         \
+            (dst) += v_;                 \
+        }                                \
+    } while (0)
+
 static void og_backward_2d(const og_ctx *c, const double *g_rgb, const double *g_depth, const double *g_alpha,
                            double *g2d)
 {
@@ -515,7 +526,11 @@ static void og_backward_2d(const og_ctx *c, const double *g_rgb, const double *g
 #ifdef _OPENMP
     nthreads = omp_get_max_threads();
 #endif
-    double *buf = (double *)calloc((size_t)nthreads * c->VN * 10, sizeof(double));
+    /* one accumulator per thread, unless that would take more than 2 GB; then one shared
+     * accumulator with atomic adds (only the FP64 summation order differs) */
+    const char *force = getenv("GS_ORACLE_SHARED_ACC");
+    const int shared_acc = (force && force[0] == '1') || (double)nthreads * (double)c->VN * 80.0 > 2e9;
+    double *buf = (double *)calloc((size_t)(shared_acc ? 1 : nthreads) * c->VN * 10, sizeof(double));
     int64_t maxlen = 1;
     for (int64_t g = 0; g < c->G; ++g) {
         int64_t l = (int64_t)c->ranges[2 * g + 1] - c->ranges[2 * g];
@@ -527,7 +542,7 @@ static void og_backward_2d(const og_ctx *c, const double *g_rgb, const double *g
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-        double *acc = buf + (size_t)tid * c->VN * 10;
+        double *acc = buf + (size_t)(shared_acc ? 0 : tid) * c->VN * 10;
         og_entry *ent = (og_entry *)malloc(sizeof(og_entry) * maxlen);
 #pragma omp for schedule(dynamic, 4)
         for (int64_t g = 0; g < c->G; ++g) {
@@ -552,30 +567,30 @@ static void og_backward_2d(const og_ctx *c, const double *g_rgb, const double *g
                         const double *col = P->c_d + 3 * gi;
                         double a = E->alpha, Tj = E->T, w = a * Tj;
                         double *o = acc + 10 * (int64_t)f;
-                        for (int ch = 0; ch < 3; ++ch) o[7 + ch] += gC[ch] * w;
-                        o[6] += gD * w;
+                        for (int ch = 0; ch < 3; ++ch) OG_ACC(o[7 + ch], gC[ch] * w);
+                        OG_ACC(o[6], gD * w);
                         double dLda = gA * T_final / (1.0 - a);
                         for (int ch = 0; ch < 3; ++ch) dLda += gC[ch] * (col[ch] * Tj - SC[ch] / (1.0 - a));
                         dLda += gD * (c->zd[f] * Tj - SD / (1.0 - a));
                         for (int ch = 0; ch < 3; ++ch) SC[ch] += col[ch] * w;
                         SD += c->zd[f] * w;
                         if (E->capped) continue;          /* alpha = alpha_max: no dependence */
-                        o[5] += dLda * E->G;              /* d alpha / d o = exp(-sigma) */
+                        OG_ACC(o[5], dLda * E->G);              /* d alpha / d o = exp(-sigma) */
                         double dLds = -dLda * a;          /* d alpha / d sigma = -alpha */
                         double dx = E->dx, dy = E->dy;
                         double A = c->cAd[f], B = c->cBd[f], C = c->cCd[f];
-                        o[2] += dLds * 0.5 * dx * dx;
-                        o[3] += dLds * dx * dy;
-                        o[4] += dLds * 0.5 * dy * dy;
-                        o[0] += dLds * (-(A * dx + B * dy));   /* dx = px - mean_x */
-                        o[1] += dLds * (-(B * dx + C * dy));
+                        OG_ACC(o[2], dLds * 0.5 * dx * dx);
+                        OG_ACC(o[3], dLds * dx * dy);
+                        OG_ACC(o[4], dLds * 0.5 * dy * dy);
+                        OG_ACC(o[0], dLds * (-(A * dx + B * dy)));   /* dx = px - mean_x */
+                        OG_ACC(o[1], dLds * (-(B * dx + C * dy)));
                     }
                 }
         }
         free(ent);
     }
     memset(g2d, 0, sizeof(double) * 10 * c->VN);
-    for (int t = 0; t < nthreads; ++t) {
+    for (int t = 0; t < (shared_acc ? 1 : nthreads); ++t) {
         const double *src = buf + (size_t)t * c->VN * 10;
 #pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < c->VN * 10; ++k) g2d[k] += src[k];

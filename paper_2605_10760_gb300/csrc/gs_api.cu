@@ -72,7 +72,9 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     L->passes = (32 + gbits + 7) / 8;
     if (L->passes > kMaxPasses) return GS_ERR_INVALID_ARG;
     L->scan_parts = std::max<long long>(1, (P + kScanTile - 1) / kScanTile);
-    L->sort_parts = std::max<long long>(1, (L->cap + kSortTile - 1) / kSortTile);
+    L->sort_ipt = sort_ipt_for(L->cap);
+    const long long sort_tile = (long long)kSortThreads * L->sort_ipt;
+    L->sort_parts = std::max<long long>(1, (L->cap + sort_tile - 1) / sort_tile);
     long long chunks_total = 0;
     for (int v = 0; v < L->V; ++v) chunks_total += (pb->view_gauss_count[v] + kChunk - 1) / kChunk;
     size_t o = 0;
@@ -86,6 +88,7 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     L->o_hist = o; o = align256(o + sizeof(uint32_t) * kMaxPasses * 256);
     L->o_sort_state = o; o = align256(o + sizeof(uint32_t) * 256 * (size_t)L->sort_parts * L->passes);
     L->o_ranges = o; o = align256(o + sizeof(uint32_t) * 2 * (size_t)L->G);
+    L->o_srec = o; o = align256(o + sizeof(float) * 12 * (size_t)L->cap);
     L->o_g2d = o; o = align256(o + sizeof(float) * 12 * (size_t)std::max<long long>(P, 1));
     L->o_pose_part = o; o = align256(o + sizeof(float) * 8 * (size_t)std::max<long long>(chunks_total, 1));
     L->total = o;
@@ -257,6 +260,7 @@ int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stre
     a.W = L.W; a.H = L.H;
     a.tw = (float)L.tw; a.th = (float)L.th; a.Tx = (float)L.Tx; a.Ty = (float)L.Ty;
     a.near_plane = pb->params.near_plane; a.dil = pb->params.dilation; a.sigmas = pb->params.radius_sigmas;
+    a.alpha_min = pb->params.alpha_min;
     launch_project(L, a, (cudaStream_t)stream);
     return check_launch();
 }
@@ -276,8 +280,9 @@ static BinArgs make_bin_args(const Layout &L, void *ws) {
     a.hist = ws_ptr<uint32_t>(ws, L.o_hist);
     a.sort_state = ws_ptr<uint32_t>(ws, L.o_sort_state);
     a.ranges = ws_ptr<uint32_t>(ws, L.o_ranges);
+    a.srec = ws_ptr<float4>(ws, L.o_srec);
     a.st = ws_ptr<DevStatus>(ws, L.o_status);
-    a.V = L.V; a.Tx = L.Tx; a.Ty = L.Ty; a.passes = L.passes;
+    a.V = L.V; a.Tx = L.Tx; a.Ty = L.Ty; a.passes = L.passes; a.sort_ipt = L.sort_ipt;
     a.tw = (float)L.tw; a.th = (float)L.th;
     a.P = L.P; a.cap = L.cap; a.sort_parts = L.sort_parts; a.max_chunks = L.max_chunks; a.G = L.G;
     a.fault_scan_part = -1;
@@ -301,8 +306,7 @@ int gs_render_fwd(const gs_problem *pb, void *ws, const gs_image *out, void *str
     if (!ws_ok(ws) || !out || !out->final_T || !out->last_idx) return GS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     FwdArgs a;
-    a.proj = ws_ptr<const float4>(ws, L.o_proj);
-    a.vals = ws_ptr<const uint32_t>(ws, L.o_vals[L.passes & 1]);
+    a.srec = ws_ptr<const float4>(ws, L.o_srec);
     a.ranges = ws_ptr<const uint32_t>(ws, L.o_ranges);
     a.rgb = out->rgb; a.depth = out->depth; a.alpha = out->alpha; a.finalT = out->final_T; a.last = out->last_idx;
     a.st = ws_ptr<DevStatus>(ws, L.o_status);
@@ -324,8 +328,7 @@ int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const g
         return GS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     BwdArgs a;
-    a.proj = ws_ptr<const float4>(ws, L.o_proj);
-    a.vals = ws_ptr<const uint32_t>(ws, L.o_vals[L.passes & 1]);
+    a.srec = ws_ptr<const float4>(ws, L.o_srec);
     a.ranges = ws_ptr<const uint32_t>(ws, L.o_ranges);
     a.finalT = fwd->final_T; a.last = fwd->last_idx;
     a.d_rgb = dimg->d_rgb; a.d_depth = dimg->d_depth; a.d_alpha = dimg->d_alpha;

@@ -16,8 +16,12 @@ namespace gs {
 
 constexpr int kMaxPasses = 8;          // 8-bit digits of a 64-bit key
 constexpr int kSortThreads = 256;
-constexpr int kSortIPT = 16;
-constexpr int kSortTile = kSortThreads * kSortIPT;   // keys per onesweep partition
+// keys per thread of a onesweep partition.  4096-key partitions (16 per thread) throughout: with
+// 1024-key partitions the per-digit look-back chains grow four times longer and a 270k-key sort
+// was measured slower on GB300, so the small variant is only compiled, not selected.
+constexpr int kSortIPTSmall = 4, kSortIPTLarge = 16;
+constexpr long long kSmallSortCap = 0;
+inline int sort_ipt_for(long long cap) { return cap <= kSmallSortCap ? kSortIPTSmall : kSortIPTLarge; }
 constexpr int kScanThreads = 256;
 constexpr int kScanIPT = 16;
 constexpr int kScanTile = kScanThreads * kScanIPT;
@@ -45,11 +49,11 @@ struct ViewEntry {                // per-view table in the workspace (32 bytes)
 };
 
 struct Layout {
-    int V, W, H, tw, th, Tx, Ty, passes;
+    int V, W, H, tw, th, Tx, Ty, passes, sort_ipt;
     long long G, P, N, cap, max_count, max_chunks;
     long long scan_parts, sort_parts;
     size_t o_status, o_views, o_proj, o_touched, o_scan_state, o_keys[2], o_vals[2], o_hist,
-        o_sort_state, o_ranges, o_g2d, o_pose_part, total;
+        o_sort_state, o_ranges, o_srec, o_g2d, o_pose_part, total;
 };
 
 // ------------------------------------------------------------------------------------------
@@ -80,7 +84,12 @@ __device__ __forceinline__ float spec_expf(float x) {
     const float kLog2e = 0x1.715476p+0f;
     const float kLn2Hi = 0x1.62e4p-1f;
     const float kLn2Lo = 0x1.7f7d1cp-20f;
-    float kf = rintf(fp::mul(x, kLog2e));
+    // round x log2(e) to the nearest integer, ties to even: adding and subtracting 1.5 * 2^23
+    // rounds exactly that way for |t| < 2^22, and the low bits of the sum hold the integer itself
+    const float kShift = 12582912.0f;
+    const float t = fp::add(fp::mul(x, kLog2e), kShift);
+    const float kf = fp::sub(t, kShift);
+    const int k = __float_as_int(t) - 0x4B400000;
     float r = fp::fma(-kf, kLn2Hi, x);
     r = fp::fma(-kf, kLn2Lo, r);
     float p = 0x1.a01a02p-13f;              // 1/7!
@@ -91,7 +100,6 @@ __device__ __forceinline__ float spec_expf(float x) {
     p = fp::fma(p, r, 0.5f);
     p = fp::fma(p, r, 1.0f);
     p = fp::fma(p, r, 1.0f);
-    int k = (int)kf;
     return fp::mul(p, __int_as_float((k + 127) << 23));
 }
 
@@ -224,6 +232,51 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// ------------------------------------------------------------------------------------------
+// TMA bulk copies (cp.async.bulk, 1-D) completing on shared-memory mbarriers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// orders this thread's earlier generic-proxy accesses of shared memory before later async-proxy
+// (TMA) accesses, and makes initialised mbarriers visible to the async proxy
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// one arrival that also announces `bytes` of transaction count, then the bulk copy that completes
+// them; dst and src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase with the given parity; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned long long limit) {
+    for (unsigned long long i = 0; i < limit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 64) __nanosleep(32);
+    }
+    return false;
 }
 
 // ------------------------------------------------------------------------------------------

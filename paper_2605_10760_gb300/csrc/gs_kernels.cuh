@@ -14,7 +14,7 @@ struct ProjArgs {
     uint32_t *touched;          // [P]
     int W, H;
     float tw, th, Tx, Ty;
-    float near_plane, dil, sigmas;
+    float near_plane, dil, sigmas, alpha_min;
 };
 
 struct ProjBwdArgs {
@@ -45,8 +45,9 @@ struct BinArgs {
     uint32_t *hist;                    // [kMaxPasses][256]
     uint32_t *sort_state;              // [passes][sort_parts][256]
     uint32_t *ranges;                  // [G,2]
+    float4 *srec;                      // [cap,3] records in list order
     DevStatus *st;
-    int V, Tx, Ty, passes;
+    int V, Tx, Ty, passes, sort_ipt;
     float tw, th;
     long long P, cap, sort_parts, max_chunks, G;
     int fault_scan_part;               // -1 normally; >= 0: that scan partition never publishes
@@ -61,8 +62,7 @@ int run_scan_only(const BinArgs &a, cudaStream_t s);
 
 // ---------------- rendering ----------------
 struct FwdArgs {
-    const float4 *proj;
-    const uint32_t *vals;
+    const float4 *srec;                // [K,3] records in list order (r1.w = pair index bits)
     const uint32_t *ranges;
     float *rgb, *depth, *alpha, *finalT;
     int32_t *last;
@@ -73,8 +73,7 @@ struct FwdArgs {
 };
 
 struct BwdArgs {
-    const float4 *proj;
-    const uint32_t *vals;
+    const float4 *srec;
     const uint32_t *ranges;
     const float *finalT;
     const int32_t *last;

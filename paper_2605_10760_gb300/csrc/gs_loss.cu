@@ -32,7 +32,7 @@ __device__ __forceinline__ void block_add_double(double v, double *out) {
 
 __global__ void k_l1(long long HWn, int V, const float *rgb, const float *rgb_t, const float *depth,
                      const float *depth_t, float sc_rgb, float sc_d, float *d_rgb, float *d_depth, double *loss) {
-    double acc = 0.0;
+    float acc_rgb = 0.f, acc_d = 0.f;      // per-thread sums of |d| (a few dozen terms each)
     const long long total = (long long)V * HWn;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const long long v = i / HWn, p = i - v * HWn;
@@ -40,16 +40,16 @@ __global__ void k_l1(long long HWn, int V, const float *rgb, const float *rgb_t,
         for (int c = 0; c < 3; ++c) {
             const long long idx = (3 * v + c) * HWn + p;
             const float d = rgb[idx] - rgb_t[idx];
-            acc += (double)fabsf(d) * sc_rgb;
+            acc_rgb += fabsf(d);
             d_rgb[idx] = sgnf(d) * sc_rgb;
         }
         if (depth && d_depth) {
             const float d = depth[i] - depth_t[i];
-            acc += (double)fabsf(d) * sc_d;
+            acc_d += fabsf(d);
             d_depth[i] = sgnf(d) * sc_d;
         }
     }
-    block_add_double(acc, loss);
+    block_add_double((double)acc_rgb * sc_rgb + (double)acc_d * sc_d, loss);
 }
 
 int launch_loss_l1(int V, int W, int H, const float *rgb, const float *rgb_t, const float *depth,

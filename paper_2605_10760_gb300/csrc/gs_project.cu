@@ -32,9 +32,16 @@ __global__ void __launch_bounds__(kChunk) k_project(ProjArgs a) {
         cnt = (uint32_t)((o.x1 - o.x0) * (o.y1 - o.y0));
         const float *col = a.colors + 3 * gi;
         float4 *rec = a.proj + 3 * f;
+        const float op = __ldg(a.opacities + gi);
+        // sigma beyond which alpha < alpha_min is certain (see gs_render.cu); +inf disables the cut
+        float cut = __int_as_float(0x7f800000);
+        if (a.alpha_min > 0.0f) {
+            if (op > 0.0f) cut = logf(op / a.alpha_min) + 1e-3f;
+            else if (op <= 0.0f) cut = -1.0f;
+        }
         rec[0] = make_float4(o.mx, o.my, o.A, o.B);
-        rec[1] = make_float4(o.C, __ldg(a.opacities + gi), o.z, o.rf);
-        rec[2] = make_float4(__ldg(col), __ldg(col + 1), __ldg(col + 2), 0.0f);
+        rec[1] = make_float4(o.C, op, o.z, o.rf);
+        rec[2] = make_float4(__ldg(col), __ldg(col + 1), __ldg(col + 2), cut);
     }
     a.touched[f] = cnt;
 }
@@ -224,19 +231,28 @@ void launch_project_bwd(const Layout &L, const ProjBwdArgs &a, cudaStream_t s) {
     count_launches(1);
 }
 
-// deterministic per-view sum of the pose partials: one warp per (view, component)
-__global__ void k_pose_reduce(const ViewEntry *views, const float *pose_part, float *out) {
-    const int v = blockIdx.x, k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// deterministic per-view sum of the pose partials: one 256-thread block per (view, component),
+// fixed per-thread strides and a fixed reduction tree
+__global__ void __launch_bounds__(256) k_pose_reduce(const ViewEntry *views, const float *pose_part, float *out) {
+    __shared__ float s_w[8];
+    const int v = blockIdx.x, k = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const ViewEntry ve = views[v];
     const long long chunks = (ve.count + kChunk - 1) / kChunk;
     float acc = 0.f;
-    for (long long c = lane; c < chunks; c += 32) acc += pose_part[(ve.chunk_off + c) * 8 + k];
+    for (long long c = threadIdx.x; c < chunks; c += 256) acc += pose_part[(ve.chunk_off + c) * 8 + k];
     acc = warp_sum(acc);
-    if (lane == 0) out[6 * v + k] = acc;
+    if (lane == 0) s_w[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) r += s_w[w];
+        out[6 * v + k] = r;
+    }
 }
 
 void launch_pose_reduce(const Layout &L, const ViewEntry *views, const float *part, float *out, cudaStream_t s) {
-    k_pose_reduce<<<L.V, 6 * 32, 0, s>>>(views, part, out);
+    k_pose_reduce<<<dim3(L.V, 6), 256, 0, s>>>(views, part, out);
     count_launches(1);
 }
 

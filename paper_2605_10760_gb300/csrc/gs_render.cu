@@ -1,101 +1,252 @@
 // gs_render.cu -- per-tile compositing (forward) and its adjoint (backward).
 //
-// One CTA = one tile of TW x TH pixels (one thread per pixel).  Both kernels are persistent: a
-// grid of (#SM x resident CTAs) claims (view, tile) work items from a device counter, so one launch
-// covers every tile of every view of every scene, whatever the per-tile list lengths.
+// One CTA = one tile of TW x TH pixels, two vertically adjacent pixels per thread (so a warp covers
+// a compact TW x 4 block when TW = 16).  Both kernels are persistent: a grid of (#SM x resident
+// CTAs) claims (view, tile) work items from a device counter, so one launch covers every tile of
+// every view of every scene, whatever the per-tile list lengths.
 //
-// Forward: the tile's list (a contiguous range of the sorted values) is staged into shared memory in
-// batches of TW*TH records; each thread walks it front to back taking the FP32 decisions of the
-// decision chain (sigma < 0 skip, alpha < alpha_min skip, stop before blending when
-// T (1 - alpha) < t_min).  The CTA leaves the list once every pixel has stopped.
+// Staging: a tile's list is a contiguous block of records (gs_bin_sort writes them in list order),
+// so each batch of TW*TH records is one TMA bulk copy (cp.async.bulk) issued by one thread into one
+// of two shared-memory buffers and completed on that buffer's mbarrier; the next batch is copied
+// while the current one is processed.  All mbarrier waits are bounded (error + drain + return).
+//
+// Forward: each thread walks the staged records front to back for its two pixels taking the FP32
+// decisions of the decision chain (sigma < 0 skip, alpha < alpha_min skip, stop before blending
+// when T (1 - alpha) < t_min).  The CTA leaves the list once every pixel has stopped.  Each record
+// carries a cut-off sigma_cut = ln(o / alpha_min) + 1e-3: for sigma > sigma_cut the exponential is
+// not evaluated because alpha < alpha_min is certain (the decision-chain exp is within 2 ulp of
+// e^x), so every decision is exactly the one the full test takes.
 //
 // Backward: from final_T and last_idx of each pixel the CTA walks the list back to front,
 // recovering T_j = T_{j+1} / (1 - alpha_j) and the colour / depth accumulated behind each entry, so
-// no per-pixel list is stored.  Each warp reduces the 10 per-Gaussian gradient components of its
-// 32 pixels with a transposed butterfly (16 shuffles instead of 50) after which 10 lanes issue one
-// atomic add each, so a (Gaussian, warp) pair costs one warp-wide atomic instruction; warps whose
-// pixels all skipped the entry issue nothing.
+// no per-pixel list is stored.  Each thread sums the 10 per-Gaussian gradient components of its two
+// pixels, then the warp reduces them with a transposed butterfly (16 shuffles instead of 50) after
+// which 10 lanes issue one atomic add each: a (Gaussian, warp) pair costs one warp-wide atomic
+// instruction; warps whose 64 pixels all skip the entry issue nothing, and entries past the
+// warp's last blended position are not visited at all.
 #include "gs_kernels.cuh"
 
 namespace gs {
 
+constexpr int kPPT = 2;   // pixels per thread
+
+// Minimum over the box [xa, xb] x [ya, yb] of sigma(d) = 1/2 (A dx^2 + C dy^2) + B dx dy,
+// d = p - mean (a convex quadratic: 0 when the mean is inside, else attained on an edge, where the
+// 1-D minimiser is clamped to the edge).  Ordinary FP32 arithmetic; callers compare it against the
+// cut-off with a margin.  Returns 0 (never skip) for non-finite or non-positive-definite input.
+__device__ __forceinline__ float sigma_min_box(float A, float B, float C, float mx, float my, float xa, float xb,
+                                               float ya, float yb) {
+    if (!(A > 0.f && C > 0.f && A < 1e30f && C < 1e30f && fabsf(B) < 1e30f && fabsf(mx) < 1e30f &&
+          fabsf(my) < 1e30f))
+        return 0.f;
+    const float dxa = xa - mx, dxb = xb - mx, dya = ya - my, dyb = yb - my;
+    if (dxa <= 0.f && dxb >= 0.f && dya <= 0.f && dyb >= 0.f) return 0.f;
+    const float iA = __fdividef(1.f, A), iC = __fdividef(1.f, C);
+    float best = 3.0e38f;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dx = e ? dxb : dxa;
+        const float dy = fminf(fmaxf(-B * dx * iC, dya), dyb);
+        best = fminf(best, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dy = e ? dyb : dya;
+        const float dx = fminf(fmaxf(-B * dy * iA, dxa), dxb);
+        best = fminf(best, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
+    }
+    return best;
+}
+
+// Bit w set <=> warp w's block of pixels (TW columns x 2*32/TW rows of the tile) may blend the
+// entry.  A cleared bit means sigma > cut at every pixel of that block: every pixel there skips the
+// entry in the decision chain, so the warp may skip it without evaluating anything.  The margin
+// (0.01 + 1e-3 |cut|) is far above the FP32 error of either sigma evaluation.
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) k_render_fwd(FwdArgs a) {
-    constexpr int NT = TW * TH;
-    __shared__ float4 s_r0[NT], s_r1[NT], s_r2[NT];
-    __shared__ long long s_item;
+__device__ __forceinline__ uint32_t warp_region_mask(const float4 &r0, const float4 &r1, float cut, int tile_x0,
+                                                     int tile_y0) {
+    constexpr int NW = TW * TH / (kPPT * 32);
+    constexpr int ROWS = kPPT * 32 / TW;
+    const float thr = cut + 0.01f + 1e-3f * fabsf(cut);
+    const float xa = (float)tile_x0 + 0.5f, xb = (float)(tile_x0 + TW) - 0.5f;
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const float ya = (float)(tile_y0 + w * ROWS) + 0.5f;
+        const float s = sigma_min_box(r0.z, r0.w, r1.x, r0.x, r0.y, xa, xb, ya, ya + (float)(ROWS - 1));
+        if (!(s > thr)) m |= 1u << w;
+    }
+    return m;
+}
+
+constexpr unsigned long long kTmaWaitLimit = 1ull << 22;   // polls of a batch's mbarrier before giving up
+
+// Shared memory of one render CTA: two batches of records (double buffer filled by TMA), the
+// per-entry warp-region masks of each batch, one mbarrier per buffer.
+// records per staged batch: one per pixel, at most 256 (keeps two buffers within 25 KB)
+template <int TW, int TH>
+__host__ __device__ constexpr int batch_records() { return TW * TH < 256 ? TW * TH : 256; }
+
+template <int TW, int TH>
+struct __align__(128) RenderSmem {
+    float4 rec[2][3 * batch_records<TW, TH>()];
+    uint8_t mask[2][batch_records<TW, TH>()];
+    uint64_t bar[2];
+    long long item;
+    int maxlast;
+};
+
+// Waits for both buffers' outstanding copies (bounded) after a failed wait, so that the CTA never
+// leaves with a copy still targeting its shared memory unless that copy is itself stuck.
+template <int TW, int TH>
+__device__ __forceinline__ void drain_after_timeout(RenderSmem<TW, TH> &sm, const uint32_t (&parity)[2],
+                                                    const bool (&pending)[2], DevStatus *st) {
+    if (threadIdx.x == 0) {
+        record_error(st, GS_ERR_TIMEOUT, 8);
+        for (int bb = 0; bb < 2; ++bb)
+            if (pending[bb]) mbar_wait_bounded(&sm.bar[bb], parity[bb], kTmaWaitLimit);
+    }
+    __syncthreads();
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
+    constexpr int NB = batch_records<TW, TH>();   // records per staged batch
+    constexpr int NT = TW * TH / kPPT;            // threads
+    __shared__ RenderSmem<TW, TH> sm;
     const int tid = threadIdx.x;
+    const uint32_t wbit = 1u << (tid >> 5);
     const long long tpv = (long long)a.Tx * a.Ty;
     const long long HW = (long long)a.W * a.H;
+    const int lx = tid % TW, ly = (tid / TW) * kPPT;
+    if (tid == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    uint32_t parity[2] = {0u, 0u};
     unsigned long long pairs = 0;
     for (;;) {
-        if (tid == 0) s_item = (long long)atomicAdd(&a.st->ctr[kCtrFwd], 1u);
+        if (tid == 0) sm.item = (long long)atomicAdd(&a.st->ctr[kCtrFwd], 1u);
         __syncthreads();
-        const long long g = s_item;
+        const long long g = sm.item;
         if (g >= a.G) break;
         const int v = (int)(g / tpv);
         const int tl = (int)(g - (long long)v * tpv);
         const int ty = tl / a.Tx, tx = tl - ty * a.Tx;
-        const int x = tx * TW + (tid % TW), y = ty * TH + (tid / TW);
-        const bool inside = x < a.W && y < a.H;
+        const int x = tx * TW + lx, y0 = ty * TH + ly;
         const uint32_t start = a.ranges[2 * g], end = a.ranges[2 * g + 1];
         const int n = (int)(end - start);
-        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-        float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-        int last = 0;
-        bool done = !inside;
-        for (int b = 0; b < n; b += NT) {
-            if (__syncthreads_and(done)) break;
-            const int j = b + tid;
-            if (j < n) {
-                uint32_t f = a.vals[start + j];
-                if (f >= (uint32_t)a.P) {                 // only after an earlier recorded failure
-                    record_error(a.st, GS_ERR_DEVICE_FAULT, 6);
-                    f = 0;
-                }
-                s_r0[tid] = a.proj[3 * (size_t)f];
-                s_r1[tid] = a.proj[3 * (size_t)f + 1];
-                s_r2[tid] = a.proj[3 * (size_t)f + 2];
+        bool done[kPPT];
+        float T[kPPT], C0[kPPT], C1[kPPT], C2[kPPT], D[kPPT], py[kPPT];
+        int last[kPPT], visited[kPPT];
+#pragma unroll
+        for (int p = 0; p < kPPT; ++p) {
+            done[p] = !(x < a.W && y0 + p < a.H);
+            T[p] = 1.0f;
+            C0[p] = C1[p] = C2[p] = D[p] = 0.f;
+            last[p] = 0;
+            visited[p] = done[p] ? 0 : n;      // entries visited, up to and including the stopping one
+            py[p] = (float)(y0 + p) + 0.5f;
+        }
+        const float px = (float)x + 0.5f;
+        const int nb = (n + NB - 1) / NB;
+        auto issue = [&](int bi, int bb) {     // thread 0: batch bi of this tile into buffer bb
+            const int b = bi * NB;
+            fence_proxy_async_smem();
+            tma_load_1d(&sm.rec[bb][0], a.srec + 3 * (size_t)(start + b), (uint32_t)min(NB, n - b) * 48u,
+                        &sm.bar[bb]);
+        };
+        if (tid == 0 && nb > 0) issue(0, 0);
+        int buf = 0;
+        for (int bi = 0; bi < nb; ++bi) {
+            const int b = bi * NB, cnt = min(NB, n - b);
+            if (tid == 0 && bi + 1 < nb) issue(bi + 1, buf ^ 1);
+            const bool ok = mbar_wait_bounded(&sm.bar[buf], parity[buf], kTmaWaitLimit);
+            if (__syncthreads_or(!ok)) {
+                const bool pending[2] = {buf == 0 || bi + 1 < nb, buf == 1 || bi + 1 < nb};
+                drain_after_timeout<TW, TH>(sm, parity, pending, a.st);
+                return;
+            }
+            parity[buf] ^= 1u;
+            const float4 *rec = sm.rec[buf];
+#pragma unroll
+            for (int q = 0; q < kPPT; ++q) {
+                const int e = tid + q * NT;
+                if (e < cnt)
+                    sm.mask[buf][e] = (uint8_t)warp_region_mask<TW, TH>(rec[3 * e], rec[3 * e + 1], rec[3 * e + 2].w,
+                                                                        tx * TW, ty * TH);
             }
             __syncthreads();
-            const int cnt = min(NT, n - b);
-            if (!done) {
-                for (int k = 0; k < cnt; ++k) {
-                    const float4 r0 = s_r0[k];
-                    const float4 r1 = s_r1[k];
-                    ++pairs;
-                    const float dx = fp::sub(px, r0.x), dy = fp::sub(py, r0.y);
-                    const float sg = spec_sigma(r0.z, r0.w, r1.x, dx, dy);
-                    if (sg < 0.0f) continue;
-                    const float al = fminf(a.amax, fp::mul(r1.y, spec_expf(-sg)));
-                    if (al < a.amin) continue;
-                    const float Tn = fp::mul(T, fp::sub(1.0f, al));
+            const uint8_t *msk = sm.mask[buf];
+            for (int k = 0; k < cnt; ++k) {
+                if (done[0] && done[1]) break;
+                if (!(msk[k] & wbit)) continue;     // no pixel of this warp can blend the entry
+                const float4 r0 = rec[3 * k];
+                const float4 r1 = rec[3 * k + 1];
+                const float cut = rec[3 * k + 2].w;
+                const float dx = fp::sub(px, r0.x);
+                float sg[kPPT];
+                bool ev[kPPT];
+#pragma unroll
+                for (int p = 0; p < kPPT; ++p) {
+                    sg[p] = spec_sigma(r0.z, r0.w, r1.x, dx, fp::sub(py[p], r0.y));
+                    ev[p] = !done[p] && !(sg[p] < 0.0f) && !(sg[p] > cut);
+                }
+                if (!(ev[0] || ev[1])) continue;
+                float al[kPPT];
+#pragma unroll
+                for (int p = 0; p < kPPT; ++p) al[p] = fminf(a.amax, fp::mul(r1.y, spec_expf(-sg[p])));
+                const float4 r2 = rec[3 * k + 2];
+#pragma unroll
+                for (int p = 0; p < kPPT; ++p) {
+                    if (!ev[p] || al[p] < a.amin) continue;
+                    const float Tn = fp::mul(T[p], fp::sub(1.0f, al[p]));
                     if (Tn < a.tmin) {
-                        done = true;
-                        break;
+                        done[p] = true;
+                        visited[p] = b + k + 1;
+                        continue;
                     }
-                    const float4 r2 = s_r2[k];
-                    const float wgt = al * T;
-                    C0 += r2.x * wgt;
-                    C1 += r2.y * wgt;
-                    C2 += r2.z * wgt;
-                    D += r1.z * wgt;
-                    T = Tn;
-                    last = b + k + 1;
+                    const float wgt = al[p] * T[p];
+                    C0[p] += r2.x * wgt;
+                    C1[p] += r2.y * wgt;
+                    C2[p] += r2.z * wgt;
+                    D[p] += r1.z * wgt;
+                    T[p] = Tn;
+                    last[p] = b + k + 1;
                 }
             }
-        }
-        if (inside) {
-            const long long pix = (long long)y * a.W + x;
-            if (a.rgb) {
-                a.rgb[(3 * (long long)v + 0) * HW + pix] = C0 + T * a.bg0;
-                a.rgb[(3 * (long long)v + 1) * HW + pix] = C1 + T * a.bg1;
-                a.rgb[(3 * (long long)v + 2) * HW + pix] = C2 + T * a.bg2;
+            const bool all_done = __syncthreads_and(done[0] && done[1]);   // also: buffer reads finished
+            if (all_done) {
+                if (bi + 1 < nb) {   // the prefetched batch must land before its buffer is reused
+                    const bool ok2 = mbar_wait_bounded(&sm.bar[buf ^ 1], parity[buf ^ 1], kTmaWaitLimit);
+                    if (__syncthreads_or(!ok2)) {
+                        const bool pending[2] = {buf == 1, buf == 0};
+                        drain_after_timeout<TW, TH>(sm, parity, pending, a.st);
+                        return;
+                    }
+                    parity[buf ^ 1] ^= 1u;
+                }
+                break;
             }
-            if (a.depth) a.depth[(long long)v * HW + pix] = D;
-            if (a.alpha) a.alpha[(long long)v * HW + pix] = 1.0f - T;
-            a.finalT[(long long)v * HW + pix] = T;
-            a.last[(long long)v * HW + pix] = last;
+            buf ^= 1;
+        }
+#pragma unroll
+        for (int p = 0; p < kPPT; ++p) {
+            pairs += (unsigned long long)visited[p];
+            if (x < a.W && y0 + p < a.H) {
+                const long long pix = (long long)(y0 + p) * a.W + x;
+                if (a.rgb) {
+                    a.rgb[(3 * (long long)v + 0) * HW + pix] = C0[p] + T[p] * a.bg0;
+                    a.rgb[(3 * (long long)v + 1) * HW + pix] = C1[p] + T[p] * a.bg1;
+                    a.rgb[(3 * (long long)v + 2) * HW + pix] = C2[p] + T[p] * a.bg2;
+                }
+                if (a.depth) a.depth[(long long)v * HW + pix] = D[p];
+                if (a.alpha) a.alpha[(long long)v * HW + pix] = 1.0f - T[p];
+                a.finalT[(long long)v * HW + pix] = T[p];
+                a.last[(long long)v * HW + pix] = last[p];
+            }
         }
         __syncthreads();
     }
@@ -104,17 +255,20 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(FwdArgs a) {
     if ((tid & 31) == 0 && pairs) atomicAdd(&a.st->fwd_pairs, pairs);
 }
 
-// Transposed butterfly: after the call lane l holds the warp sum of component
-// c(l) = 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of l) in v[0].
+// Transposed butterfly over 16 slots: after the call lane l holds, in v[0], the warp sum of slot
+// s(l) = 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of l).  The 10 gradient components live in slots
+// 0..4 and 8..12 (kSlot); slots 5..7 and 13..15 are zero in every lane, so the first stage skips
+// their three all-zero pairs: 13 shuffles in total.
 __device__ __forceinline__ void warp_transpose_reduce16(float (&v)[16], int lane) {
     {
         const bool up = lane & 16;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < 5; ++i) {
             const float send = up ? v[i] : v[i + 8];
             const float keep = up ? v[i + 8] : v[i];
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
         }
+        v[5] = v[6] = v[7] = 0.f;
     }
     {
         const bool up = lane & 8;
@@ -143,121 +297,176 @@ __device__ __forceinline__ void warp_transpose_reduce16(float (&v)[16], int lane
     v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// slot of each gradient component (mean_x, mean_y, A, B, C, opacity, depth, r, g, b)
+enum : int { kSMx = 0, kSMy = 1, kSA = 2, kSB = 3, kSC = 4, kSO = 8, kSZ = 9, kSR = 10, kSG = 11, kSBl = 12 };
+
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) k_render_bwd(BwdArgs a) {
-    constexpr int NT = TW * TH;
-    __shared__ float4 s_r0[NT], s_r1[NT], s_r2[NT];
-    __shared__ uint32_t s_f[NT];
-    __shared__ long long s_item;
-    __shared__ int s_maxlast;
+__global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
+    constexpr int NB = batch_records<TW, TH>();
+    constexpr int NT = TW * TH / kPPT;
+    __shared__ RenderSmem<TW, TH> sm;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int comp = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-    const bool issuer = ((lane & 1) == 0) && comp < 10;
+    const uint32_t wbit = 1u << (tid >> 5);
+    const int slot = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+    const int comp = slot < 5 ? slot : slot - 3;           // component index in the grad2d record
+    const bool issuer = ((lane & 1) == 0) && (slot < 5 || (slot >= 8 && slot < 13));
     const long long tpv = (long long)a.Tx * a.Ty;
     const long long HW = (long long)a.W * a.H;
+    const int lx = tid % TW, ly = (tid / TW) * kPPT;
+    if (tid == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    uint32_t parity[2] = {0u, 0u};
     unsigned long long pairs = 0;
     for (;;) {
         if (tid == 0) {
-            s_item = (long long)atomicAdd(&a.st->ctr[kCtrBwd], 1u);
-            s_maxlast = 0;
+            sm.item = (long long)atomicAdd(&a.st->ctr[kCtrBwd], 1u);
+            sm.maxlast = 0;
         }
         __syncthreads();
-        const long long g = s_item;
+        const long long g = sm.item;
         if (g >= a.G) break;
         const int v = (int)(g / tpv);
         const int tl = (int)(g - (long long)v * tpv);
         const int ty = tl / a.Tx, tx = tl - ty * a.Tx;
-        const int x = tx * TW + (tid % TW), y = ty * TH + (tid / TW);
-        const bool inside = x < a.W && y < a.H;
+        const int x = tx * TW + lx, y0 = ty * TH + ly;
         const uint32_t start = a.ranges[2 * g];
-        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-        int lst = 0;
-        float T = 1.0f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f;
-        if (inside) {
-            const long long pix = (long long)y * a.W + x;
-            lst = a.last[(long long)v * HW + pix];
-            T = a.finalT[(long long)v * HW + pix];
-            if (a.d_rgb) {
-                gC0 = a.d_rgb[(3 * (long long)v + 0) * HW + pix];
-                gC1 = a.d_rgb[(3 * (long long)v + 1) * HW + pix];
-                gC2 = a.d_rgb[(3 * (long long)v + 2) * HW + pix];
-            }
-            if (a.d_depth) gD = a.d_depth[(long long)v * HW + pix];
-            if (a.d_alpha) gA = a.d_alpha[(long long)v * HW + pix];
-        }
-        pairs += (unsigned long long)lst;
-        const float Tfin = T;
-        float SC0 = Tfin * a.bg0, SC1 = Tfin * a.bg1, SC2 = Tfin * a.bg2, SD = 0.f;
-        const int wmax = __reduce_max_sync(0xffffffffu, lst);
-        if (lane == 0) atomicMax(&s_maxlast, wmax);
-        __syncthreads();
-        const int maxl = s_maxlast;
-        for (int hi = maxl; hi > 0; hi -= NT) {
-            const int lo = max(0, hi - NT);
-            __syncthreads();
-            const int j = lo + tid;
-            if (j < hi) {
-                uint32_t f = a.vals[start + j];
-                if (f >= (uint32_t)a.P) {                 // only after an earlier recorded failure
-                    record_error(a.st, GS_ERR_DEVICE_FAULT, 7);
-                    f = 0;
+        const int n = (int)(a.ranges[2 * g + 1] - start);
+        const float px = (float)x + 0.5f;
+        int lst[kPPT];
+        float T[kPPT], Tfin[kPPT], gC0[kPPT], gC1[kPPT], gC2[kPPT], gD[kPPT], gA[kPPT], py[kPPT];
+        float SC0[kPPT], SC1[kPPT], SC2[kPPT], SD[kPPT];
+        int tmax = 0;
+#pragma unroll
+        for (int p = 0; p < kPPT; ++p) {
+            lst[p] = 0;
+            T[p] = 1.0f;
+            gC0[p] = gC1[p] = gC2[p] = gD[p] = gA[p] = 0.f;
+            py[p] = (float)(y0 + p) + 0.5f;
+            if (x < a.W && y0 + p < a.H) {
+                const long long pix = (long long)(y0 + p) * a.W + x;
+                lst[p] = min(max(a.last[(long long)v * HW + pix], 0), n);   // never past the list
+                T[p] = a.finalT[(long long)v * HW + pix];
+                if (a.d_rgb) {
+                    gC0[p] = a.d_rgb[(3 * (long long)v + 0) * HW + pix];
+                    gC1[p] = a.d_rgb[(3 * (long long)v + 1) * HW + pix];
+                    gC2[p] = a.d_rgb[(3 * (long long)v + 2) * HW + pix];
                 }
-                s_f[tid] = f;
-                s_r0[tid] = a.proj[3 * (size_t)f];
-                s_r1[tid] = a.proj[3 * (size_t)f + 1];
-                s_r2[tid] = a.proj[3 * (size_t)f + 2];
+                if (a.d_depth) gD[p] = a.d_depth[(long long)v * HW + pix];
+                if (a.d_alpha) gA[p] = a.d_alpha[(long long)v * HW + pix];
+            }
+            Tfin[p] = T[p];
+            SC0[p] = T[p] * a.bg0;
+            SC1[p] = T[p] * a.bg1;
+            SC2[p] = T[p] * a.bg2;
+            SD[p] = 0.f;
+            pairs += (unsigned long long)lst[p];
+            tmax = max(tmax, lst[p]);
+        }
+        const int wmax = __reduce_max_sync(0xffffffffu, tmax);
+        if (lane == 0) atomicMax(&sm.maxlast, wmax);
+        __syncthreads();
+        const int maxl = sm.maxlast;
+        const int nb = (maxl + NB - 1) / NB;   // batches, back to front: [max(0, maxl-(bi+1)NB), maxl-bi NB)
+        auto issue = [&](int bi, int bb) {
+            const int hi = maxl - bi * NB, lo = max(0, hi - NB);
+            fence_proxy_async_smem();
+            tma_load_1d(&sm.rec[bb][0], a.srec + 3 * (size_t)(start + lo), (uint32_t)(hi - lo) * 48u, &sm.bar[bb]);
+        };
+        if (tid == 0 && nb > 0) issue(0, 0);
+        int buf = 0;
+        for (int bi = 0; bi < nb; ++bi) {
+            const int hi = maxl - bi * NB, lo = max(0, hi - NB), cnt = hi - lo;
+            if (tid == 0 && bi + 1 < nb) issue(bi + 1, buf ^ 1);
+            const bool ok = mbar_wait_bounded(&sm.bar[buf], parity[buf], kTmaWaitLimit);
+            if (__syncthreads_or(!ok)) {
+                const bool pending[2] = {buf == 0 || bi + 1 < nb, buf == 1 || bi + 1 < nb};
+                drain_after_timeout<TW, TH>(sm, parity, pending, a.st);
+                return;
+            }
+            parity[buf] ^= 1u;
+            const float4 *rec = sm.rec[buf];
+#pragma unroll
+            for (int q = 0; q < kPPT; ++q) {
+                const int e = tid + q * NT;
+                if (e < cnt)
+                    sm.mask[buf][e] = (uint8_t)warp_region_mask<TW, TH>(rec[3 * e], rec[3 * e + 1], rec[3 * e + 2].w,
+                                                                        tx * TW, ty * TH);
             }
             __syncthreads();
-            for (int k = hi - lo - 1; k >= 0; --k) {
+            const uint8_t *msk = sm.mask[buf];
+            // entries at or beyond the warp's largest last_idx contribute nothing to this warp
+            const int kend = min(hi, wmax) - lo;
+            for (int k = kend - 1; k >= 0; --k) {
+                if (!(msk[k] & wbit)) continue;       // every pixel of this warp skips the entry
+                const int pos = lo + k;
+                const float4 r0 = rec[3 * k];
+                const float4 r1 = rec[3 * k + 1];
+                const float cut = rec[3 * k + 2].w;
+                const float dx = fp::sub(px, r0.x);
+                float sg[kPPT], dyv[kPPT];
+                bool ev[kPPT];
+#pragma unroll
+                for (int p = 0; p < kPPT; ++p) {
+                    dyv[p] = fp::sub(py[p], r0.y);
+                    sg[p] = spec_sigma(r0.z, r0.w, r1.x, dx, dyv[p]);
+                    ev[p] = pos < lst[p] && !(sg[p] < 0.0f) && !(sg[p] > cut);
+                }
                 float gv[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) gv[c] = 0.f;
                 bool contrib = false;
-                if (lo + k < lst) {
-                    const float4 r0 = s_r0[k];
-                    const float4 r1 = s_r1[k];
-                    const float dx = fp::sub(px, r0.x), dy = fp::sub(py, r0.y);
-                    const float sg = spec_sigma(r0.z, r0.w, r1.x, dx, dy);
-                    if (sg >= 0.0f) {
-                        const float e = spec_expf(-sg);
-                        const float araw = fp::mul(r1.y, e);
-                        const float al = fminf(a.amax, araw);
-                        if (al >= a.amin) {
-                            contrib = true;
-                            const float4 r2 = s_r2[k];
-                            const float oma = 1.0f - al;
-                            const float ioma = 1.0f / oma;
-                            const float Tj = T * ioma;
-                            const float w = al * Tj;
-                            gv[7] = gC0 * w;
-                            gv[8] = gC1 * w;
-                            gv[9] = gC2 * w;
-                            gv[6] = gD * w;
-                            const float dLda = gA * Tfin * ioma + gC0 * (r2.x * Tj - SC0 * ioma) +
-                                               gC1 * (r2.y * Tj - SC1 * ioma) + gC2 * (r2.z * Tj - SC2 * ioma) +
-                                               gD * (r1.z * Tj - SD * ioma);
-                            SC0 += r2.x * w;
-                            SC1 += r2.y * w;
-                            SC2 += r2.z * w;
-                            SD += r1.z * w;
-                            T = Tj;
-                            if (araw <= a.amax) {
-                                gv[5] = dLda * e;
-                                const float dLds = -dLda * al;
-                                gv[2] = 0.5f * dLds * dx * dx;
-                                gv[3] = dLds * dx * dy;
-                                gv[4] = 0.5f * dLds * dy * dy;
-                                gv[0] = -dLds * (r0.z * dx + r0.w * dy);
-                                gv[1] = -dLds * (r0.w * dx + r1.x * dy);
-                            }
+                if (ev[0] || ev[1]) {
+                    float e[kPPT], araw[kPPT];
+#pragma unroll
+                    for (int p = 0; p < kPPT; ++p) {
+                        e[p] = spec_expf(-sg[p]);
+                        araw[p] = fp::mul(r1.y, e[p]);
+                    }
+                    const float4 r2 = rec[3 * k + 2];
+#pragma unroll
+                    for (int p = 0; p < kPPT; ++p) {
+                        const float al = fminf(a.amax, araw[p]);
+                        if (!ev[p] || al < a.amin) continue;
+                        contrib = true;
+                        const float dy = dyv[p];
+                        const float ioma = __fdividef(1.0f, 1.0f - al);
+                        const float Tj = T[p] * ioma;
+                        const float w = al * Tj;
+                        gv[kSR] += gC0[p] * w;
+                        gv[kSG] += gC1[p] * w;
+                        gv[kSBl] += gC2[p] * w;
+                        gv[kSZ] += gD[p] * w;
+                        const float dLda = gA[p] * Tfin[p] * ioma + gC0[p] * (r2.x * Tj - SC0[p] * ioma) +
+                                           gC1[p] * (r2.y * Tj - SC1[p] * ioma) +
+                                           gC2[p] * (r2.z * Tj - SC2[p] * ioma) + gD[p] * (r1.z * Tj - SD[p] * ioma);
+                        SC0[p] += r2.x * w;
+                        SC1[p] += r2.y * w;
+                        SC2[p] += r2.z * w;
+                        SD[p] += r1.z * w;
+                        T[p] = Tj;
+                        if (araw[p] <= a.amax) {
+                            gv[kSO] += dLda * e[p];
+                            const float dLds = -dLda * al;
+                            gv[kSA] += 0.5f * dLds * dx * dx;
+                            gv[kSB] += dLds * dx * dy;
+                            gv[kSC] += 0.5f * dLds * dy * dy;
+                            gv[kSMx] -= dLds * (r0.z * dx + r0.w * dy);
+                            gv[kSMy] -= dLds * (r0.w * dx + r1.x * dy);
                         }
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
                     warp_transpose_reduce16(gv, lane);
-                    if (issuer) atomicAdd(a.g2d + 12 * (size_t)s_f[k] + comp, gv[0]);
+                    const uint32_t f = __float_as_uint(r1.w);
+                    if (issuer) atomicAdd(a.g2d + 12 * (size_t)f + comp, gv[0]);
                 }
             }
+            __syncthreads();                          // buffer reads finished before its refill
+            buf ^= 1;
         }
         __syncthreads();
     }
@@ -275,22 +484,24 @@ static int persistent_grid(F fn, int threads) {
 
 template <int TW, int TH>
 static int fwd_t(const FwdArgs &a, cudaStream_t s) {
-    static int grid = persistent_grid(k_render_fwd<TW, TH>, TW * TH);
+    constexpr int NT = TW * TH / kPPT;
+    static int grid = persistent_grid(k_render_fwd<TW, TH>, NT);
     if (cudaMemsetAsync(&a.st->ctr[kCtrFwd], 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
     if (cudaMemsetAsync(&a.st->fwd_pairs, 0, sizeof(unsigned long long), s) != cudaSuccess) return GS_ERR_CUDA;
     const long long g = std::min<long long>(grid, std::max<long long>(1, a.G));
-    k_render_fwd<TW, TH><<<(unsigned)g, TW * TH, 0, s>>>(a);
+    k_render_fwd<TW, TH><<<(unsigned)g, NT, 0, s>>>(a);
     count_launches(1);
     return check_launch();
 }
 
 template <int TW, int TH>
 static int bwd_t(const BwdArgs &a, cudaStream_t s) {
-    static int grid = persistent_grid(k_render_bwd<TW, TH>, TW * TH);
+    constexpr int NT = TW * TH / kPPT;
+    static int grid = persistent_grid(k_render_bwd<TW, TH>, NT);
     if (cudaMemsetAsync(&a.st->ctr[kCtrBwd], 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
     if (cudaMemsetAsync(&a.st->bwd_pairs, 0, sizeof(unsigned long long), s) != cudaSuccess) return GS_ERR_CUDA;
     const long long g = std::min<long long>(grid, std::max<long long>(1, a.G));
-    k_render_bwd<TW, TH><<<(unsigned)g, TW * TH, 0, s>>>(a);
+    k_render_bwd<TW, TH><<<(unsigned)g, NT, 0, s>>>(a);
     count_launches(1);
     return check_launch();
 }

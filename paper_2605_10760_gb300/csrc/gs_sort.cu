@@ -12,9 +12,12 @@
 //                  stably (warp match_any + per-warp digit counters), publishes its digit counts,
 //                  looks back over its predecessors' counts (bounded spins) and scatters through
 //                  shared memory so that each digit run is written contiguously;
-//   6. k_ranges    [start, end) of every global tile in the sorted keys.
+//   6. k_ranges    [start, end) of every global tile in the sorted keys, and every entry's record
+//                  copied into list order (so a tile's list is one contiguous block for TMA).
 // Depth is positive (z > near > 0), so its float bit pattern orders like its value, and the sort is
 // stable, so equal keys keep the emission order (ascending flattened index).
+#include <algorithm>
+
 #include "gs_kernels.cuh"
 
 namespace gs {
@@ -70,33 +73,43 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(BinArgs a) {
                 if (lane >= o) wi += y;
             }
             if (lane < kScanThreads / 32) s_wsum[lane] = wi - w;   // exclusive warp offsets
-            if (lane == kScanThreads / 32 - 1) {
-                // lane 7 holds the block total: publish and look back
-                const unsigned long long total = wi;
-                unsigned long long prefix = 0;
-                const bool silent = (part == a.fault_scan_part);
-                if (part == 0) {
-                    if (!silent) st_relaxed_u64(a.scan_state, kFlagInc64 | total);
-                } else {
-                    if (!silent) st_relaxed_u64(a.scan_state + part, kFlagAgg64 | total);
-                    long long j = part - 1;
-                    unsigned long long spins = 0;
-                    bool timed_out = false;
-                    while (j >= 0) {
-                        unsigned long long w2 = ld_relaxed_u64(a.scan_state + j);
-                        unsigned long long fl = w2 & ~kVal64;
-                        if (fl == 0) {
-                            if (++spins > a.spin_limit) { timed_out = true; break; }
-                            __nanosleep(100);
-                            continue;
-                        }
-                        prefix += w2 & kVal64;
-                        if (fl == kFlagInc64) break;
-                        --j;
+            const unsigned long long total = __shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
+            const bool silent = (part == a.fault_scan_part);
+            unsigned long long prefix = 0;
+            if (part == 0) {
+                if (lane == 0 && !silent) st_relaxed_u64(a.scan_state, kFlagInc64 | total);
+            } else {
+                if (lane == 0 && !silent) st_relaxed_u64(a.scan_state + part, kFlagAgg64 | total);
+                // warp look-back: lane i reads predecessor j - i; the nearest inclusive word ends it
+                long long j = part - 1;
+                unsigned long long spins = 0;
+                bool timed_out = false;
+                for (;;) {
+                    const long long jj = j - lane;
+                    const unsigned long long w2 = jj >= 0 ? ld_relaxed_u64(a.scan_state + jj) : kFlagInc64;
+                    const unsigned long long fl = w2 & ~kVal64;
+                    const unsigned ready = __ballot_sync(0xffffffffu, fl != 0);
+                    const unsigned inc = __ballot_sync(0xffffffffu, fl == kFlagInc64);
+                    const int first = inc ? __ffs(inc) - 1 : 32;               // nearest inclusive lane
+                    const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
+                    if ((ready & need) == need) {
+                        unsigned long long v = (lane <= first) ? (w2 & kVal64) : 0ull;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        prefix += v;
+                        if (inc) break;
+                        j -= 32;
+                        continue;
                     }
+                    if (++spins > a.spin_limit) { timed_out = true; break; }
+                    __nanosleep(100);
+                }
+                if (lane == 0) {
                     if (timed_out) record_error(a.st, GS_ERR_TIMEOUT, 1);
                     if (!silent) st_relaxed_u64(a.scan_state + part, kFlagInc64 | ((prefix + total) & kVal64));
                 }
+            }
+            if (lane == 0) {
                 s_prefix = prefix;
                 if (part == nparts - 1) {
                     const unsigned long long K = prefix + total;
@@ -229,9 +242,13 @@ struct SweepArgs {
 };
 
 constexpr int kSweepWarps = kSortThreads / 32;
-constexpr size_t kSweepDynSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(uint32_t));
+template <int IPT>
+constexpr size_t sweep_dyn_smem() { return (size_t)kSortThreads * IPT * (sizeof(uint64_t) + sizeof(uint32_t)); }
 
+template <int IPT>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
+    constexpr int kSortIPT = IPT;
+    constexpr int kSortTile = kSortThreads * IPT;
     extern __shared__ __align__(16) unsigned char sw_smem[];
     uint64_t *s_keys = reinterpret_cast<uint64_t *>(sw_smem);
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kSortTile);
@@ -303,20 +320,38 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
         // look back over the predecessors' counts of digit d
         uint32_t excl = 0;
         if (part > 0) {
+            // window of kLookback predecessors loaded together, consumed nearest first until an
+            // inclusive word (done) or a not-yet-published one (wait, then reload from there)
+            constexpr int kLookback = 8;
             int j = (int)part - 1;
             unsigned long long spins = 0;
             bool timed_out = false;
-            while (j >= 0) {
-                const uint32_t w = ld_relaxed_u32(a.state + (size_t)j * 256 + d);
-                const uint32_t fl = w & ~kVal;
-                if (fl == 0u) {
+            for (;;) {
+                uint32_t w[kLookback];
+#pragma unroll
+                for (int q = 0; q < kLookback; ++q)
+                    w[q] = (j - q >= 0) ? ld_relaxed_u32(a.state + (size_t)(j - q) * 256 + d) : kFlagInc;
+                bool found = false, stop = false;
+                int adv = 0;
+#pragma unroll
+                for (int q = 0; q < kLookback; ++q) {
+                    if (!stop) {
+                        const uint32_t fl = w[q] & ~kVal;
+                        if (fl == 0u) {
+                            stop = true;
+                        } else {
+                            excl += w[q] & kVal;
+                            ++adv;
+                            if (fl == kFlagInc) found = stop = true;
+                        }
+                    }
+                }
+                if (found) break;
+                j -= adv;
+                if (stop) {
                     if (++spins > a.spin_limit) { timed_out = true; break; }
                     __nanosleep(64);
-                    continue;
                 }
-                excl += w & kVal;
-                if (fl == kFlagInc) break;
-                --j;
             }
             st_relaxed_u32(my_state, kFlagInc | ((excl + total) & kVal));
             if (timed_out) {
@@ -360,17 +395,26 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
 // ------------------------------------------------------------------------------------------
 // 6. tile ranges
 // ------------------------------------------------------------------------------------------
-__global__ void k_ranges(const uint64_t *keys, DevStatus *st, long long cap, long long G, uint32_t *ranges) {
+__global__ void k_ranges(const uint64_t *keys, const uint32_t *vals, const float4 *proj, float4 *srec, DevStatus *st,
+                         long long cap, long long G, long long P, uint32_t *ranges) {
     const unsigned long long K = min(st->num_keys, (unsigned long long)cap);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < K;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long g = keys[i] >> 32;
-        if (g >= (unsigned long long)G) {            // only after an earlier recorded failure
+        uint32_t f = vals[i];
+        if (g >= (unsigned long long)G || f >= (uint32_t)P) {   // only after an earlier recorded failure
             record_error(st, GS_ERR_DEVICE_FAULT, 5);
             continue;
         }
         if (i == 0 || (keys[i - 1] >> 32) != g) ranges[2 * g] = (uint32_t)i;
         if (i == K - 1 || (keys[i + 1] >> 32) != g) ranges[2 * g + 1] = (uint32_t)(i + 1);
+        // the entry's record in list order, so a tile's batch is one contiguous block;
+        // the radius slot (used only by key emission) carries the pair index instead
+        float4 r1 = proj[3 * (size_t)f + 1];
+        r1.w = __uint_as_float(f);
+        srec[3 * i] = proj[3 * (size_t)f];
+        srec[3 * i + 1] = r1;
+        srec[3 * i + 2] = proj[3 * (size_t)f + 2];
     }
 }
 
@@ -399,6 +443,35 @@ int run_scan_only(const BinArgs &a, cudaStream_t s) {
     return check_launch();
 }
 
+template <int IPT>
+static int sweep_passes(const BinArgs &a, cudaStream_t s) {
+    static bool attr = [] {
+        return cudaFuncSetAttribute((const void *)k_onesweep<IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sweep_dyn_smem<IPT>()) == cudaSuccess;
+    }();
+    if (!attr) return GS_ERR_CUDA;
+    static int occ = occupancy((const void *)k_onesweep<IPT>, kSortThreads, sweep_dyn_smem<IPT>());
+    const int sms = device_sm_count();
+    const long long grid = std::max<long long>(1, std::min<long long>(a.sort_parts, (long long)sms * occ));
+    for (int p = 0; p < a.passes; ++p) {
+        SweepArgs sa;
+        sa.kin = a.keys[p & 1];
+        sa.vin = a.vals[p & 1];
+        sa.kout = a.keys[(p + 1) & 1];
+        sa.vout = a.vals[(p + 1) & 1];
+        sa.digit_off = a.hist + 256 * p;
+        sa.state = a.sort_state + (size_t)256 * a.sort_parts * p;
+        sa.ctr = &a.st->ctr[kCtrSort0 + p];
+        sa.st = a.st;
+        sa.cap = a.cap;
+        sa.shift = 8 * p;
+        sa.spin_limit = a.spin_limit;
+        k_onesweep<IPT><<<(unsigned)grid, kSortThreads, sweep_dyn_smem<IPT>(), s>>>(sa);
+        count_launches(1);
+    }
+    return GS_OK;
+}
+
 int run_bin_sort(const BinArgs &a, cudaStream_t s) {
     // counters of the scan and of every sort pass
     if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t) * (1 + kMaxPasses), s) != cudaSuccess)
@@ -414,34 +487,15 @@ int run_bin_sort(const BinArgs &a, cudaStream_t s) {
     if (cudaMemsetAsync(a.sort_state, 0, sizeof(uint32_t) * 256 * (size_t)a.sort_parts * a.passes, s) != cudaSuccess)
         return GS_ERR_CUDA;
     const int sms = device_sm_count();
-    k_hist<<<sms * 4, 256, 0, s>>>(a);
+    const int hist_grid = (int)std::min<long long>(sms * 4, std::max<long long>(sms, (a.cap + 2047) / 2048));
+    k_hist<<<hist_grid, 256, 0, s>>>(a);
     k_digit_scan<<<a.passes, 256, 0, s>>>(a.hist);
     count_launches(2);
-    static bool attr = [] {
-        return cudaFuncSetAttribute((const void *)k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kSweepDynSmem) == cudaSuccess;
-    }();
-    if (!attr) return GS_ERR_CUDA;
-    static int occ = occupancy((const void *)k_onesweep, kSortThreads, kSweepDynSmem);
-    const long long grid = std::max<long long>(1, std::min<long long>(a.sort_parts, (long long)sms * occ));
-    for (int p = 0; p < a.passes; ++p) {
-        SweepArgs sa;
-        sa.kin = a.keys[p & 1];
-        sa.vin = a.vals[p & 1];
-        sa.kout = a.keys[(p + 1) & 1];
-        sa.vout = a.vals[(p + 1) & 1];
-        sa.digit_off = a.hist + 256 * p;
-        sa.state = a.sort_state + (size_t)256 * a.sort_parts * p;
-        sa.ctr = &a.st->ctr[kCtrSort0 + p];
-        sa.st = a.st;
-        sa.cap = a.cap;
-        sa.shift = 8 * p;
-        sa.spin_limit = a.spin_limit;
-        k_onesweep<<<(unsigned)grid, kSortThreads, kSweepDynSmem, s>>>(sa);
-        count_launches(1);
-    }
+    const int rc2 = a.sort_ipt == kSortIPTSmall ? sweep_passes<kSortIPTSmall>(a, s) : sweep_passes<kSortIPTLarge>(a, s);
+    if (rc2) return rc2;
     if (cudaMemsetAsync(a.ranges, 0, sizeof(uint32_t) * 2 * (size_t)a.G, s) != cudaSuccess) return GS_ERR_CUDA;
-    k_ranges<<<sms * 8, 256, 0, s>>>(a.keys[a.passes & 1], a.st, a.cap, a.G, a.ranges);
+    k_ranges<<<sms * 8, 256, 0, s>>>(a.keys[a.passes & 1], a.vals[a.passes & 1], a.proj, a.srec, a.st, a.cap, a.G,
+                                      a.P, a.ranges);
     count_launches(1);
     return check_launch();
 }

@@ -56,8 +56,9 @@ def test_workspace_size_and_validation(lib):
     n = C.c_size_t()
     pb = _problem()
     assert lib.gs_workspace_size(C.byref(pb), C.byref(n)) == 0
-    # proj + grad2d (48 B each per pair) + keys (2 x 12 B per key) dominate
-    assert 500_000 * 96 + (1 << 21) * 24 < n.value < 500_000 * 140 + (1 << 21) * 40
+    # proj + grad2d (48 B each per pair), keys + values (2 x 12 B per key) and the records in list
+    # order (48 B per key) dominate
+    assert 500_000 * 96 + (1 << 21) * 72 < n.value < 500_000 * 140 + (1 << 21) * 90
     bad = [_problem(V=0), _problem(W=0), _problem(cap=0), _problem(cap=1 << 30), _problem(tile_w=8),
            _problem(alpha_max=1.5), _problem(t_min=0.0), _problem(near_plane=0.0)]
     for b in bad:

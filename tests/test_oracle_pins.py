@@ -320,3 +320,16 @@ def test_finite_differences_all_gradients(seed):
             checked += 1
     assert checked == n * 14 + 6 * V
     assert np.abs(g["pose"]).max() > 0 and np.abs(g["quats"]).max() > 0
+
+
+def test_shared_accumulator_mode_gives_same_gradients(monkeypatch):
+    """The backward's shared atomic accumulator (used for large problems) only reorders FP64 sums."""
+    means, ls, q, o, c, cams, W, H = _tiny_problem(8, n=12, V=2, W=40, H=36)
+    n, V = len(means), len(cams)
+    rng = np.random.default_rng(9)
+    w = (rng.normal(0, 1, (V, 3, H, W)), rng.normal(0, 0.3, (V, H, W)), rng.normal(0, 1, (V, H, W)))
+    a = Oracle(means, ls, q, o, c, cams, [0] * V, [n] * V, W, H).backward(*w)
+    monkeypatch.setenv("GS_ORACLE_SHARED_ACC", "1")
+    b = Oracle(means, ls, q, o, c, cams, [0] * V, [n] * V, W, H).backward(*w)
+    for k in ("g2d", "means", "log_scales", "quats", "opacities", "colors", "pose"):
+        np.testing.assert_allclose(a[k], b[k], rtol=1e-12, atol=1e-15)
