@@ -253,6 +253,48 @@ typedef struct gs_adam_state {
 int gs_adam_step(int64_t n, const gs_adam_state *st, const gs_grads *grads, const float lr[5],
                  int32_t zero_grads, void *stream);
 
+/* ---- joint pose-Gaussian refinement after fusion (Sec. III-C) ---- */
+
+/* Mutable Gaussian arrays, same shapes as gs_gaussians. */
+typedef struct gs_gaussian_arrays {
+    float *means, *log_scales, *quats, *opacities, *colors;
+} gs_gaussian_arrays;
+
+/* Refinement loss of Eq. 23 on the exposure-compensated render I~_v = exp(a_v) I^_v + b_v of each
+ * view (per-keyframe log-gain and bias, Sec. III-C):
+ *   L = w_l1 L1(I~, I) + w_ssim (1 - SSIM(I~, I)) + w_depth L1(D^, D-)
+ * (the paper's alpha' = 1.75, lambda = 0.2, beta = 0.25; its normal term needs a monocular normal
+ * prior and is not computed).  SSIM as in gs_loss_l1_ssim, on I~.  expo [V,2] = (a_v, b_v).
+ * Writes d_rgb = dL/dI^ [V,3,H,W], d_depth = dL/dD^ [V,H,W] (depth, depth_t, d_depth may all be
+ * NULL), d_expo = dL/d(a_v, b_v) [V,2] (may be NULL) and L to *loss (double), all overwritten.
+ * scratch: gs_refine_scratch_size() bytes, 256-byte aligned. */
+size_t gs_refine_scratch_size(int32_t views, int32_t width, int32_t height);
+int gs_loss_refine(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
+                   const float *depth, const float *depth_t, const float *expo, float w_l1, float w_ssim,
+                   float w_depth, float *d_rgb, float *d_depth, float *d_expo, double *loss, void *scratch,
+                   void *stream);
+
+/* Pruning of the refined map (Sec. III-C removes Gaussians with opacity below 0.005): copies the
+ * Gaussians of `in` with opacity >= threshold, in their original order, to `out` (capacity n rows,
+ * must not alias `in`) and writes their number to *kept (device int64).  scratch:
+ * gs_prune_scratch_size(n) bytes, 256-byte aligned.  n < 2^30. */
+size_t gs_prune_scratch_size(int64_t n);
+int gs_prune(int64_t n, const gs_gaussians *in, float threshold, const gs_gaussian_arrays *out, int64_t *kept,
+             void *scratch, void *stream);
+
+/* One bias-corrected Adam step (beta1 0.9, beta2 0.999, eps 1e-15) on each view's pose delta and
+ * exposure (the per-keyframe delta xi_k and (a_k, b_k) of Sec. III-C): gradients pose_grad [V,6]
+ * (from gs_pose_grad) and expo_grad [V,2] (from gs_loss_refine); moments m, v [V,8]; the pose part
+ * of the step is applied to the world-to-camera pose as T <- Exp(delta) T (SE(3) exponential),
+ * the exposure part is added to expo [V,2].  `step` (device int32) is incremented. */
+typedef struct gs_view_adam_state {
+    gs_camera *cameras;
+    float *expo, *m, *v;
+    int32_t *step;
+} gs_view_adam_state;
+int gs_view_adam_step(int32_t views, const gs_view_adam_state *st, const float *pose_grad, const float *expo_grad,
+                      float lr_pose, float lr_expo, void *stream);
+
 /* Zeroes the five gradient arrays of n Gaussians (stream-ordered memsets). */
 int gs_grads_zero(int64_t n, const gs_grads *grads, void *stream);
 

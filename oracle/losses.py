@@ -92,3 +92,62 @@ def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-15):
     mh = m / (1 - beta1 ** step)
     vh = v / (1 - beta2 ** step)
     return param - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def refine_loss(rgb, rgb_t, depth, depth_t, a, b, w_l1=1.75, w_ssim=0.2, w_depth=0.25, fp32_sign=False):
+    """Refinement loss of Eq. 23 on the exposure-compensated render (the normal term needs a
+    monocular normal prior and is not included):
+
+        I~_v = exp(a_v) I^_v + b_v      (per keyframe log-gain a_v and bias b_v, every channel)
+        L = w_l1 L1(I~, I) + w_ssim (1 - SSIM(I~, I)) + w_depth L1(D^, D-)
+
+    with w_l1 = alpha' = 1.75, w_ssim = lambda = 0.2, w_depth = beta = 0.25 (Eq. 4's beta).
+    rgb, rgb_t: [V,3,H,W]; depth, depth_t: [V,H,W] (or None); a, b: [V].
+    fp32_sign: take the sign of the L1 term (a decision) on I~ formed in FP32 as fl(fl(e^a I^) + b)
+    with the decision-chain exponential, the way an FP32 implementation forms it; values stay FP64.
+    Returns (L, dL/drgb, dL/ddepth or None, dL/da [V], dL/db [V])."""
+    rgb = np.asarray(rgb, np.float64)
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    ea = np.exp(a)[:, None, None, None]
+    It = ea * rgb + b[:, None, None, None]
+    L1v, g1 = l1(It, rgb_t)
+    if fp32_sign:
+        from .oracle import expf
+        ea32 = expf(a.astype(np.float32))[:, None, None, None]
+        It32 = (ea32 * np.asarray(rgb, np.float32)).astype(np.float32) + b.astype(np.float32)[:, None, None, None]
+        g1 = np.sign(It32.astype(np.float64) - np.asarray(rgb_t, np.float32)) / It.size
+    S, gs = ssim(It, rgb_t)
+    g_It = w_l1 * g1 - w_ssim * gs
+    L = w_l1 * L1v + w_ssim * (1.0 - S)
+    g_d = None
+    if depth is not None and w_depth != 0.0:
+        Ld, g_d = l1(depth, depth_t)
+        L += w_depth * Ld
+        g_d = g_d * w_depth
+    g_rgb = ea * g_It
+    g_a = (g_It * ea * rgb).sum(axis=(1, 2, 3))
+    g_b = g_It.sum(axis=(1, 2, 3))
+    return L, g_rgb, g_d, g_a, g_b
+
+
+def prune_keep(opacities, threshold=0.005):
+    """Gaussians kept by the refinement's pruning (opacity below 0.005 removed, Sec. III-C), in
+    their original order: the indices i with o_i >= threshold."""
+    o = np.asarray(opacities, np.float32)
+    return np.nonzero(o >= np.float32(threshold))[0]
+
+
+def view_adam_step(cam_row, expo, pose_grad, expo_grad, m, v, step, lr_pose, lr_expo, beta1=0.9, beta2=0.999,
+                   eps=1e-15):
+    """One Adam step on a keyframe's pose delta and exposure (Sec. III-C joint refinement of pose
+    deltas and log-gain / bias): the 8 gradients (rho, phi, a, b) update bias-corrected moments;
+    the pose part of the step, delta, is applied as the left perturbation T <- Exp(delta) T of the
+    world-to-camera pose; the exposure part is added.  Returns (cam_row, expo, m, v)."""
+    from .oracle import exp_se3_left
+    g = np.concatenate([np.asarray(pose_grad, np.float64), np.asarray(expo_grad, np.float64)])
+    m = beta1 * m + (1 - beta1) * g
+    v = beta2 * v + (1 - beta2) * g * g
+    lr = np.array([lr_pose] * 6 + [lr_expo] * 2)
+    d = -lr * (m / (1 - beta1 ** step)) / (np.sqrt(v / (1 - beta2 ** step)) + eps)
+    return exp_se3_left(cam_row, d[:6]), np.asarray(expo, np.float64) + d[6:], m, v

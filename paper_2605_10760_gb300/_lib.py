@@ -76,6 +76,16 @@ class gs_stats(C.Structure):
     _fields_ = [("num_keys", C.c_int64), ("fwd_pairs", C.c_int64), ("bwd_pairs", C.c_int64)]
 
 
+class gs_gaussian_arrays(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacities", C.c_void_p), ("colors", C.c_void_p)]
+
+
+class gs_view_adam_state(C.Structure):
+    _fields_ = [("cameras", C.c_void_p), ("expo", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p),
+                ("step", C.c_void_p)]
+
+
 class gs_adam_state(C.Structure):
     _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity_logits", C.c_void_p), ("opacities", C.c_void_p), ("colors", C.c_void_p),
@@ -106,7 +116,13 @@ _SIGS = {
                                           _P]),
     "gs_adam_step": (C.c_int, [C.c_int64, C.POINTER(gs_adam_state), C.POINTER(gs_grads),
                                C.POINTER(C.c_float), C.c_int32, _P]),
-"gs_grads_zero": (C.c_int, [C.c_int64, C.POINTER(gs_grads), _P]),
+"gs_refine_scratch_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
+    "gs_loss_refine": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P, C.c_float, C.c_float,
+                                 C.c_float, _P, _P, _P, _P, _P, _P]),
+    "gs_prune_scratch_size": (C.c_size_t, [C.c_int64]),
+    "gs_prune": (C.c_int, [C.c_int64, C.POINTER(gs_gaussians), C.c_float, C.POINTER(gs_gaussian_arrays), _P, _P, _P]),
+    "gs_view_adam_step": (C.c_int, [C.c_int32, C.POINTER(gs_view_adam_state), _P, _P, C.c_float, C.c_float, _P]),
+    "gs_grads_zero": (C.c_int, [C.c_int64, C.POINTER(gs_grads), _P]),
     "gs_launch_count": (C.c_int64, []),
     "gs_debug_expf": (C.c_int, [_P, _P, _P, C.c_int64, _P]),
     "gs_debug_scan_scratch_size": (C.c_size_t, [C.c_int64]),

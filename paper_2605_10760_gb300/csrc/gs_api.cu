@@ -396,6 +396,42 @@ int gs_loss_l1_ssim_noalloc(int32_t views, int32_t width, int32_t height, const 
                                        (cudaStream_t)stream);
 }
 
+size_t gs_refine_scratch_size(int32_t views, int32_t width, int32_t height) {
+    if (views < 1 || width < 1 || height < 1) return 0;
+    return refine_scratch_bytes(views, width, height);
+}
+
+int gs_loss_refine(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
+                   const float *depth, const float *depth_t, const float *expo, float w_l1, float w_ssim,
+                   float w_depth, float *d_rgb, float *d_depth, float *d_expo, double *loss, void *scratch,
+                   void *stream) {
+    if (views < 1 || views > GS_MAX_VIEWS || width < 1 || height < 1 || !rgb || !rgb_t || !expo || !d_rgb ||
+        !loss || !ws_ok(scratch))
+        return GS_ERR_INVALID_ARG;
+    if (w_depth != 0.f && (!depth || !depth_t || !d_depth)) return GS_ERR_INVALID_ARG;
+    return launch_loss_refine(views, width, height, rgb, rgb_t, depth, depth_t, expo, w_l1, w_ssim, w_depth, d_rgb,
+                              d_depth, d_expo, loss, scratch, (cudaStream_t)stream);
+}
+
+size_t gs_prune_scratch_size(int64_t n) { return n < 1 ? 0 : prune_scratch_bytes(n); }
+
+int gs_prune(int64_t n, const gs_gaussians *in, float threshold, const gs_gaussian_arrays *out, int64_t *kept,
+             void *scratch, void *stream) {
+    if (n < 1 || n >= (1LL << 30) || !in || !out || !kept || !ws_ok(scratch)) return GS_ERR_INVALID_ARG;
+    if (!in->means || !in->log_scales || !in->quats || !in->opacities || !in->colors || !out->means ||
+        !out->log_scales || !out->quats || !out->opacities || !out->colors)
+        return GS_ERR_INVALID_ARG;
+    return launch_prune(n, *in, threshold, *out, reinterpret_cast<long long *>(kept), scratch, (cudaStream_t)stream);
+}
+
+int gs_view_adam_step(int32_t views, const gs_view_adam_state *st, const float *pose_grad, const float *expo_grad,
+                      float lr_pose, float lr_expo, void *stream) {
+    if (views < 1 || views > GS_MAX_VIEWS || !st || !st->cameras || !st->expo || !st->m || !st->v || !st->step ||
+        !pose_grad || !expo_grad)
+        return GS_ERR_INVALID_ARG;
+    return launch_view_adam(views, *st, pose_grad, expo_grad, lr_pose, lr_expo, (cudaStream_t)stream);
+}
+
 int gs_adam_step(int64_t n, const gs_adam_state *st, const gs_grads *grads, const float lr[5], int32_t zero_grads,
                  void *stream) {
     if (n < 0 || !st || !grads || !lr || !st->step || !st->m || !st->v) return GS_ERR_INVALID_ARG;

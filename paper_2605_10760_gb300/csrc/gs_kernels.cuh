@@ -51,6 +51,7 @@ struct BinArgs {
     float tw, th;
     long long P, cap, sort_parts, max_chunks, G;
     int fault_scan_part;               // -1 normally; >= 0: that scan partition never publishes
+    int zero_for_sort;                 // the scan kernel also clears hist, sort_state and ranges
     unsigned long long spin_limit;
 };
 
@@ -97,6 +98,15 @@ int launch_loss_l1_ssim(int V, int W, int H, const float *rgb, const float *rgb_
                         float *d_rgb, double *loss, void *scratch, cudaStream_t s);
 int launch_loss_l1_ssim_noalloc(int V, int W, int H, const float *rgb, const float *rgb_t, float w_l1,
                                 float w_ssim, float *d_rgb, double *loss, cudaStream_t s);
+size_t refine_scratch_bytes(int V, int W, int H);
+int launch_loss_refine(int V, int W, int H, const float *rgb, const float *rgb_t, const float *depth,
+                       const float *depth_t, const float *expo, float w_l1, float w_ssim, float w_depth, float *d_rgb,
+                       float *d_depth, float *d_expo, double *loss, void *scratch, cudaStream_t s);
+size_t prune_scratch_bytes(long long n);
+int launch_prune(long long n, const gs_gaussians &in, float thr, const gs_gaussian_arrays &out, long long *kept,
+                 void *scratch, cudaStream_t s);
+int launch_view_adam(int V, const gs_view_adam_state &st, const float *pose_grad, const float *expo_grad, float lr_pose,
+                     float lr_expo, cudaStream_t s);
 int launch_adam(long long n, const gs_adam_state &st, const gs_grads &g, const float lr[5], int zero_grads,
                 cudaStream_t s);
 

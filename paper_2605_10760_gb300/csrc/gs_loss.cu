@@ -9,6 +9,7 @@
 //          and combines dSSIM/dx = blur(dS/dmu_x) + 2 x blur(dS/dE[x^2]) + y blur(dS/dE[xy]),
 //          fused with the L1 gradient.
 // Adam: one thread per Gaussian, 14 parameters, bias-corrected, opacity through its logit.
+#include <cstring>
 #include <mutex>
 
 #include "gs_kernels.cuh"
@@ -360,6 +361,337 @@ int launch_adam(long long n, const gs_adam_state &st, const gs_grads &g, const f
     }
     k_step_inc<<<1, 1, 0, s>>>(st.step);
     count_launches(1);
+    return check_launch();
+}
+
+}  // namespace gs
+
+namespace gs {
+
+// ------------------------------------------------------------------------------------------
+// Joint refinement (Sec. III-C, Eq. 23): loss on the exposure-compensated render
+// I~_v = exp(a_v) I^_v + b_v, its gradients with respect to I^, D^ and (a_v, b_v); pruning of
+// Gaussians with opacity below a threshold; Adam on per-view pose deltas and exposures.
+// ------------------------------------------------------------------------------------------
+// I~ is formed as fl(fl(e^a I^) + b) with the decision-chain exponential, so the sign of the L1 term
+// (an FP32 decision) is reproducible by any implementation that follows the same two roundings.
+struct RefineArgs {
+    int V, W, H;
+    const float *rgb, *rgb_t, *depth, *depth_t, *expo;
+    float w_l1, w_ssim, w_depth;
+    float *d_rgb, *d_depth, *d_expo;
+    double *loss;
+    double *sums;          // [0] sum |I~ - I|, [1] sum SSIM map, [2] sum |D^ - D-|, then g_a[V], g_b[V]
+    float *dmu, *dexx, *dexy;
+};
+
+__global__ void k_refine_l1(RefineArgs a) {
+    const long long HWn = (long long)a.W * a.H, total = (long long)a.V * HWn;
+    float acc_rgb = 0.f, acc_d = 0.f;
+    const float sc_d = (float)((double)a.w_depth / (double)total);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long v = i / HWn, p = i - v * HWn;
+        const float ea = spec_expf(a.expo[2 * v]), eb = a.expo[2 * v + 1];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long idx = (3 * v + c) * HWn + p;
+            acc_rgb += fabsf(fp::add(fp::mul(ea, a.rgb[idx]), eb) - a.rgb_t[idx]);
+        }
+        if (a.depth && a.d_depth) {
+            const float d = a.depth[i] - a.depth_t[i];
+            acc_d += fabsf(d);
+            a.d_depth[i] = sgnf(d) * sc_d;
+        }
+    }
+    block_add_double((double)acc_rgb, a.sums);
+    block_add_double((double)acc_d, a.sums + 2);
+}
+
+__global__ void __launch_bounds__(256) k_refine_ssim1(RefineArgs a, SsimTaps tp, float inv_n) {
+    __shared__ float sx[kSI][kSI], sy[kSI][kSI];
+    __shared__ float h[5][kSI][kSB];
+    const int W = a.W, H = a.H;
+    const long long plane = blockIdx.z;
+    const int v = (int)(plane / 3);
+    const float ea = spec_expf(a.expo[2 * v]), eb = a.expo[2 * v + 1];
+    const float *xp = a.rgb + plane * (long long)W * H;
+    const float *yp = a.rgb_t + plane * (long long)W * H;
+    const int x0 = blockIdx.x * kSB - kR, y0 = blockIdx.y * kSB - kR;
+    for (int i = threadIdx.x; i < kSI * kSI; i += 256) {
+        const int r = i / kSI, c = i % kSI;
+        const int gx = x0 + c, gy = y0 + r;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        sx[r][c] = in ? fp::add(fp::mul(ea, xp[(long long)gy * W + gx]), eb) : 0.f;   // zero padding of I~
+        sy[r][c] = in ? yp[(long long)gy * W + gx] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSI * kSB; i += 256) {
+        const int r = i / kSB, c = i % kSB;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const float xv = sx[r][c + k], yv = sy[r][c + k], w = tp.w[k];
+            a0 += w * xv;
+            a1 += w * yv;
+            a2 += w * xv * xv;
+            a3 += w * yv * yv;
+            a4 += w * xv * yv;
+        }
+        h[0][r][c] = a0; h[1][r][c] = a1; h[2][r][c] = a2; h[3][r][c] = a3; h[4][r][c] = a4;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < kSB * kSB; i += 256) {
+        const int r = i / kSB, c = i % kSB;
+        const int gx = blockIdx.x * kSB + c, gy = blockIdx.y * kSB + r;
+        if (gx >= W || gy >= H) continue;
+        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const float w = tp.w[k];
+            mx += w * h[0][r + k][c];
+            my += w * h[1][r + k][c];
+            exx += w * h[2][r + k][c];
+            eyy += w * h[3][r + k][c];
+            exy += w * h[4][r + k][c];
+        }
+        const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
+        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
+        const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+        const float iB = 1.f / (B1 * B2);
+        const float S = A1 * A2 * iB;
+        acc += (double)S;
+        const long long o = plane * (long long)W * H + (long long)gy * W + gx;
+        a.dmu[o] = inv_n * ((2.f * my * A2 - 2.f * my * A1) * iB - S * (2.f * mx / B1 - 2.f * mx / B2));
+        a.dexx[o] = inv_n * (-S / B2);
+        a.dexy[o] = inv_n * (2.f * A1 * iB);
+    }
+    block_add_double(acc, a.sums + 1);
+}
+
+__global__ void __launch_bounds__(256) k_refine_ssim2(RefineArgs a, SsimTaps tp, float l1_scale) {
+    __shared__ float s[3][kSI][kSI];
+    __shared__ float h[3][kSI][kSB];
+    const int W = a.W, H = a.H;
+    const long long plane = blockIdx.z;
+    const int v = (int)(plane / 3);
+    const float ea = spec_expf(a.expo[2 * v]), eb = a.expo[2 * v + 1];
+    const long long off = plane * (long long)W * H;
+    const int x0 = blockIdx.x * kSB - kR, y0 = blockIdx.y * kSB - kR;
+    for (int i = threadIdx.x; i < kSI * kSI; i += 256) {
+        const int r = i / kSI, c = i % kSI;
+        const int gx = x0 + c, gy = y0 + r;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const long long o = off + (long long)gy * W + gx;
+        s[0][r][c] = in ? a.dmu[o] : 0.f;
+        s[1][r][c] = in ? a.dexx[o] : 0.f;
+        s[2][r][c] = in ? a.dexy[o] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSI * kSB; i += 256) {
+        const int r = i / kSB, c = i % kSB;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const float w = tp.w[k];
+            a0 += w * s[0][r][c + k];
+            a1 += w * s[1][r][c + k];
+            a2 += w * s[2][r][c + k];
+        }
+        h[0][r][c] = a0; h[1][r][c] = a1; h[2][r][c] = a2;
+    }
+    __syncthreads();
+    float ga = 0.f, gb = 0.f;
+    for (int i = threadIdx.x; i < kSB * kSB; i += 256) {
+        const int r = i / kSB, c = i % kSB;
+        const int gx = blockIdx.x * kSB + c, gy = blockIdx.y * kSB + r;
+        if (gx >= W || gy >= H) continue;
+        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const float w = tp.w[k];
+            b0 += w * h[0][r + k][c];
+            b1 += w * h[1][r + k][c];
+            b2 += w * h[2][r + k][c];
+        }
+        const long long o = off + (long long)gy * W + gx;
+        const float xv = a.rgb[o], yv = a.rgb_t[o];
+        const float xt = fp::add(fp::mul(ea, xv), eb);       // I~ exactly as the FP32 L1 sign decision takes it
+        const float g = l1_scale * sgnf(xt - yv) - a.w_ssim * (b0 + 2.f * xt * b1 + yv * b2);   // dL/dI~
+        a.d_rgb[o] = ea * g;
+        ga += g * ea * xv;
+        gb += g;
+    }
+    block_add_double((double)ga, a.sums + 3 + v);
+    block_add_double((double)gb, a.sums + 3 + a.V + v);
+}
+
+__global__ void k_refine_finish(RefineArgs a, double inv_n) {
+    const int v = threadIdx.x;
+    if (v == 0) {
+        const double npx = (double)a.V * a.W * a.H;
+        *a.loss = a.w_l1 * a.sums[0] * inv_n + a.w_ssim * (1.0 - a.sums[1] * inv_n) + a.w_depth * a.sums[2] / npx;
+    }
+    if (v < a.V && a.d_expo) {
+        a.d_expo[2 * v] = (float)a.sums[3 + v];
+        a.d_expo[2 * v + 1] = (float)a.sums[3 + a.V + v];
+    }
+}
+
+size_t refine_scratch_bytes(int V, int W, int H) {
+    const size_t head = ((size_t)(3 + 2 * V) * sizeof(double) + 255) & ~(size_t)255;
+    return head + 3 * sizeof(float) * (size_t)V * 3 * W * H;
+}
+
+int launch_loss_refine(int V, int W, int H, const float *rgb, const float *rgb_t, const float *depth,
+                       const float *depth_t, const float *expo, float w_l1, float w_ssim, float w_depth, float *d_rgb,
+                       float *d_depth, float *d_expo, double *loss, void *scratch, cudaStream_t s) {
+    static const SsimTaps taps = make_taps();
+    const long long plane = (long long)W * H, n = 3LL * V * plane;
+    const size_t head = ((size_t)(3 + 2 * V) * sizeof(double) + 255) & ~(size_t)255;
+    RefineArgs a;
+    a.V = V; a.W = W; a.H = H;
+    a.rgb = rgb; a.rgb_t = rgb_t; a.depth = depth; a.depth_t = depth_t; a.expo = expo;
+    a.w_l1 = w_l1; a.w_ssim = w_ssim; a.w_depth = (depth && depth_t && d_depth) ? w_depth : 0.f;
+    a.d_rgb = d_rgb; a.d_depth = (depth && depth_t) ? d_depth : nullptr; a.d_expo = d_expo;
+    a.loss = loss;
+    a.sums = reinterpret_cast<double *>(scratch);
+    a.dmu = reinterpret_cast<float *>(static_cast<char *>(scratch) + head);
+    a.dexx = a.dmu + n;
+    a.dexy = a.dexx + n;
+    if (cudaMemsetAsync(a.sums, 0, (size_t)(3 + 2 * V) * sizeof(double), s) != cudaSuccess) return GS_ERR_CUDA;
+    const float inv_n = (float)(1.0 / (double)n);
+    const long long total = (long long)V * plane;
+    const int g1 = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, (long long)device_sm_count() * 8));
+    k_refine_l1<<<g1, 256, 0, s>>>(a);
+    dim3 grid((W + kSB - 1) / kSB, (H + kSB - 1) / kSB, 3 * V);
+    k_refine_ssim1<<<grid, 256, 0, s>>>(a, taps, inv_n);
+    k_refine_ssim2<<<grid, 256, 0, s>>>(a, taps, w_l1 * inv_n);
+    k_refine_finish<<<1, ((V + 31) / 32) * 32, 0, s>>>(a, 1.0 / (double)n);
+    count_launches(4);
+    return check_launch();
+}
+
+// ---- pruning: order-preserving compaction of the Gaussians with opacity >= threshold ----
+__global__ void k_prune_flags(long long n, const float *op, float thr, uint32_t *flags) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        flags[i] = op[i] >= thr ? 1u : 0u;
+}
+
+__global__ void k_prune_scatter(long long n, gs_gaussians in, gs_gaussian_arrays out, const uint32_t *incl,
+                                long long *kept) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t hi = incl[i], lo = i > 0 ? incl[i - 1] : 0u;
+        if (i == n - 1) *kept = (long long)hi;
+        if (hi == lo) continue;
+        const long long j = hi - 1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            out.means[3 * j + k] = in.means[3 * i + k];
+            out.log_scales[3 * j + k] = in.log_scales[3 * i + k];
+            out.colors[3 * j + k] = in.colors[3 * i + k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out.quats[4 * j + k] = in.quats[4 * i + k];
+        out.opacities[j] = in.opacities[i];
+    }
+}
+
+size_t prune_scratch_bytes(long long n) {
+    const long long parts = (n + kScanTile - 1) / kScanTile;
+    return 256 + (((size_t)n * 4 + 255) & ~(size_t)255) + (size_t)parts * 8;
+}
+
+int launch_prune(long long n, const gs_gaussians &in, float thr, const gs_gaussian_arrays &out, long long *kept,
+                 void *scratch, cudaStream_t s) {
+    BinArgs b;
+    std::memset(&b, 0, sizeof(b));
+    b.st = reinterpret_cast<DevStatus *>(scratch);
+    b.touched = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + 256);
+    b.scan_state = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 256 +
+                                                          (((size_t)n * 4 + 255) & ~(size_t)255));
+    b.P = n;
+    b.cap = (1LL << 30) - 1;
+    b.fault_scan_part = -1;
+    b.spin_limit = kSpinLimit;
+    if (cudaMemsetAsync(b.st, 0, sizeof(DevStatus), s) != cudaSuccess) return GS_ERR_CUDA;
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)device_sm_count() * 8));
+    k_prune_flags<<<grid, 256, 0, s>>>(n, in.opacities, thr, b.touched);
+    count_launches(1);
+    int rc = run_scan_only(b, s);
+    if (rc) return rc;
+    k_prune_scatter<<<grid, 256, 0, s>>>(n, in, out, b.touched, kept);
+    count_launches(1);
+    return check_launch();
+}
+
+// ---- per-view Adam on the pose delta (applied as T <- Exp(delta) T) and the exposure ----
+__global__ void k_view_adam(int V, gs_camera *cams, float *expo, float *m, float *vv, const int32_t *step,
+                            const float *pose_grad, const float *expo_grad, float lr_pose, float lr_expo) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int t = *step + 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-15f;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    float d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float g = k < 6 ? pose_grad[6 * v + k] : expo_grad[2 * v + (k - 6)];
+        const float mm = b1 * m[8 * v + k] + (1.f - b1) * g;
+        const float vk = b2 * vv[8 * v + k] + (1.f - b2) * g * g;
+        m[8 * v + k] = mm;
+        vv[8 * v + k] = vk;
+        d[k] = -(k < 6 ? lr_pose : lr_expo) * (mm / c1) / (sqrtf(vk / c2) + eps);
+    }
+    expo[2 * v] += d[6];
+    expo[2 * v + 1] += d[7];
+    // Exp of the twist (rho = d[0..2], phi = d[3..5]): Rodrigues rotation and left Jacobian
+    const float px = d[3], py = d[4], pz = d[5];
+    const float th2 = px * px + py * py + pz * pz, th = sqrtf(th2);
+    float A, B, Cc;   // Exp(phi) = I + A K + B K^2 ; Jl = I + B K + Cc K^2
+    if (th < 1e-4f) {
+        A = 1.f - th2 / 6.f;
+        B = 0.5f - th2 / 24.f;
+        Cc = 1.f / 6.f - th2 / 120.f;
+    } else {
+        A = sinf(th) / th;
+        B = (1.f - cosf(th)) / th2;
+        Cc = (th - sinf(th)) / (th2 * th);
+    }
+    const float K[9] = {0.f, -pz, py, pz, 0.f, -px, -py, px, 0.f};
+    float K2[9], Rx[9], Jl[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float I = (i % 4 == 0) ? 1.f : 0.f;
+        Rx[i] = I + A * K[i] + B * K2[i];
+        Jl[i] = I + B * K[i] + Cc * K2[i];
+    }
+    gs_camera c = cams[v];
+    float R[9], tt[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) R[3 * i + j] = Rx[3 * i] * c.R[j] + Rx[3 * i + 1] * c.R[3 + j] + Rx[3 * i + 2] * c.R[6 + j];
+        tt[i] = Rx[3 * i] * c.t[0] + Rx[3 * i + 1] * c.t[1] + Rx[3 * i + 2] * c.t[2] + Jl[3 * i] * d[0] +
+                Jl[3 * i + 1] * d[1] + Jl[3 * i + 2] * d[2];
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) c.R[i] = R[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c.t[i] = tt[i];
+    cams[v] = c;
+}
+
+int launch_view_adam(int V, const gs_view_adam_state &st, const float *pose_grad, const float *expo_grad, float lr_pose,
+                     float lr_expo, cudaStream_t s) {
+    k_view_adam<<<(V + 127) / 128, 128, 0, s>>>(V, st.cameras, st.expo, st.m, st.v, st.step, pose_grad, expo_grad,
+                                                 lr_pose, lr_expo);
+    k_step_inc<<<1, 1, 0, s>>>(st.step);
+    count_launches(2);
     return check_launch();
 }
 

@@ -18,8 +18,9 @@
 // e^x), so every decision is exactly the one the full test takes.
 //
 // Backward: from final_T and last_idx of each pixel the CTA walks the list back to front,
-// recovering T_j = T_{j+1} / (1 - alpha_j) and the colour / depth accumulated behind each entry, so
-// no per-pixel list is stored.  Each thread sums the 10 per-Gaussian gradient components of its two
+// recovering T_j = T_{j+1} / (1 - alpha_j) and one running scalar Q (the upstream-weighted colour
+// and depth accumulated behind each entry, with the background and alpha-output terms), so no
+// per-pixel list is stored.  Each thread sums the 10 per-Gaussian gradient components of its two
 // pixels, then the warp reduces them with a transposed butterfly (16 shuffles instead of 50) after
 // which 10 lanes issue one atomic add each: a (Gaussian, warp) pair costs one warp-wide atomic
 // instruction; warps whose 64 pixels all skip the entry issue nothing, and entries past the
@@ -337,14 +338,17 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
         const int n = (int)(a.ranges[2 * g + 1] - start);
         const float px = (float)x + 0.5f;
         int lst[kPPT];
-        float T[kPPT], Tfin[kPPT], gC0[kPPT], gC1[kPPT], gC2[kPPT], gD[kPPT], gA[kPPT], py[kPPT];
-        float SC0[kPPT], SC1[kPPT], SC2[kPPT], SD[kPPT];
+        float T[kPPT], gC0[kPPT], gC1[kPPT], gC2[kPPT], gD[kPPT], py[kPPT];
+        // Q = sum over blended entries behind the current one of (gC . c + gD z) alpha T, plus the
+        // background and alpha-output terms: dL/dalpha_j = T_j (gC . c_j + gD z_j) - Q / (1 - alpha_j)
+        float Q[kPPT];
         int tmax = 0;
 #pragma unroll
         for (int p = 0; p < kPPT; ++p) {
             lst[p] = 0;
             T[p] = 1.0f;
-            gC0[p] = gC1[p] = gC2[p] = gD[p] = gA[p] = 0.f;
+            gC0[p] = gC1[p] = gC2[p] = gD[p] = 0.f;
+            float gA = 0.f;
             py[p] = (float)(y0 + p) + 0.5f;
             if (x < a.W && y0 + p < a.H) {
                 const long long pix = (long long)(y0 + p) * a.W + x;
@@ -356,13 +360,10 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
                     gC2[p] = a.d_rgb[(3 * (long long)v + 2) * HW + pix];
                 }
                 if (a.d_depth) gD[p] = a.d_depth[(long long)v * HW + pix];
-                if (a.d_alpha) gA[p] = a.d_alpha[(long long)v * HW + pix];
+                if (a.d_alpha) gA = a.d_alpha[(long long)v * HW + pix];
             }
-            Tfin[p] = T[p];
-            SC0[p] = T[p] * a.bg0;
-            SC1[p] = T[p] * a.bg1;
-            SC2[p] = T[p] * a.bg2;
-            SD[p] = 0.f;
+            // rgb = sum c alpha T + T_final bg, alpha_out = 1 - T_final
+            Q[p] = T[p] * (gC0[p] * a.bg0 + gC1[p] * a.bg1 + gC2[p] * a.bg2 - gA);
             pairs += (unsigned long long)lst[p];
             tmax = max(tmax, lst[p]);
         }
@@ -440,13 +441,9 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
                         gv[kSG] += gC1[p] * w;
                         gv[kSBl] += gC2[p] * w;
                         gv[kSZ] += gD[p] * w;
-                        const float dLda = gA[p] * Tfin[p] * ioma + gC0[p] * (r2.x * Tj - SC0[p] * ioma) +
-                                           gC1[p] * (r2.y * Tj - SC1[p] * ioma) +
-                                           gC2[p] * (r2.z * Tj - SC2[p] * ioma) + gD[p] * (r1.z * Tj - SD[p] * ioma);
-                        SC0[p] += r2.x * w;
-                        SC1[p] += r2.y * w;
-                        SC2[p] += r2.z * w;
-                        SD[p] += r1.z * w;
+                        const float Pj = gC0[p] * r2.x + gC1[p] * r2.y + gC2[p] * r2.z + gD[p] * r1.z;
+                        const float dLda = Tj * Pj - Q[p] * ioma;
+                        Q[p] += Pj * w;
                         T[p] = Tj;
                         if (araw[p] <= a.amax) {
                             gv[kSO] += dLda * e[p];

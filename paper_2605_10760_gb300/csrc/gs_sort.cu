@@ -6,8 +6,9 @@
 //   2. k_emit      one key (global tile << 32 | float bits of depth) per touched tile, tiles in
 //                  row-major order, value = flattened (view, Gaussian) index; also clears that
 //                  pair's backward accumulator;
-//   3. k_hist      digit histograms of every 8-bit pass in one read of the keys;
-//   4. k_digit_scan exclusive scan of each pass's 256 digit counts;
+//   3. k_hist      digit histograms of every 8-bit pass in one read of the keys (the scan kernel
+//                  cleared the histograms, look-back words and ranges beforehand);
+//   4. (each onesweep CTA turns its pass's histogram into digit start offsets itself);
 //   5. k_onesweep  one launch per pass: each CTA claims the next partition of 4096 keys, ranks them
 //                  stably (warp match_any + per-warp digit counters), publishes its digit counts,
 //                  looks back over its predecessors' counts (bounded spins) and scatters through
@@ -34,6 +35,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(BinArgs a) {
     __shared__ unsigned long long s_prefix;
     const long long nparts = (a.P + kScanTile - 1) / kScanTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (a.zero_for_sort) {
+        // clear what the later binning kernels accumulate into (they run after this kernel)
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        for (long long i = t0; i < (long long)kMaxPasses * 256; i += stride) a.hist[i] = 0u;
+        const long long ns = 256LL * a.sort_parts * a.passes / 4;
+        uint4 *ss = reinterpret_cast<uint4 *>(a.sort_state);
+        for (long long i = t0; i < ns; i += stride) ss[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (long long i = t0; i < 2 * a.G; i += stride) a.ranges[i] = 0u;
+    }
     for (;;) {
         if (threadIdx.x == 0) s_part = atomicAdd(&a.st->ctr[kCtrScan], 1u);
         __syncthreads();
@@ -206,24 +217,6 @@ __global__ void __launch_bounds__(256) k_hist(BinArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_digit_scan(uint32_t *hist) {
-    __shared__ uint32_t s_w[8];
-    uint32_t *h = hist + blockIdx.x * 256;
-    const uint32_t x = h[threadIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    uint32_t off = 0;
-    for (int w = 0; w < warp; ++w) off += s_w[w];
-    h[threadIdx.x] = off + incl - x;
-}
-
 // ------------------------------------------------------------------------------------------
 // 5. onesweep pass
 // ------------------------------------------------------------------------------------------
@@ -232,7 +225,7 @@ struct SweepArgs {
     const uint32_t *vin;
     uint64_t *kout;
     uint32_t *vout;
-    const uint32_t *digit_off;   // [256] exclusive global digit starts of this pass
+    const uint32_t *hist;        // [256] digit counts of this pass over all keys
     uint32_t *state;             // [parts][256]
     uint32_t *ctr;
     DevStatus *st;
@@ -258,6 +251,24 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
     __shared__ uint32_t s_wsum[kSweepWarps];
     __shared__ uint32_t s_part;
     __shared__ int s_bad;
+    __shared__ uint32_t s_goff[256];      // exclusive global start of each digit in this pass
+    {
+        // exclusive scan of the pass's 256 digit counts, once per CTA
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const uint32_t c = a.hist[threadIdx.x];
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_tstart[warp] = incl;   // scratch: per-warp totals
+        __syncthreads();
+        uint32_t off = 0;
+        for (int w = 0; w < warp; ++w) off += s_tstart[w];
+        s_goff[threadIdx.x] = off + incl - c;
+        __syncthreads();
+    }
     const unsigned long long Kll = min(a.st->num_keys, (unsigned long long)a.cap);
     const uint32_t K = (uint32_t)Kll;
     const uint32_t nparts = (K + kSortTile - 1) / kSortTile;
@@ -364,7 +375,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
         for (int w = 0; w < warp; ++w) woff += s_wsum[w];
         const uint32_t tstart = woff + incl - total;
         s_tstart[d] = tstart;
-        s_gbase[d] = a.digit_off[d] + excl - tstart;
+        s_gbase[d] = s_goff[d] + excl - tstart;
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kSortIPT; ++r) {
@@ -459,7 +470,7 @@ static int sweep_passes(const BinArgs &a, cudaStream_t s) {
         sa.vin = a.vals[p & 1];
         sa.kout = a.keys[(p + 1) & 1];
         sa.vout = a.vals[(p + 1) & 1];
-        sa.digit_off = a.hist + 256 * p;
+        sa.hist = a.hist + 256 * p;
         sa.state = a.sort_state + (size_t)256 * a.sort_parts * p;
         sa.ctr = &a.st->ctr[kCtrSort0 + p];
         sa.st = a.st;
@@ -476,24 +487,25 @@ int run_bin_sort(const BinArgs &a, cudaStream_t s) {
     // counters of the scan and of every sort pass
     if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t) * (1 + kMaxPasses), s) != cudaSuccess)
         return GS_ERR_CUDA;
-    int rc = run_scan_only(a, s);
+    BinArgs sa = a;
+    sa.zero_for_sort = 1;                 // the scan also clears hist, look-back state and ranges
+    if (a.P == 0) {
+        if (cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, s) != cudaSuccess) return GS_ERR_CUDA;
+        if (cudaMemsetAsync(a.ranges, 0, sizeof(uint32_t) * 2 * (size_t)a.G, s) != cudaSuccess) return GS_ERR_CUDA;
+    }
+    int rc = run_scan_only(sa, s);
     if (rc) return rc;
     if (a.P > 0) {
         dim3 grid((unsigned)a.max_chunks, (unsigned)a.V);
         k_emit<<<grid, kChunk, 0, s>>>(a);
         count_launches(1);
     }
-    if (cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, s) != cudaSuccess) return GS_ERR_CUDA;
-    if (cudaMemsetAsync(a.sort_state, 0, sizeof(uint32_t) * 256 * (size_t)a.sort_parts * a.passes, s) != cudaSuccess)
-        return GS_ERR_CUDA;
     const int sms = device_sm_count();
     const int hist_grid = (int)std::min<long long>(sms * 4, std::max<long long>(sms, (a.cap + 2047) / 2048));
     k_hist<<<hist_grid, 256, 0, s>>>(a);
-    k_digit_scan<<<a.passes, 256, 0, s>>>(a.hist);
-    count_launches(2);
+    count_launches(1);
     const int rc2 = a.sort_ipt == kSortIPTSmall ? sweep_passes<kSortIPTSmall>(a, s) : sweep_passes<kSortIPTLarge>(a, s);
     if (rc2) return rc2;
-    if (cudaMemsetAsync(a.ranges, 0, sizeof(uint32_t) * 2 * (size_t)a.G, s) != cudaSuccess) return GS_ERR_CUDA;
     k_ranges<<<sms * 8, 256, 0, s>>>(a.keys[a.passes & 1], a.vals[a.passes & 1], a.proj, a.srec, a.st, a.cap, a.G,
                                       a.P, a.ranges);
     count_launches(1);

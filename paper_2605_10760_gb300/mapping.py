@@ -119,3 +119,54 @@ def autotune(make_problem, g: R.Gaussians, rgb_target, candidates=((16, 16), (16
         data[cache_key] = {"pick": pick, "table": table, "when": time.time()}
         json.dump(data, open(_CACHE, "w"), indent=1)
     return pick["tile"][0], pick["tile"][1], pick["ms_per_iter"], table
+
+
+class RefineLoop:
+    """Joint pose-Gaussian photometric refinement of a fused map (Sec. III-C): each iteration
+    renders every keyframe, evaluates Eq. 23 on the exposure-compensated render
+    (w_l1 = 1.75, w_ssim = 0.2, w_depth = 0.25), back-propagates to the Gaussians (Adam at half the
+    per-agent learning rates) and to each keyframe's pose delta and exposure (per-view Adam, pose
+    applied as T <- Exp(delta) T).  Iterations are graph-capturable like MappingLoop; pruning of
+    Gaussians with opacity below 0.005 is a separate call (`prune`) that rebuilds the problem."""
+
+    def __init__(self, problem: R.Problem, g: R.Gaussians, rgb_target, depth_target=None,
+                 lr=(0.8e-4, 2.5e-3, 0.5e-3, 2.5e-2, 1.25e-3), lr_pose=1e-4, lr_expo=1e-3,
+                 w_l1=1.75, w_ssim=0.2, w_depth=0.25, headroom=2.0):
+        self.pb, self.g = problem, g
+        self.rgb_t = rgb_target.contiguous()
+        self.depth_t = None if depth_target is None else depth_target.contiguous()
+        self.w = (float(w_l1), float(w_ssim), float(w_depth) if depth_target is not None else 0.0)
+        self.adam = R.AdamState(g, lr)
+        self.view = R.ViewAdamState(problem, lr_pose, lr_expo)
+        self.grads = R.zeros_like_grads(g)
+        self.img = problem.alloc_image()
+        V, H, W = problem.V, problem.H, problem.W
+        dev = g.means.device
+        self.d_rgb = torch.empty_like(self.img["rgb"])
+        self.d_depth = torch.empty_like(self.img["depth"]) if depth_target is not None else None
+        self.d_expo = torch.zeros(V, 2, device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.pose = torch.zeros(V, 6, device=dev)
+        self.scratch = R.refine_scratch(V, H, W, dev)
+        self.graph = None
+        problem.forward_checked(g, self.img)
+        torch.cuda.synchronize()
+        want = int(problem.stats()["num_keys"] * headroom) + 4096
+        if want > problem.cap:
+            problem.set_capacity(want)
+
+    def iteration(self):
+        pb = self.pb
+        pb.project(self.g)
+        pb.bin_sort()
+        pb.render_fwd(self.img)
+        R.loss_refine(self.img["rgb"], self.rgb_t, self.view.expo, self.img["depth"], self.depth_t, *self.w,
+                      d_rgb=self.d_rgb, d_depth=self.d_depth, d_expo=self.d_expo, loss=self.loss,
+                      scratch=self.scratch)
+        pb.render_bwd(self.g, self.img, self.d_rgb, self.d_depth, None, self.grads)
+        pb.pose_grad(self.pose)
+        self.adam.apply(self.grads, zero_grads=True)
+        self.view.apply(self.pose, self.d_expo)
+
+    capture = MappingLoop.capture
+    replay = MappingLoop.replay

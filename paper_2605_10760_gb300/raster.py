@@ -311,3 +311,68 @@ def rasterize(means, log_scales, quats, opacities, colors, problem: Problem, pos
     if pose_delta is None:
         pose_delta = torch.zeros(problem.V, 6, device=means.device, requires_grad=False)
     return _Rasterize.apply(means, log_scales, quats, opacities, colors, pose_delta, problem)
+
+
+# ------------------------------------------------------------------------------------------
+# joint refinement (exposure-compensated loss, pruning, per-view pose / exposure Adam)
+# ------------------------------------------------------------------------------------------
+
+def refine_scratch(V, H, W, device="cuda") -> torch.Tensor:
+    n = L.load().gs_refine_scratch_size(V, W, H)
+    return torch.empty(int(n), dtype=torch.uint8, device=device)
+
+
+def loss_refine(rgb, rgb_t, expo, depth=None, depth_t=None, w_l1=1.75, w_ssim=0.2, w_depth=0.25,
+                d_rgb=None, d_depth=None, d_expo=None, loss=None, scratch=None):
+    """Eq. 23 on I~ = exp(a) I^ + b.  Returns (loss, d_rgb, d_depth, d_expo)."""
+    V, _, H, W = rgb.shape
+    dev = rgb.device
+    d_rgb = d_rgb if d_rgb is not None else torch.empty_like(rgb)
+    use_d = depth is not None and w_depth != 0.0
+    if use_d and d_depth is None:
+        d_depth = torch.empty_like(depth)
+    d_expo = d_expo if d_expo is not None else torch.empty(V, 2, device=dev)
+    loss = loss if loss is not None else torch.zeros(1, dtype=torch.float64, device=dev)
+    scratch = scratch if scratch is not None else refine_scratch(V, H, W, dev)
+    L.check(L.load().gs_loss_refine(V, W, H, _ptr(rgb), _ptr(rgb_t), _ptr(depth) if use_d else None,
+                                    _ptr(depth_t) if use_d else None, _ptr(expo), float(w_l1), float(w_ssim),
+                                    float(w_depth) if use_d else 0.0, _ptr(d_rgb), _ptr(d_depth) if use_d else None,
+                                    _ptr(d_expo), _ptr(loss), _ptr(scratch), _stream()), "gs_loss_refine")
+    return loss, d_rgb, d_depth, d_expo
+
+
+def prune(g: Gaussians, threshold=0.005) -> Gaussians:
+    """Gaussians with opacity >= threshold, in order (the refinement's pruning).  Syncs to read the count."""
+    n = g.n
+    out = Gaussians(*[torch.empty_like(getattr(g, k)) for k in ("means", "log_scales", "quats", "opacities",
+                                                                 "colors")])
+    kept = torch.zeros(1, dtype=torch.int64, device=g.means.device)
+    scratch = torch.empty(int(L.load().gs_prune_scratch_size(n)), dtype=torch.uint8, device=g.means.device)
+    gi = g.struct()
+    go = L.gs_gaussian_arrays(*[getattr(out, k).data_ptr() for k in ("means", "log_scales", "quats", "opacities",
+                                                                      "colors")])
+    L.check(L.load().gs_prune(n, C.byref(gi), float(threshold), C.byref(go), _ptr(kept), _ptr(scratch), _stream()),
+            "gs_prune")
+    k = int(kept.item())
+    return Gaussians(*[getattr(out, f)[:k].contiguous() for f in ("means", "log_scales", "quats", "opacities",
+                                                                   "colors")])
+
+
+class ViewAdamState:
+    """Adam over each view's pose delta (applied to the problem's cameras as T <- Exp(delta) T) and
+    exposure (a, b)."""
+
+    def __init__(self, problem: Problem, lr_pose=1e-4, lr_expo=1e-3):
+        dev = problem.device
+        self.pb = problem
+        self.expo = torch.zeros(problem.V, 2, device=dev)
+        self.m = torch.zeros(problem.V, 8, device=dev)
+        self.v = torch.zeros(problem.V, 8, device=dev)
+        self.step = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.lr_pose, self.lr_expo = float(lr_pose), float(lr_expo)
+
+    def apply(self, pose_grad: torch.Tensor, expo_grad: torch.Tensor):
+        st = L.gs_view_adam_state(self.pb.cameras.data_ptr(), self.expo.data_ptr(), self.m.data_ptr(),
+                                  self.v.data_ptr(), self.step.data_ptr())
+        L.check(L.load().gs_view_adam_step(self.pb.V, C.byref(st), _ptr(pose_grad), _ptr(expo_grad), self.lr_pose,
+                                           self.lr_expo, _stream()), "gs_view_adam_step")

@@ -93,3 +93,35 @@ def test_adam_vs_torch(steps):
         pt.grad = torch.tensor(g)
         opt.step()
     np.testing.assert_allclose(p, pt.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_refine_loss_gradients_vs_autograd():
+    """Exposure-compensated refinement loss (Eq. 23): every gradient against torch.autograd."""
+    rng = np.random.default_rng(4)
+    V, H, W = 2, 18, 23
+    rgb, tgt = rng.uniform(0, 1, (V, 3, H, W)), rng.uniform(0, 1, (V, 3, H, W))
+    d, dt = rng.uniform(1, 4, (V, H, W)), rng.uniform(1, 4, (V, H, W))
+    a, b = rng.normal(0, 0.2, V), rng.normal(0, 0.05, V)
+    Lv, g_rgb, g_d, g_a, g_b = L.refine_loss(rgb, tgt, d, dt, a, b)
+    t = lambda x: torch.tensor(x, requires_grad=True)
+    rt, dtt, at, bt = t(rgb), t(d), t(a), t(b)
+    It = torch.exp(at)[:, None, None, None] * rt + bt[:, None, None, None]
+    yt = torch.tensor(tgt)
+    Lt = (1.75 * (It - yt).abs().mean() + 0.2 * (1 - _torch_ssim(It, yt))
+          + 0.25 * (dtt - torch.tensor(dt)).abs().mean())
+    Lt.backward()
+    assert abs(Lv - Lt.item()) < 1e-12
+    np.testing.assert_allclose(g_rgb, rt.grad.numpy(), rtol=1e-9, atol=1e-15)
+    np.testing.assert_allclose(g_d, dtt.grad.numpy(), rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(g_a, at.grad.numpy(), rtol=1e-9)
+    np.testing.assert_allclose(g_b, bt.grad.numpy(), rtol=1e-9)
+    # zero exposure reduces to the plain loss terms
+    L0, g0, _, _, _ = L.refine_loss(rgb, tgt, None, None, np.zeros(V), np.zeros(V), 1.75, 0.2, 0.0)
+    Lp, gp = L.l1_ssim_loss(rgb, tgt, 1.75, 0.2)
+    assert abs(L0 - Lp) < 1e-14
+    np.testing.assert_allclose(g0, gp, rtol=1e-14)
+
+
+def test_prune_keep_threshold():
+    o = np.array([0.5, 0.004, 0.005, 0.0049999, 1.0, 0.0], np.float32)
+    assert list(L.prune_keep(o)) == [0, 2, 4]

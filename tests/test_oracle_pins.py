@@ -333,3 +333,26 @@ def test_shared_accumulator_mode_gives_same_gradients(monkeypatch):
     b = Oracle(means, ls, q, o, c, cams, [0] * V, [n] * V, W, H).backward(*w)
     for k in ("g2d", "means", "log_scales", "quats", "opacities", "colors", "pose"):
         np.testing.assert_allclose(a[k], b[k], rtol=1e-12, atol=1e-15)
+
+
+def test_exp_se3_left_matches_matrix_exponential():
+    """The SE(3) left update T <- Exp(xi) T equals scipy's matrix exponential of the twist."""
+    from scipy.linalg import expm
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        Rm = exp_se3_left(np.concatenate([np.eye(3).ravel(), [0, 0, 0], [1, 1, 1, 1]]),
+                          np.concatenate([[0, 0, 0], rng.normal(0, 1, 3)]))[:9].reshape(3, 3)
+        cam = np.concatenate([Rm.ravel(), rng.normal(0, 1, 3), [500, 500, 320, 240]])
+        xi = rng.normal(0, 0.7, 6)
+        rho, phi = xi[:3], xi[3:]
+        Xi = np.zeros((4, 4))
+        Xi[:3, :3] = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
+        Xi[:3, 3] = rho
+        T = np.eye(4)
+        T[:3, :3] = cam[:9].reshape(3, 3)
+        T[:3, 3] = cam[9:12]
+        Tn = expm(Xi) @ T
+        out = exp_se3_left(cam, xi)
+        np.testing.assert_allclose(out[:9].reshape(3, 3), Tn[:3, :3], atol=1e-12)
+        np.testing.assert_allclose(out[9:12], Tn[:3, 3], atol=1e-12)
+        np.testing.assert_array_equal(out[12:], cam[12:])
