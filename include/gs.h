@@ -253,6 +253,13 @@ typedef struct gs_adam_state {
 int gs_adam_step(int64_t n, const gs_adam_state *st, const gs_grads *grads, const float lr[5],
                  int32_t zero_grads, void *stream);
 
+/* gs_adam_step with the isotropy regulariser of the mapping loss (Eq. 4: lambda_s L_iso,
+ * L_iso = sum_i sum_axes |s_i - mean(s_i)| over each Gaussian's per-axis scales s = exp(log-scale),
+ * lambda_s = 10 in the paper) added to the log-scale gradients inside the same pass.  iso_loss
+ * (device double, may be NULL) receives lambda_s L_iso at the pre-step parameters. */
+int gs_adam_step_reg(int64_t n, const gs_adam_state *st, const gs_grads *grads, const float lr[5], float iso_weight,
+                     int32_t zero_grads, double *iso_loss, void *stream);
+
 /* ---- joint pose-Gaussian refinement after fusion (Sec. III-C) ---- */
 
 /* Mutable Gaussian arrays, same shapes as gs_gaussians. */

@@ -151,3 +151,17 @@ def view_adam_step(cam_row, expo, pose_grad, expo_grad, m, v, step, lr_pose, lr_
     lr = np.array([lr_pose] * 6 + [lr_expo] * 2)
     d = -lr * (m / (1 - beta1 ** step)) / (np.sqrt(v / (1 - beta2 ** step)) + eps)
     return exp_se3_left(cam_row, d[:6]), np.asarray(expo, np.float64) + d[6:], m, v
+
+
+def iso_loss(log_scales, weight=10.0):
+    """Isotropy regulariser of the mapping loss (Eq. 4: lambda_s L_iso, lambda_s = 10) with
+    L_iso = sum_i sum_axes |s_i - mean(s_i)|, s_i = exp(log-scales) the Gaussian's per-axis scales:
+    it pulls each Gaussian's scales toward their mean.  Returns (weight * L_iso, d/d log_scales)."""
+    ls = np.asarray(log_scales, np.float64)
+    s = np.exp(ls)
+    sbar = s.mean(axis=1, keepdims=True)
+    d = s - sbar
+    sg = np.sign(d)
+    # d|s_a - sbar| / d s_b = sg_a (delta_ab - 1/3); chain through s_b = exp(l_b)
+    g_s = sg - sg.sum(axis=1, keepdims=True) / 3.0
+    return weight * np.abs(d).sum(), weight * g_s * s

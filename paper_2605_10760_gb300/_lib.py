@@ -116,7 +116,9 @@ _SIGS = {
                                           _P]),
     "gs_adam_step": (C.c_int, [C.c_int64, C.POINTER(gs_adam_state), C.POINTER(gs_grads),
                                C.POINTER(C.c_float), C.c_int32, _P]),
-"gs_refine_scratch_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
+"gs_adam_step_reg": (C.c_int, [C.c_int64, C.POINTER(gs_adam_state), C.POINTER(gs_grads), C.POINTER(C.c_float),
+                                   C.c_float, C.c_int32, _P, _P]),
+    "gs_refine_scratch_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
     "gs_loss_refine": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P, C.c_float, C.c_float,
                                  C.c_float, _P, _P, _P, _P, _P, _P]),
     "gs_prune_scratch_size": (C.c_size_t, [C.c_int64]),

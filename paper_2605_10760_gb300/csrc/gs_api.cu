@@ -442,6 +442,16 @@ int gs_adam_step(int64_t n, const gs_adam_state *st, const gs_grads *grads, cons
     return launch_adam(n, *st, *grads, lr, zero_grads, (cudaStream_t)stream);
 }
 
+int gs_adam_step_reg(int64_t n, const gs_adam_state *st, const gs_grads *grads, const float lr[5], float iso_weight,
+                     int32_t zero_grads, double *iso_loss, void *stream) {
+    if (n < 0 || !st || !grads || !lr || !st->step || !st->m || !st->v) return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!st->means || !st->log_scales || !st->quats || !st->opacity_logits || !st->opacities ||
+                  !st->colors || !grads->means || !grads->log_scales || !grads->quats || !grads->opacities ||
+                  !grads->colors))
+        return GS_ERR_INVALID_ARG;
+    return launch_adam(n, *st, *grads, lr, zero_grads, (cudaStream_t)stream, iso_weight, iso_loss);
+}
+
 __global__ void k_debug_expf(const float *x, float *ys, float *yc, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float v = x[i];

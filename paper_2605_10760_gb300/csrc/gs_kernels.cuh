@@ -108,6 +108,6 @@ int launch_prune(long long n, const gs_gaussians &in, float thr, const gs_gaussi
 int launch_view_adam(int V, const gs_view_adam_state &st, const float *pose_grad, const float *expo_grad, float lr_pose,
                      float lr_expo, cudaStream_t s);
 int launch_adam(long long n, const gs_adam_state &st, const gs_grads &g, const float lr[5], int zero_grads,
-                cudaStream_t s);
+                cudaStream_t s, float iso_weight = 0.f, double *iso_loss = nullptr);
 
 }  // namespace gs

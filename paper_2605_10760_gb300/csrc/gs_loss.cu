@@ -305,6 +305,8 @@ struct AdamArgs {
     const int32_t *step;
     float lr[5];
     int zero;
+    float iso_weight;       // lambda_s of the isotropy regulariser (0: none)
+    double *iso_loss;       // optional: receives lambda_s L_iso (overwritten)
 };
 
 __global__ void __launch_bounds__(256) k_adam(AdamArgs a) {
@@ -316,6 +318,26 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs a) {
     const int dims[5] = {3, 3, 4, 1, 3};
     int col = 0;
     float *m = a.m + 14 * i, *v = a.v + 14 * i;
+    // isotropy regulariser (Eq. 4): lambda_s sum_axes |s - mean(s)|, s = exp(log-scale); its
+    // gradient with respect to log-scale b is lambda_s (sg_b - mean(sg)) s_b, sg = sign(s - mean)
+    float giso[3] = {0.f, 0.f, 0.f};
+    if (a.iso_weight != 0.f) {
+        float sc[3], sg[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sc[k] = expf(a.p[1][3 * i + k]);
+        const float sbar = (sc[0] + sc[1] + sc[2]) * (1.f / 3.f);
+        float lsum = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float d = sc[k] - sbar;
+            sg[k] = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+            lsum += fabsf(d);
+        }
+        const float sgm = (sg[0] + sg[1] + sg[2]) * (1.f / 3.f);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) giso[k] = a.iso_weight * (sg[k] - sgm) * sc[k];
+        if (a.iso_loss) atomicAdd(a.iso_loss, (double)(a.iso_weight * lsum));
+    }
 #pragma unroll
     for (int grp = 0; grp < 5; ++grp) {
 #pragma unroll
@@ -323,6 +345,7 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs a) {
             if (d >= dims[grp]) break;
             const long long idx = i * dims[grp] + d;
             float gr = a.g[grp][idx];
+            if (grp == 1) gr += giso[d];
             if (grp == 3) {
                 const float o = a.opac[i];
                 gr *= o * (1.f - o);
@@ -344,8 +367,11 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs a) {
 __global__ void k_step_inc(int32_t *step) { *step += 1; }
 
 int launch_adam(long long n, const gs_adam_state &st, const gs_grads &g, const float lr[5], int zero_grads,
-                cudaStream_t s) {
+                cudaStream_t s, float iso_weight, double *iso_loss) {
     AdamArgs a;
+    a.iso_weight = iso_weight;
+    a.iso_loss = iso_loss;
+    if (iso_loss && cudaMemsetAsync(iso_loss, 0, sizeof(double), s) != cudaSuccess) return GS_ERR_CUDA;
     a.n = n;
     a.p[0] = st.means; a.p[1] = st.log_scales; a.p[2] = st.quats; a.p[3] = st.opacity_logits; a.p[4] = st.colors;
     a.opac = st.opacities;

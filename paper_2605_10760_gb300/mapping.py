@@ -26,8 +26,9 @@ _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "aut
 
 class MappingLoop:
     def __init__(self, problem: R.Problem, g: R.Gaussians, rgb_target: torch.Tensor,
-                 lr=(1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3), w_l1=0.8, w_ssim=0.2, headroom=2.0):
+                 lr=(1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3), w_l1=0.8, w_ssim=0.2, headroom=2.0, iso_weight=0.0):
         self.pb, self.g = problem, g
+        self.iso_weight = float(iso_weight)      # lambda_s of Eq. 4's isotropy term (10 in the paper)
         self.rgb_t = rgb_target.contiguous()
         self.w_l1, self.w_ssim = float(w_l1), float(w_ssim)
         self.adam = R.AdamState(g, lr)
@@ -56,7 +57,7 @@ class MappingLoop:
         R.loss_l1_ssim(self.img["rgb"], self.rgb_t, self.w_l1, self.w_ssim, self.d_rgb, self.loss, self.scratch)
         pb.render_bwd(self.g, self.img, self.d_rgb, None, None, self.grads)
         pb.pose_grad(self.pose)
-        self.adam.apply(self.grads, zero_grads=True)
+        self.adam.apply(self.grads, zero_grads=True, iso_weight=self.iso_weight)
 
     def capture(self, iters: int = 100):
         """Capture `iters` iterations into one CUDA graph (after one eager warm-up iteration)."""

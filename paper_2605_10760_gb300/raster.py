@@ -265,14 +265,15 @@ class AdamState:
         self.step = torch.zeros(1, dtype=torch.int32, device=g.means.device)
         self.lr = (C.c_float * 5)(*lr)
 
-    def apply(self, grads: Gaussians, zero_grads=True):
+    def apply(self, grads: Gaussians, zero_grads=True, iso_weight=0.0, iso_loss=None):
+        """One Adam step; iso_weight > 0 adds the isotropy regulariser lambda_s L_iso (Eq. 4)."""
         st = L.gs_adam_state(self.g.means.data_ptr(), self.g.log_scales.data_ptr(), self.g.quats.data_ptr(),
                              self.logits.data_ptr(), self.g.opacities.data_ptr(), self.g.colors.data_ptr(),
                              self.m.data_ptr(), self.v.data_ptr(), self.step.data_ptr())
         go = L.gs_grads(*[getattr(grads, k).data_ptr() for k in ("means", "log_scales", "quats", "opacities",
                                                                    "colors")])
-        L.check(L.load().gs_adam_step(self.g.n, C.byref(st), C.byref(go), self.lr, int(bool(zero_grads)),
-                                      _stream()), "gs_adam_step")
+        L.check(L.load().gs_adam_step_reg(self.g.n, C.byref(st), C.byref(go), self.lr, float(iso_weight),
+                                          int(bool(zero_grads)), _ptr(iso_loss), _stream()), "gs_adam_step_reg")
 
 
 # ------------------------------------------------------------------------------------------

@@ -76,3 +76,24 @@ def test_adam_step_matches_oracle(R):
     np.testing.assert_allclose(st.logits.cpu().numpy(), ref["logit"], rtol=1e-5, atol=1e-5)
     np.testing.assert_allclose(g.opacities.cpu().numpy(), 1 / (1 + np.exp(-ref["logit"])), rtol=1e-5, atol=1e-6)
     assert int(st.step.item()) == 3
+
+
+def test_adam_with_isotropy_regulariser_matches_oracle(R):
+    """Adam with lambda_s L_iso (Eq. 4) fused into the log-scale update."""
+    rng = np.random.default_rng(8)
+    sc = S.random_cloud(2000, seed=12)
+    g = R.Gaussians.from_scene(sc)
+    st = R.AdamState(g, lr=(1.6e-4, 5e-3, 1e-3, 5e-2, 2.5e-3))
+    ls = sc.log_scales.astype(np.float64)
+    m, v = np.zeros_like(ls), np.zeros_like(ls)
+    iso = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for step in range(1, 3):
+        gls = rng.normal(0, 1, ls.shape).astype(np.float32)
+        grads = R.zeros_like_grads(g)
+        grads.log_scales.copy_(torch.from_numpy(gls).cuda())
+        val, giso = OL.iso_loss(ls, 10.0)
+        st.apply(grads, zero_grads=True, iso_weight=10.0, iso_loss=iso)
+        torch.cuda.synchronize()
+        assert abs(iso.item() - val) <= 1e-5 * val
+        ls, m, v = OL.adam_step(ls, gls + giso, m, v, step, 5e-3)
+    np.testing.assert_allclose(g.log_scales.cpu().numpy(), ls, rtol=1e-5, atol=2e-6)

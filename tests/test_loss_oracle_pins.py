@@ -125,3 +125,17 @@ def test_refine_loss_gradients_vs_autograd():
 def test_prune_keep_threshold():
     o = np.array([0.5, 0.004, 0.005, 0.0049999, 1.0, 0.0], np.float32)
     assert list(L.prune_keep(o)) == [0, 2, 4]
+
+
+def test_iso_loss_vs_autograd_and_isotropic_minimum():
+    rng = np.random.default_rng(6)
+    ls = rng.normal(-3, 0.5, (40, 3))
+    val, g = L.iso_loss(ls, 10.0)
+    lt = torch.tensor(ls, requires_grad=True)
+    st = torch.exp(lt)
+    (10.0 * (st - st.mean(1, keepdim=True)).abs().sum()).backward()
+    assert abs(val - 10.0 * np.abs(np.exp(ls) - np.exp(ls).mean(1, keepdims=True)).sum()) < 1e-12
+    np.testing.assert_allclose(g, lt.grad.numpy(), rtol=1e-12, atol=1e-15)
+    iso = np.full((5, 3), -2.0)
+    v0, g0 = L.iso_loss(iso)
+    assert v0 == 0.0 and np.all(g0 == 0.0)
