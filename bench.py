@@ -390,6 +390,117 @@ def refine_graph(R, S, torch, iters=100, reps=2):
             "status": rc or rc0}
 
 
+# algorithmic FP32 work of one in-frame anchor pixel of the Eq. 12 kernel (FMA = 2): decision chain
+# 94, bilinear sample + gradient + Huber + moments for 3 channels 81, A = d pi / d xi 53, the
+# 2 x 2 fold 42, the 7-vector 28, the 28 upper-triangle entries 112
+FLOP_PHO = 410
+# HBM bytes per anchor pixel: source RGB + depth (16 B) and the target RGB once (12 B)
+BYTES_PHO = 28
+
+
+def pho_bench(R, S, torch, reps=20):
+    """Eq. 12 photometric blocks of 16 pose-graph edges: 8 rooms of agents8x4 (50k..400k
+    Gaussians), in each an anchor keyframe and a second one moved 8 cm / 2 deg, rendered at
+    1200x680 (RGB + normalised depth); edges in both directions, a perturbed source correction."""
+    from scipy.linalg import expm
+    wl = S.workload("agents8x4")
+    cams, sov = [], []
+    sk = lambda v: np.array([[0, -v[2], v[1]], [v[2], 0, -v[0]], [-v[1], v[0], 0]])
+    for r in range(8):
+        c = wl.cameras[4 * r]
+        Rb = (expm(sk([0.01, -0.03, 0.02])) @ c.R.astype(np.float64)).astype(np.float32)
+        tb = (c.t.astype(np.float64) + np.array([0.08, -0.02, 0.03])).astype(np.float32)
+        cams += [c, S.Camera(Rb, tb, c.fx, c.fy, c.cx, c.cy, c.width, c.height)]
+        sov += [r, r]
+    sov = np.array(sov)
+    vb = wl.scene_offsets[sov]
+    vc = wl.scene_offsets[sov + 1] - vb
+    pb = R.Problem(vb, vc, wl.scene.n, wl.width, wl.height, R.cameras_tensor(cams))
+    img = pb.forward_checked(R.Gaussians.from_scene(wl.scene))
+    a = img["alpha"]
+    depth = torch.where(a > 0.5, img["depth"] / a.clamp_min(1e-6), torch.zeros_like(a)).contiguous()
+    rgb = img["rgb"].contiguous()
+    ident = ([1.0, 0, 0, 0], [0.0, 0, 0], 1.0)
+    pert = ([0.99999, 0.002, -0.0015, 0.001], [0.005, -0.003, 0.003], 1.002)
+    corrs = R.sim3_tensor([ident, pert])
+    edges = R.pho_edges([e for r in range(8) for e in ((2 * r, 2 * r + 1, 1, 0, 1.0), (2 * r + 1, 2 * r, 0, 1, 1.0))])
+    pr = R.PhoResidual(16)
+    out = pr(edges, rgb, depth, pb.cameras, corrs)
+    for _ in range(3):
+        pr(edges, rgb, depth, pb.cameras, corrs, out=out)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = R.L.load().gs_launch_count()
+    ev0.record(st)
+    for _ in range(reps):
+        pr(edges, rgb, depth, pb.cameras, corrs, out=out)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    count = out["count"].cpu().numpy()
+    px = 16 * wl.width * wl.height
+    inframe = int(count.sum())
+    flops = FLOP_PHO * inframe + 94 * (px - inframe)
+    ach = flops / (ms * 1e-3) / 1e12
+    peak = 152 * 128 * 2 * _peaks()["sm_max_mhz"] * 1e6 / 1e12
+    return {"workload": "agents8x4 anchor pairs: 16 edges, 1200x680 anchors, stride 1, Huber 9/255",
+            "ms_per_call": ms, "edges_per_s": 16 / (ms * 1e-3), "anchor_pixels_per_s": px / (ms * 1e-3),
+            "in_frame_fraction": inframe / px, "launches_per_call": (R.L.load().gs_launch_count() - n0) // reps,
+            "roofline": {"kernel": "k_pho_edge + k_pho_finish", "bound": "alu", "achieved": ach, "unit": "TFLOP/s",
+                         "peak": peak, "frac": ach / peak,
+                         "hbm_gbs": BYTES_PHO * px / (ms * 1e-3) / 1e9}}
+
+
+def fusion_bench(R, S, torch, voxel=0.05, k=3.0, stride=2, reps=3):
+    """floor4m split into a target map (agents 0-7) and a borrowed map (agents 8-15, moved by a
+    Sim(3) correction): Eq. 19 on the borrowed Gaussians, Eq. 20 occupied voxels of the target,
+    Eq. 21 free voxels carved from 8 target keyframe depth maps (rendered, every 2nd pixel), Eq. 22
+    keep flags of the borrowed Gaussians.  Times each stage with CUDA events."""
+    wl = S.workload("floor4m")
+    ao = wl.meta["agent_offsets"]
+    half = int(ao[8])
+    g = R.Gaussians.from_scene(wl.scene)
+    tgt = R.Gaussians(*[getattr(g, f)[:half].contiguous() for f in ("means", "log_scales", "quats", "opacities",
+                                                                     "colors")])
+    bor = R.Gaussians(*[getattr(g, f)[half:].contiguous() for f in ("means", "log_scales", "quats", "opacities",
+                                                                     "colors")])
+    views = list(range(8))
+    cams = R.cameras_tensor([wl.cameras[v] for v in views])
+    pb = R.Problem(np.zeros(8, np.int64), np.full(8, tgt.n, np.int64), tgt.n, wl.width, wl.height, cams)
+    img = pb.forward_checked(tgt)
+    a = img["alpha"]
+    depth = torch.where(a > 0.5, img["depth"] / a.clamp_min(1e-6), torch.zeros_like(a)).contiguous()
+    occ, fre = R.VoxSet(1 << 25), R.VoxSet(1 << 25)
+    moved = R.sim3_apply(bor, [1.0, 0.0, 0.0, 0.02], [0.05, -0.03, 0.0], 1.01)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    t = {"sim3": [], "occupied": [], "free": [], "keep": []}
+    for _ in range(reps):
+        occ.clear()
+        fre.clear()
+        ev[0].record()
+        R.sim3_apply(bor, [1.0, 0.0, 0.0, 0.02], [0.05, -0.03, 0.0], 1.01, out=moved)
+        ev[1].record()
+        occ.add_boxes(tgt.means, tgt.log_scales, k, voxel)
+        ev[2].record()
+        fre.add_rays(pb.cameras, depth, stride, voxel)
+        ev[3].record()
+        keep = R.dedup_keep(moved.means, occ, fre, voxel)
+        ev[4].record()
+        torch.cuda.synchronize()
+        for i, key in enumerate(t):
+            t[key].append(ev[i].elapsed_time(ev[i + 1]))
+    rc_o, n_o = occ.status()
+    rc_f, n_f = fre.status()
+    kept = int(keep.sum().item())
+    ms = {key: statistics.median(val) for key, val in t.items()}
+    return {"workload": "floor4m halves: 2M target / 2M borrowed Gaussians, 8 keyframes 1200x680 (stride 2), "
+                        "voxel %.2f m, k = %g" % (voxel, k),
+            "ms": ms, "total_ms": sum(ms.values()), "borrowed": bor.n, "kept": kept,
+            "occupied_voxels": n_o, "free_voxels": n_f, "status": [rc_o, rc_f],
+            "rays": 8 * ((wl.width + stride - 1) // stride) * ((wl.height + stride - 1) // stride)}
+
+
 def fused_map(R, S, torch, steps=3):
     """floor4m: 16 agents' submaps merged into 4M Gaussians (multi-room floor), 64 views in one
     batched problem, forward + backward with per-view pose gradients."""
@@ -538,19 +649,24 @@ def main():
         "pose_grad": 0,
     }
     fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s at max SM clock
+    # DRAM bytes (read + write) of one launch from an ncu capture of this workload; see
+    # profiles/render_bwd_room500k.md (None for a stage without a capture of its current code)
+    traffic = {"render_bwd": 35207424}
     if dom in ("render_fwd", "render_bwd"):
         flops = stats["fwd_pairs"] * FLOP_FWD if dom == "render_fwd" else stats["bwd_pairs"] * FLOP_BWD
         ach = flops / (stage_ms[dom] * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None,
+                "frac": ach / fp32_peak, "traffic": traffic.get(dom),
                 "peak_note": "FP32 FMA pipes: 152 SM x 128 lanes x 2 FLOP x max SM clock (derived)"}
     else:
         ach = alg_bytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_note": "of %s" % peaks["src"]}
+                "frac": ach / peaks["hbm_gbs"], "traffic": traffic.get(dom), "peak_note": "of %s" % peaks["src"]}
     batched = None if args.no_batched else batched_speedup(R, S, torch, flush)
     graph_loop = None if args.no_extra else mapping_graph(R, S, torch)
     refine = None if args.no_extra else refine_graph(R, S, torch)
+    fusion = None if args.no_extra else fusion_bench(R, S, torch)
+    pho = None if args.no_extra else pho_bench(R, S, torch)
     fused = None if args.no_extra else fused_map(R, S, torch)
     cpu = None if args.no_cpu else cpu_baseline()
     line = {
@@ -573,6 +689,8 @@ def main():
         "batched": batched,
         "mapping_graph": graph_loop,
         "refine_graph": refine,
+        "fusion": fusion,
+        "photometric": pho,
         "fused_map": fused,
         "cpu_baseline": cpu,
         "clocks": clocks,

@@ -203,7 +203,7 @@ int gs_pose_grad(const gs_problem *pb, void *ws, float *pose_grad, void *stream)
 /* Photometric + depth L1 terms of the mapping loss (Eq. 4): L = w_rgb mean|rgb - rgb_t| +
  * w_depth mean|depth - depth_t| over `views` views of width x height.  Writes d_rgb [V,3,H,W],
  * d_depth [V,H,W] (d_depth / depth / depth_t may be NULL when w_depth = 0) and writes L to
- * *loss (device double, overwritten).  sign(0) = 0. */
+ * *loss (device double, overwritten).  sign(0) = 0.  1 <= views <= 65535. */
 int gs_loss_l1(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
                const float *depth, const float *depth_t, float w_rgb, float w_depth,
                float *d_rgb, float *d_depth, double *loss, void *stream);
@@ -301,6 +301,96 @@ typedef struct gs_view_adam_state {
 } gs_view_adam_state;
 int gs_view_adam_step(int32_t views, const gs_view_adam_state *st, const float *pose_grad, const float *expo_grad,
                       float lr_pose, float lr_expo, void *stream);
+
+/* ---- occupancy-aware fusion of aligned submaps (Sec. III-C, Eqs. 19-22) ---- */
+
+/* Sim(3) correction: rotation as a quaternion (w,x,y,z) (normalised internally), translation t,
+ * scale s > 0. */
+typedef struct gs_sim3 {
+    float q[4];
+    float t[3];
+    float s;
+} gs_sim3;
+
+/* Eq. 19: out = C applied to n Gaussians: mu' = s R mu + t, Sigma' = s^2 R Sigma R^T (rotation
+ * q' = q_R (x) q, log-scales + ln s), opacity and colour unchanged.  C is a host pointer; out may
+ * alias in. */
+int gs_sim3_apply(int64_t n, const gs_gaussians *in, const gs_sim3 *C, const gs_gaussian_arrays *out, void *stream);
+
+/* Voxel sets: open-addressing hash sets of 64-bit voxel keys.  A voxel index is
+ * kappa(x) = floor(x / voxel) per axis (FP32 division), packed 21 bits per axis with offset 2^20
+ * (indices clamped to [-2^20, 2^20)).  A set occupies gs_voxset_bytes(capacity) bytes of device
+ * memory (256-byte aligned); capacity is a power of two >= 2 and should be about twice the number
+ * of distinct voxels.  A full table records GS_ERR_CAPACITY, a box or ray beyond the supported
+ * extent (64 voxels per axis per Gaussian, 65536 voxels per ray) records GS_ERR_INVALID_ARG; both
+ * are read by gs_voxset_status. */
+size_t gs_voxset_bytes(int64_t capacity);
+int gs_voxset_clear(void *set, int64_t capacity, void *stream);
+int gs_voxset_status(void *set, void *stream, int64_t *count, int64_t capacity);
+
+/* Eq. 20: inserts the occupied voxels of n target Gaussians, every voxel of the box
+ * [kappa(mu - k s), kappa(mu + k s)] with s = exp(log-scales) per axis. */
+int gs_voxset_add_boxes(void *set, int64_t capacity, int64_t n, const float *means, const float *log_scales, float k,
+                        float voxel, void *stream);
+
+/* Eq. 21: inserts the free voxels carved by keyframe depth maps: for every stride-th pixel (row and
+ * column) of each view with depth d > 0 (camera z, [V,H,W]), every voxel crossed by the segment from
+ * the camera centre to the back-projected point, excluding the end point (t in [0, 1)). */
+int gs_voxset_add_rays(void *set, int64_t capacity, int32_t views, int32_t width, int32_t height,
+                       const gs_camera *cams, const float *depth, int32_t stride, float voxel, void *stream);
+
+/* Eq. 22: keep[i] = 1 iff kappa(means[i]) is in neither set (free_set may be NULL). */
+int gs_voxset_keep(int64_t n, const float *means, void *occ, int64_t occ_capacity, void *free_set,
+                   int64_t free_capacity, float voxel, uint8_t *keep, void *stream);
+
+/* ---- Anchor-image photometric residuals of the submap pose graph (Sec. III-B, Eq. 12) ----
+ *
+ * For an inter-agent edge with a source anchor keyframe s and a target anchor keyframe a (images,
+ * z-depth maps and world-to-camera cameras given in their own submaps' coordinates) and the two
+ * submap corrections C_src, C_tgt (gs_sim3: x -> s R(q) x + t), every anchor pixel u of s (every
+ * stride-th row and column) gives three residuals (one per colour channel)
+ *   r(u) = I_s(u) - I_a(pi_a(C_tgt^-1 C_src p_s(u))),   p_s(u) = R_s^T (d(u) K_s^-1 [u + 0.5, 1] - t_s),
+ * with I_a sampled bilinearly at pi_a - 0.5 (pixel centres at +0.5).  U_e, the in-frame,
+ * finite-depth anchor-pixel set, holds the pixels with 0 < d < inf, camera-space depth in the
+ * target above near_plane and all four bilinear taps inside the target image; membership and the
+ * bilinear cell follow one fixed FP32 operation sequence (deterministic, reproducible).
+ * Jacobians are taken w.r.t. left Sim(3) twists xi = (rho, phi, sigma) (translation, rotation,
+ * log-scale) of the global frame, C <- Exp(xi) C, for the source (columns 0-6) and target
+ * (columns 7-13) corrections.  With Huber weights omega (threshold huber_delta on each scalar
+ * residual) and n = |U_e|, each edge returns
+ *   cost = (w_e / n) sum rho(r),  H = (w_e / n) sum omega J^T J (14 x 14),  g = (w_e / n) sum omega J^T r,
+ * the robust Gauss-Newton blocks of the edge's term of the graph cost (the cost gradient is 2 g);
+ * an empty U_e gives zeros. */
+typedef struct gs_pho_edge {
+    int32_t src_image, tgt_image;      /* anchor keyframes: indices into images/depths/cameras */
+    int32_t src_corr, tgt_corr;        /* indices into the correction array */
+    float weight;                      /* w_e of the edge */
+    float reserved[3];
+} gs_pho_edge;
+
+typedef struct gs_pho_params {
+    int32_t stride;                    /* anchor pixels on every stride-th row and column, >= 1 */
+    float huber_delta;                 /* Huber threshold per scalar residual (default 9/255) */
+    float near_plane;                  /* target camera-space depth must exceed this (default 0.2) */
+    int32_t reserved;
+} gs_pho_params;
+
+gs_pho_params gs_default_pho_params(void);
+
+/* Device scratch for gs_pho_residual (per-block partial sums), in bytes. */
+size_t gs_pho_scratch_size(int32_t num_edges);
+
+/* num_edges edges (device array, 32 B each); images [M, 3, H, W] and depths [M, H, W] FP32 planar
+ * (device); cameras [M] and corrections [num_corr] device arrays; params a host pointer.
+ * Outputs (device): cost [E] double, count [E] int64 (|U_e|, or -1 for an edge whose indices are
+ * out of range, whose other outputs are then zero), H [E, 14, 14] double (row-major), g [E, 14]
+ * double.  scratch: gs_pho_scratch_size(num_edges) bytes of device memory (any contents).
+ * Results are deterministic (fixed reduction order).  GS_ERR_INVALID_ARG for null pointers,
+ * stride < 1, num_edges outside [0, 65535], empty images or too small a scratch. */
+int gs_pho_residual(int32_t num_edges, const gs_pho_edge *edges, int32_t num_images, int32_t width, int32_t height,
+                    const float *images, const float *depths, const gs_camera *cameras, int32_t num_corr,
+                    const gs_sim3 *corrections, const gs_pho_params *params, double *cost, int64_t *count,
+                    double *H, double *g, void *scratch, size_t scratch_bytes, void *stream);
 
 /* Zeroes the five gradient arrays of n Gaussians (stream-ordered memsets). */
 int gs_grads_zero(int64_t n, const gs_grads *grads, void *stream);

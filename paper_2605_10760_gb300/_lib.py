@@ -86,6 +86,20 @@ class gs_view_adam_state(C.Structure):
                 ("step", C.c_void_p)]
 
 
+class gs_sim3(C.Structure):
+    _fields_ = [("q", C.c_float * 4), ("t", C.c_float * 3), ("s", C.c_float)]
+
+
+class gs_pho_edge(C.Structure):
+    _fields_ = [("src_image", C.c_int32), ("tgt_image", C.c_int32), ("src_corr", C.c_int32), ("tgt_corr", C.c_int32),
+                ("weight", C.c_float), ("reserved", C.c_float * 3)]
+
+
+class gs_pho_params(C.Structure):
+    _fields_ = [("stride", C.c_int32), ("huber_delta", C.c_float), ("near_plane", C.c_float),
+                ("reserved", C.c_int32)]
+
+
 class gs_adam_state(C.Structure):
     _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity_logits", C.c_void_p), ("opacities", C.c_void_p), ("colors", C.c_void_p),
@@ -116,7 +130,20 @@ _SIGS = {
                                           _P]),
     "gs_adam_step": (C.c_int, [C.c_int64, C.POINTER(gs_adam_state), C.POINTER(gs_grads),
                                C.POINTER(C.c_float), C.c_int32, _P]),
-"gs_adam_step_reg": (C.c_int, [C.c_int64, C.POINTER(gs_adam_state), C.POINTER(gs_grads), C.POINTER(C.c_float),
+"gs_sim3_apply": (C.c_int, [C.c_int64, C.POINTER(gs_gaussians), C.POINTER(gs_sim3), C.POINTER(gs_gaussian_arrays),
+                                _P]),
+    "gs_voxset_bytes": (C.c_size_t, [C.c_int64]),
+    "gs_voxset_clear": (C.c_int, [_P, C.c_int64, _P]),
+    "gs_voxset_status": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.c_int64]),
+    "gs_voxset_add_boxes": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, C.c_float, C.c_float, _P]),
+    "gs_voxset_add_rays": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_int32, C.c_float,
+                                     _P]),
+    "gs_voxset_keep": (C.c_int, [C.c_int64, _P, _P, C.c_int64, _P, C.c_int64, C.c_float, _P, _P]),
+    "gs_default_pho_params": (gs_pho_params, []),
+    "gs_pho_scratch_size": (C.c_size_t, [C.c_int32]),
+    "gs_pho_residual": (C.c_int, [C.c_int32, _P, C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, C.c_int32, _P,
+                                  C.POINTER(gs_pho_params), _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "gs_adam_step_reg": (C.c_int, [C.c_int64, C.POINTER(gs_adam_state), C.POINTER(gs_grads), C.POINTER(C.c_float),
                                    C.c_float, C.c_int32, _P, _P]),
     "gs_refine_scratch_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
     "gs_loss_refine": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P, C.c_float, C.c_float,

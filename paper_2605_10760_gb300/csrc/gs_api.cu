@@ -369,7 +369,8 @@ int gs_pose_grad(const gs_problem *pb, void *ws, float *pose_grad, void *stream)
 int gs_loss_l1(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
                const float *depth, const float *depth_t, float w_rgb, float w_depth, float *d_rgb, float *d_depth,
                double *loss, void *stream) {
-    if (views < 1 || width < 1 || height < 1 || !rgb || !rgb_t || !d_rgb || !loss) return GS_ERR_INVALID_ARG;
+    if (views < 1 || views > 65535 || width < 1 || height < 1 || !rgb || !rgb_t || !d_rgb || !loss)
+        return GS_ERR_INVALID_ARG;
     if (w_depth != 0.f && (!depth || !depth_t || !d_depth)) return GS_ERR_INVALID_ARG;
     return launch_loss_l1(views, width, height, rgb, rgb_t, depth, depth_t, w_rgb, w_depth, d_rgb, d_depth, loss,
                           (cudaStream_t)stream);
@@ -430,6 +431,122 @@ int gs_view_adam_step(int32_t views, const gs_view_adam_state *st, const float *
         !pose_grad || !expo_grad)
         return GS_ERR_INVALID_ARG;
     return launch_view_adam(views, *st, pose_grad, expo_grad, lr_pose, lr_expo, (cudaStream_t)stream);
+}
+
+static bool pow2(long long c) { return c >= 2 && (c & (c - 1)) == 0; }
+
+int gs_sim3_apply(int64_t n, const gs_gaussians *in, const gs_sim3 *C, const gs_gaussian_arrays *out, void *stream) {
+    if (n < 0 || !in || !C || !out || !(C->s > 0.f)) return GS_ERR_INVALID_ARG;
+    const float nq = C->q[0] * C->q[0] + C->q[1] * C->q[1] + C->q[2] * C->q[2] + C->q[3] * C->q[3];
+    if (!(nq > 0.f)) return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!in->means || !in->log_scales || !in->quats || !in->opacities || !in->colors || !out->means ||
+                  !out->log_scales || !out->quats || !out->opacities || !out->colors))
+        return GS_ERR_INVALID_ARG;
+    return launch_sim3(n, *in, C->q, C->t, C->s, *out, (cudaStream_t)stream);
+}
+
+size_t gs_voxset_bytes(int64_t capacity) { return pow2(capacity) ? 256 + 8 * (size_t)capacity : 0; }
+
+int gs_voxset_clear(void *set, int64_t capacity, void *stream) {
+    if (!ws_ok(set) || !pow2(capacity)) return GS_ERR_INVALID_ARG;
+    return launch_voxset_clear(set, capacity, (cudaStream_t)stream);
+}
+
+__global__ void k_voxset_count(const unsigned long long *keys, long long capacity, unsigned long long *out) {
+    unsigned long long c = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < capacity; i += (long long)gridDim.x * blockDim.x)
+        c += keys[i] != ~0ull;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+int gs_voxset_status(void *set, void *stream, int64_t *count, int64_t capacity) {
+    if (!ws_ok(set)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t code = 0;
+    if (count) {
+        if (!pow2(capacity)) return GS_ERR_INVALID_ARG;
+        // counter in the status block's spare bytes (offset 8)
+        unsigned long long *c = reinterpret_cast<unsigned long long *>(static_cast<char *>(set) + 8);
+        if (cudaMemsetAsync(c, 0, 8, s) != cudaSuccess) return GS_ERR_CUDA;
+        k_voxset_count<<<std::max(1, std::min((int)((capacity + 255) / 256), device_sm_count() * 8)), 256, 0, s>>>(
+            reinterpret_cast<const unsigned long long *>(static_cast<char *>(set) + 256), capacity, c);
+        count_launches(1);
+        unsigned long long h = 0;
+        if (cudaMemcpyAsync(&h, c, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return GS_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return GS_ERR_CUDA;
+        *count = (int64_t)h;
+    }
+    if (cudaMemcpyAsync(&code, set, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GS_ERR_CUDA;
+    return code;
+}
+
+int gs_voxset_add_boxes(void *set, int64_t capacity, int64_t n, const float *means, const float *log_scales, float k,
+                        float voxel, void *stream) {
+    if (!ws_ok(set) || !pow2(capacity) || n < 0 || (n > 0 && (!means || !log_scales)) || !(voxel > 0.f) || !(k >= 0.f))
+        return GS_ERR_INVALID_ARG;
+    return launch_voxset_add_boxes(set, capacity, n, means, log_scales, k, voxel, (cudaStream_t)stream);
+}
+
+int gs_voxset_add_rays(void *set, int64_t capacity, int32_t views, int32_t width, int32_t height,
+                       const gs_camera *cams, const float *depth, int32_t stride, float voxel, void *stream) {
+    if (!ws_ok(set) || !pow2(capacity) || views < 1 || width < 1 || height < 1 || !cams || !depth || stride < 1 ||
+        !(voxel > 0.f))
+        return GS_ERR_INVALID_ARG;
+    return launch_voxset_add_rays(set, capacity, views, width, height, cams, depth, stride, voxel, (cudaStream_t)stream);
+}
+
+int gs_voxset_keep(int64_t n, const float *means, void *occ, int64_t occ_capacity, void *free_set,
+                   int64_t free_capacity, float voxel, uint8_t *keep, void *stream) {
+    if (n < 0 || (n > 0 && (!means || !keep)) || !ws_ok(occ) || !pow2(occ_capacity) || !(voxel > 0.f))
+        return GS_ERR_INVALID_ARG;
+    if (free_set && (!ws_ok(free_set) || !pow2(free_capacity))) return GS_ERR_INVALID_ARG;
+    return launch_voxset_keep(n, means, occ, occ_capacity, free_set, free_capacity, voxel, keep, (cudaStream_t)stream);
+}
+
+gs_pho_params gs_default_pho_params(void) {
+    gs_pho_params p;
+    p.stride = 1;
+    p.huber_delta = 9.0f / 255.0f;
+    p.near_plane = 0.2f;
+    p.reserved = 0;
+    return p;
+}
+
+size_t gs_pho_scratch_size(int32_t num_edges) { return num_edges > 0 ? pho_scratch_bytes(num_edges) : 0; }
+
+int gs_pho_residual(int32_t num_edges, const gs_pho_edge *edges, int32_t num_images, int32_t width, int32_t height,
+                    const float *images, const float *depths, const gs_camera *cameras, int32_t num_corr,
+                    const gs_sim3 *corrections, const gs_pho_params *params, double *cost, int64_t *count,
+                    double *H, double *g, void *scratch, size_t scratch_bytes, void *stream) {
+    if (num_edges < 0 || num_edges > 65535 || !params) return GS_ERR_INVALID_ARG;
+    if (num_edges == 0) return GS_OK;
+    if (!edges || !images || !depths || !cameras || !corrections || !cost || !count || !H || !g || !scratch)
+        return GS_ERR_INVALID_ARG;
+    if (num_images < 1 || num_corr < 1 || width < 2 || height < 2 || params->stride < 1) return GS_ERR_INVALID_ARG;
+    if (scratch_bytes < pho_scratch_bytes(num_edges)) return GS_ERR_INVALID_ARG;
+    PhoArgs a;
+    a.edges = edges;
+    a.num_images = num_images;
+    a.num_corr = num_corr;
+    a.width = width;
+    a.height = height;
+    a.stride = params->stride;
+    a.images = images;
+    a.depths = depths;
+    a.cams = cameras;
+    a.corrs = corrections;
+    a.huber_delta = params->huber_delta;
+    a.near_plane = params->near_plane;
+    a.partials = static_cast<double *>(scratch);
+    a.cost = cost;
+    a.H = H;
+    a.g = g;
+    a.count = count;
+    const int rc = launch_pho(a, num_edges, (cudaStream_t)stream);
+    count_launches(2);
+    return rc != GS_OK ? rc : check_launch();
 }
 
 int gs_adam_step(int64_t n, const gs_adam_state *st, const gs_grads *grads, const float lr[5], int32_t zero_grads,

@@ -107,7 +107,32 @@ int launch_prune(long long n, const gs_gaussians &in, float thr, const gs_gaussi
                  void *scratch, cudaStream_t s);
 int launch_view_adam(int V, const gs_view_adam_state &st, const float *pose_grad, const float *expo_grad, float lr_pose,
                      float lr_expo, cudaStream_t s);
+int launch_voxset_clear(void *mem, long long capacity, cudaStream_t s);
+int launch_voxset_add_boxes(void *mem, long long capacity, long long n, const float *means, const float *log_scales,
+                            float k, float v, cudaStream_t s);
+int launch_voxset_add_rays(void *mem, long long capacity, int V, int W, int H, const gs_camera *cams,
+                           const float *depth, int stride, float v, cudaStream_t s);
+int launch_voxset_keep(long long n, const float *means, void *occ, long long occ_cap, void *fre, long long free_cap,
+                       float v, uint8_t *keep, cudaStream_t s);
+int launch_sim3(long long n, const gs_gaussians &in, const float q[4], const float t[3], float sc,
+                const gs_gaussian_arrays &out, cudaStream_t s);
 int launch_adam(long long n, const gs_adam_state &st, const gs_grads &g, const float lr[5], int zero_grads,
                 cudaStream_t s, float iso_weight = 0.f, double *iso_loss = nullptr);
+
+// Eq. 12 photometric residual blocks (gs_photometric.cu)
+constexpr int kPhoMaxBlocksPerEdge = 1024;
+struct PhoArgs {
+    const gs_pho_edge *edges;
+    int num_images, num_corr, width, height, stride;
+    const float *images, *depths;
+    const gs_camera *cams;
+    const gs_sim3 *corrs;
+    float huber_delta, near_plane;
+    double *partials;                  // [edges, blocks per edge, 40]
+    double *cost, *H, *g;
+    int64_t *count;
+};
+size_t pho_scratch_bytes(int num_edges);
+int launch_pho(const PhoArgs &a, int num_edges, cudaStream_t s);
 
 }  // namespace gs

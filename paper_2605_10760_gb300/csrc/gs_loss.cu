@@ -31,27 +31,58 @@ __device__ __forceinline__ void block_add_double(double v, double *out) {
     }
 }
 
-__global__ void k_l1(long long HWn, int V, const float *rgb, const float *rgb_t, const float *depth,
-                     const float *depth_t, float sc_rgb, float sc_d, float *d_rgb, float *d_depth, double *loss) {
+// grid (blocks, V): view v = blockIdx.y; pixels of the view strided over the x-blocks, four at a
+// time (16-byte loads and stores) when the plane size and the pointers allow it.
+template <bool kVec>
+__global__ void k_l1(long long HWn, const float *rgb, const float *rgb_t, const float *depth, const float *depth_t,
+                     float sc_rgb, float sc_d, float *d_rgb, float *d_depth, double *loss) {
     float acc_rgb = 0.f, acc_d = 0.f;      // per-thread sums of |d| (a few dozen terms each)
-    const long long total = (long long)V * HWn;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const long long v = i / HWn, p = i - v * HWn;
+    const long long v = blockIdx.y;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (kVec) {
+        const long long n4 = HWn >> 2;
+        for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const long long idx = (3 * v + c) * HWn + p;
-            const float d = rgb[idx] - rgb_t[idx];
-            acc_rgb += fabsf(d);
-            d_rgb[idx] = sgnf(d) * sc_rgb;
+            for (int c = 0; c < 3; ++c) {
+                const long long off = (3 * v + c) * n4 + q;
+                const float4 x = reinterpret_cast<const float4 *>(rgb)[off];
+                const float4 y = reinterpret_cast<const float4 *>(rgb_t)[off];
+                const float4 d = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+                acc_rgb += (fabsf(d.x) + fabsf(d.y)) + (fabsf(d.z) + fabsf(d.w));
+                reinterpret_cast<float4 *>(d_rgb)[off] =
+                    make_float4(sgnf(d.x) * sc_rgb, sgnf(d.y) * sc_rgb, sgnf(d.z) * sc_rgb, sgnf(d.w) * sc_rgb);
+            }
+            if (depth) {
+                const long long off = v * n4 + q;
+                const float4 x = reinterpret_cast<const float4 *>(depth)[off];
+                const float4 y = reinterpret_cast<const float4 *>(depth_t)[off];
+                const float4 d = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+                acc_d += (fabsf(d.x) + fabsf(d.y)) + (fabsf(d.z) + fabsf(d.w));
+                reinterpret_cast<float4 *>(d_depth)[off] =
+                    make_float4(sgnf(d.x) * sc_d, sgnf(d.y) * sc_d, sgnf(d.z) * sc_d, sgnf(d.w) * sc_d);
+            }
         }
-        if (depth && d_depth) {
-            const float d = depth[i] - depth_t[i];
-            acc_d += fabsf(d);
-            d_depth[i] = sgnf(d) * sc_d;
+    } else {
+        for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < HWn; p += stride) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const long long idx = (3 * v + c) * HWn + p;
+                const float d = rgb[idx] - rgb_t[idx];
+                acc_rgb += fabsf(d);
+                d_rgb[idx] = sgnf(d) * sc_rgb;
+            }
+            if (depth) {
+                const long long idx = v * HWn + p;
+                const float d = depth[idx] - depth_t[idx];
+                acc_d += fabsf(d);
+                d_depth[idx] = sgnf(d) * sc_d;
+            }
         }
     }
     block_add_double((double)acc_rgb * sc_rgb + (double)acc_d * sc_d, loss);
 }
+
+static bool aligned16(const void *p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
 
 int launch_loss_l1(int V, int W, int H, const float *rgb, const float *rgb_t, const float *depth,
                    const float *depth_t, float w_rgb, float w_depth, float *d_rgb, float *d_depth, double *loss,
@@ -60,11 +91,20 @@ int launch_loss_l1(int V, int W, int H, const float *rgb, const float *rgb_t, co
     const float sc_rgb = (float)((double)w_rgb / (3.0 * V * HWn));
     const float sc_d = (float)((double)w_depth / ((double)V * HWn));
     const bool use_d = depth && depth_t && d_depth && w_depth != 0.f;
-    const long long total = (long long)V * HWn;
-    const int grid = (int)std::min<long long>((total + 255) / 256, (long long)device_sm_count() * 8);
+    const bool vec = (HWn % 4 == 0) && aligned16(rgb) && aligned16(rgb_t) && aligned16(d_rgb) &&
+                     (!use_d || (aligned16(depth) && aligned16(depth_t) && aligned16(d_depth)));
+    const long long units = vec ? HWn / 4 : HWn;
+    // about four resident blocks of 256 threads per SM in total, spread over the views
+    const long long want = std::max<long long>(1, ((long long)device_sm_count() * 4 + V - 1) / V);
+    const int gx = (int)std::max<long long>(1, std::min<long long>((units + 255) / 256, want));
     if (cudaMemsetAsync(loss, 0, sizeof(double), s) != cudaSuccess) return GS_ERR_CUDA;
-    k_l1<<<std::max(grid, 1), 256, 0, s>>>(HWn, V, rgb, rgb_t, use_d ? depth : nullptr, depth_t, sc_rgb, sc_d,
-                                             d_rgb, use_d ? d_depth : nullptr, loss);
+    const dim3 grid(gx, V);
+    if (vec)
+        k_l1<true><<<grid, 256, 0, s>>>(HWn, rgb, rgb_t, use_d ? depth : nullptr, depth_t, sc_rgb, sc_d, d_rgb,
+                                        use_d ? d_depth : nullptr, loss);
+    else
+        k_l1<false><<<grid, 256, 0, s>>>(HWn, rgb, rgb_t, use_d ? depth : nullptr, depth_t, sc_rgb, sc_d, d_rgb,
+                                         use_d ? d_depth : nullptr, loss);
     count_launches(1);
     return check_launch();
 }

@@ -377,3 +377,124 @@ class ViewAdamState:
                                   self.v.data_ptr(), self.step.data_ptr())
         L.check(L.load().gs_view_adam_step(self.pb.V, C.byref(st), _ptr(pose_grad), _ptr(expo_grad), self.lr_pose,
                                            self.lr_expo, _stream()), "gs_view_adam_step")
+
+
+# ------------------------------------------------------------------------------------------
+# occupancy-aware fusion (Sim(3) action, voxel sets, deduplication)
+# ------------------------------------------------------------------------------------------
+
+def sim3_apply(g: Gaussians, q, t, s, out: Gaussians | None = None) -> Gaussians:
+    """Eq. 19: the Sim(3) correction (rotation quaternion q (w,x,y,z), translation t, scale s)."""
+    out = out if out is not None else Gaussians(*[torch.empty_like(getattr(g, k)) for k in
+                                                  ("means", "log_scales", "quats", "opacities", "colors")])
+    c = L.gs_sim3()
+    for i in range(4):
+        c.q[i] = float(q[i])
+    for i in range(3):
+        c.t[i] = float(t[i])
+    c.s = float(s)
+    gi = g.struct()
+    go = L.gs_gaussian_arrays(*[getattr(out, k).data_ptr() for k in ("means", "log_scales", "quats", "opacities",
+                                                                      "colors")])
+    L.check(L.load().gs_sim3_apply(g.n, C.byref(gi), C.byref(c), C.byref(go), _stream()), "gs_sim3_apply")
+    return out
+
+
+class VoxSet:
+    """A device hash set of packed voxel keys (Eqs. 20-22)."""
+
+    def __init__(self, capacity: int, device="cuda"):
+        cap = 1
+        while cap < capacity:
+            cap <<= 1
+        self.capacity = max(cap, 2)
+        self.mem = torch.empty(int(L.load().gs_voxset_bytes(self.capacity)), dtype=torch.uint8, device=device)
+        self.clear()
+
+    def clear(self):
+        L.check(L.load().gs_voxset_clear(_ptr(self.mem), self.capacity, _stream()), "gs_voxset_clear")
+
+    def add_boxes(self, means, log_scales, k, voxel):
+        L.check(L.load().gs_voxset_add_boxes(_ptr(self.mem), self.capacity, int(means.shape[0]), _ptr(means),
+                                             _ptr(log_scales), float(k), float(voxel), _stream()), "gs_voxset_add_boxes")
+
+    def add_rays(self, cams, depth, stride, voxel):
+        V, H, W = depth.shape
+        L.check(L.load().gs_voxset_add_rays(_ptr(self.mem), self.capacity, V, W, H, _ptr(cams), _ptr(depth),
+                                            int(stride), float(voxel), _stream()), "gs_voxset_add_rays")
+
+    def status(self):
+        """(recorded error code, number of stored keys); synchronises."""
+        n = C.c_int64()
+        rc = L.load().gs_voxset_status(_ptr(self.mem), _stream(), C.byref(n), self.capacity)
+        return rc, int(n.value)
+
+    def keys(self) -> set:
+        k = self.mem[256:256 + 8 * self.capacity].view(torch.int64).cpu().numpy().view(np.uint64)
+        return set(int(x) for x in k[k != np.uint64(0xFFFFFFFFFFFFFFFF)])
+
+
+def dedup_keep(means, occ: VoxSet, free: VoxSet | None, voxel) -> torch.Tensor:
+    """Eq. 22: uint8 keep flag per borrowed Gaussian."""
+    n = int(means.shape[0])
+    keep = torch.empty(n, dtype=torch.uint8, device=means.device)
+    L.check(L.load().gs_voxset_keep(n, _ptr(means), _ptr(occ.mem), occ.capacity,
+                                    None if free is None else _ptr(free.mem), 0 if free is None else free.capacity,
+                                    float(voxel), _ptr(keep), _stream()), "gs_voxset_keep")
+    return keep
+
+
+# ------------------------------------------------------------------------------------------
+# anchor-image photometric residuals of the submap pose graph (Eq. 12)
+# ------------------------------------------------------------------------------------------
+
+def pho_edges(edges, device="cuda") -> torch.Tensor:
+    """Device array of gs_pho_edge from [(src_image, tgt_image, src_corr, tgt_corr, weight)]."""
+    n = len(edges)
+    raw = np.zeros((max(n, 1), 8), np.int32)
+    for i, (a, b, ca, cb, w) in enumerate(edges):
+        raw[i, :4] = (a, b, ca, cb)
+        raw[i, 4] = np.array([w], np.float32).view(np.int32)[0]
+    return torch.from_numpy(raw[:n].copy()).to(device)
+
+
+def sim3_tensor(corrs, device="cuda") -> torch.Tensor:
+    """[C, 8] float32 device array of gs_sim3 from [(q[4], t[3], s)]."""
+    return torch.tensor(np.array([np.concatenate([np.asarray(q, np.float32), np.asarray(t, np.float32),
+                                                  [np.float32(s)]]) for q, t, s in corrs], np.float32),
+                        device=device)
+
+
+class PhoResidual:
+    """Eq. 12 photometric blocks of a batch of pose-graph edges (gs_pho_residual); the scratch is
+    allocated once for `max_edges`."""
+
+    def __init__(self, max_edges: int, device="cuda"):
+        self.max_edges = max(1, int(max_edges))
+        self.scratch = torch.empty(int(L.load().gs_pho_scratch_size(self.max_edges)), dtype=torch.uint8,
+                                   device=device)
+
+    def __call__(self, edges, images, depths, cams, corrs, stride=1, huber_delta=None, near_plane=None, out=None):
+        """edges: device [E, 8] int32 (pho_edges); images [M, 3, H, W]; depths [M, H, W]; cams [M, 16];
+        corrs [C, 8].  Returns dict(cost [E] f64, count [E] i64, H [E, 14, 14] f64, g [E, 14] f64)."""
+        E = int(edges.shape[0])
+        if E > self.max_edges:
+            raise ValueError("more edges than the scratch was sized for")
+        M, _, Hh, W = images.shape
+        p = L.load().gs_default_pho_params()
+        p.stride = int(stride)
+        if huber_delta is not None:
+            p.huber_delta = float(huber_delta)
+        if near_plane is not None:
+            p.near_plane = float(near_plane)
+        dev = images.device
+        o = out or dict(cost=torch.empty(E, dtype=torch.float64, device=dev),
+                        count=torch.empty(E, dtype=torch.int64, device=dev),
+                        H=torch.empty(E, 14, 14, dtype=torch.float64, device=dev),
+                        g=torch.empty(E, 14, dtype=torch.float64, device=dev))
+        L.check(L.load().gs_pho_residual(E, _ptr(edges), M, W, Hh, _ptr(images), _ptr(depths), _ptr(cams),
+                                         int(corrs.shape[0]), _ptr(corrs), C.byref(p), _ptr(o["cost"]),
+                                         _ptr(o["count"]), _ptr(o["H"]), _ptr(o["g"]), _ptr(self.scratch),
+                                         self.scratch.numel(), _stream()), "gs_pho_residual")
+        return o
+
