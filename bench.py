@@ -598,9 +598,20 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the graph-loop and 4M/64-view measurements")
+    ap.add_argument("--only", choices=["photometric", "fusion", "mapping", "refine"],
+                    help="run one secondary measurement alone and print its JSON (not the headline line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.only:
+        import torch
+        from paper_2605_10760_gb300 import raster as R
+        from paper_2605_10760_gb300 import scenes as S
+        R.L.load()
+        fn = {"photometric": pho_bench, "fusion": fusion_bench, "mapping": mapping_graph,
+              "refine": refine_graph}[args.only]
+        print(json.dumps({"section": args.only, "result": fn(R, S, torch)}))
+        return 0
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -649,9 +660,9 @@ def main():
         "pose_grad": 0,
     }
     fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s at max SM clock
-    # DRAM bytes (read + write) of one launch from an ncu capture of this workload; see
-    # profiles/render_bwd_room500k.md (None for a stage without a capture of its current code)
-    traffic = {"render_bwd": 35207424}
+    # DRAM bytes (read + write) of one launch from an ncu capture of this workload's current
+    # kernel code (profiles/*_room500k.md); a stage without such a capture reports None
+    traffic = {}
     if dom in ("render_fwd", "render_bwd"):
         flops = stats["fwd_pairs"] * FLOP_FWD if dom == "render_fwd" else stats["bwd_pairs"] * FLOP_BWD
         ach = flops / (stage_ms[dom] * 1e-3) / 1e12

@@ -25,7 +25,8 @@ Readings (the paper gives none of these): the robust norm is Huber with delta = 
 centres at +0.5 (as in the rasterizer); near plane 0.2; the anchor depth is the keyframe's z-depth.
 The membership of U_e and the bilinear cell are integer decisions: they are taken in FP32 with the
 fixed operation sequence of `decision_chain` (IEEE-rounded multiply, add, subtract, divide and
-square root, no fused multiply-add), values in FP64.
+square root, no fused multiply-add; divisions by f_x, f_y and s_tgt are multiplications by their
+rounded reciprocals, and 1 / c_z is rounded once per pixel), values in FP64.
 """
 from __future__ import annotations
 
@@ -75,9 +76,9 @@ def decision_chain(cam_s, cam_t, sim_s, sim_t, W, H, depth, stride=1, near=NEAR)
     Rs, ts = cs[:9].reshape(3, 3), cs[9:12]
     Ra, ta = ct[:9].reshape(3, 3), ct[9:12]
     with np.errstate(all="ignore"):
-        xn = F(F(xs.astype(F) + F(0.5)) - cs[14]) / cs[12]
-        yn = F(F(ys.astype(F) + F(0.5)) - cs[15]) / cs[13]
-        xn, yn = xn.astype(F), yn.astype(F)
+        ifx, ify = F(F(1.0) / cs[12]), F(F(1.0) / cs[13])
+        xn = (F(F(xs.astype(F) + F(0.5)) - cs[14]) * ifx).astype(F)
+        yn = (F(F(ys.astype(F) + F(0.5)) - cs[15]) * ify).astype(F)
         pc = [(F(xn * d) - ts[0]).astype(F), (F(yn * d) - ts[1]).astype(F), (d - ts[2]).astype(F)]
         p = _mtv(Rs, pc)
         Q1 = quat_matrix_f32(sim_s[0])
@@ -88,11 +89,13 @@ def decision_chain(cam_s, cam_t, sim_s, sim_t, W, H, depth, stride=1, near=NEAR)
         w = [(F(s1 * rp[i]) + t1[i]).astype(F) for i in range(3)]
         dw = [(w[i] - t2[i]).astype(F) for i in range(3)]
         rq = _mtv(Q2, dw)
-        q = [(rq[i] / s2).astype(F) for i in range(3)]
+        is2 = F(F(1.0) / s2)
+        q = [(rq[i] * is2).astype(F) for i in range(3)]
         rc = _mv(Ra, q)
         c = [(rc[i] + ta[i]).astype(F) for i in range(3)]
-        px = (F(ct[12] * F(c[0] / c[2])) + ct[14]).astype(F)
-        py = (F(ct[13] * F(c[1] / c[2])) + ct[15]).astype(F)
+        iz = (F(1.0) / c[2]).astype(F)
+        px = (F(ct[12] * F(c[0] * iz)) + ct[14]).astype(F)
+        py = (F(ct[13] * F(c[1] * iz)) + ct[15]).astype(F)
         sx, sy = (px - F(0.5)).astype(F), (py - F(0.5)).astype(F)
         valid = (d > 0) & (d < np.inf) & (c[2] > F(near))
         valid &= (sx >= 0) & (sx < F(W - 1)) & (sy >= 0) & (sy < F(H - 1))

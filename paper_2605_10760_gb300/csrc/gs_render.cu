@@ -1,7 +1,8 @@
 // gs_render.cu -- per-tile compositing (forward) and its adjoint (backward).
 //
-// One CTA = one tile of TW x TH pixels, two vertically adjacent pixels per thread (so a warp covers
-// a compact TW x 4 block when TW = 16).  Both kernels are persistent: a grid of (#SM x resident
+// One CTA = one tile of TW x TH pixels, two vertically adjacent pixels per thread; a warp covers a
+// square 8 x 8 block of the tile (lanes 8 wide, 4 tall, 2 pixels each), the shape whose bounding
+// box a footprint overlaps least, which keeps the per-warp region masks selective.  Both kernels are persistent: a grid of (#SM x resident
 // CTAs) claims (view, tile) work items from a device counter, so one launch covers every tile of
 // every view of every scene, whatever the per-tile list lengths.
 //
@@ -30,6 +31,16 @@
 namespace gs {
 
 constexpr int kPPT = 2;   // pixels per thread
+constexpr int kWX = 8;    // warp block: kWX columns x (32 / kWX) * kPPT rows
+constexpr int kWY = 32 / kWX * kPPT;
+
+// Pixel of a thread inside its tile: warp w takes block (w mod (TW / kWX), w div (TW / kWX)).
+template <int TW>
+__device__ __forceinline__ void thread_pixel(int tid, int &lx, int &ly) {
+    const int w = tid >> 5, lane = tid & 31;
+    lx = (w % (TW / kWX)) * kWX + lane % kWX;
+    ly = (w / (TW / kWX)) * kWY + (lane / kWX) * kPPT;
+}
 
 // Minimum over the box [xa, xb] x [ya, yb] of sigma(d) = 1/2 (A dx^2 + C dy^2) + B dx dy,
 // d = p - mean (a convex quadratic: 0 when the mean is inside, else attained on an edge, where the
@@ -59,22 +70,22 @@ __device__ __forceinline__ float sigma_min_box(float A, float B, float C, float 
     return best;
 }
 
-// Bit w set <=> warp w's block of pixels (TW columns x 2*32/TW rows of the tile) may blend the
-// entry.  A cleared bit means sigma > cut at every pixel of that block: every pixel there skips the
+// Bit w set <=> warp w's block of pixels (kWX x kWY, see thread_pixel) may blend the entry.  A cleared bit means sigma > cut at every pixel of that block: every pixel there skips the
 // entry in the decision chain, so the warp may skip it without evaluating anything.  The margin
 // (0.01 + 1e-3 |cut|) is far above the FP32 error of either sigma evaluation.
 template <int TW, int TH>
 __device__ __forceinline__ uint32_t warp_region_mask(const float4 &r0, const float4 &r1, float cut, int tile_x0,
                                                      int tile_y0) {
     constexpr int NW = TW * TH / (kPPT * 32);
-    constexpr int ROWS = kPPT * 32 / TW;
+    static_assert(TW % kWX == 0 && TH % kWY == 0, "tile must hold whole warp blocks");
     const float thr = cut + 0.01f + 1e-3f * fabsf(cut);
-    const float xa = (float)tile_x0 + 0.5f, xb = (float)(tile_x0 + TW) - 0.5f;
     uint32_t m = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
-        const float ya = (float)(tile_y0 + w * ROWS) + 0.5f;
-        const float s = sigma_min_box(r0.z, r0.w, r1.x, r0.x, r0.y, xa, xb, ya, ya + (float)(ROWS - 1));
+        const float xa = (float)(tile_x0 + (w % (TW / kWX)) * kWX) + 0.5f;
+        const float ya = (float)(tile_y0 + (w / (TW / kWX)) * kWY) + 0.5f;
+        const float s = sigma_min_box(r0.z, r0.w, r1.x, r0.x, r0.y, xa, xa + (float)(kWX - 1), ya,
+                                      ya + (float)(kWY - 1));
         if (!(s > thr)) m |= 1u << w;
     }
     return m;
@@ -119,7 +130,8 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
     const uint32_t wbit = 1u << (tid >> 5);
     const long long tpv = (long long)a.Tx * a.Ty;
     const long long HW = (long long)a.W * a.H;
-    const int lx = tid % TW, ly = (tid / TW) * kPPT;
+    int lx, ly;
+    thread_pixel<TW>(tid, lx, ly);
     if (tid == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
@@ -313,7 +325,8 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
     const bool issuer = ((lane & 1) == 0) && (slot < 5 || (slot >= 8 && slot < 13));
     const long long tpv = (long long)a.Tx * a.Ty;
     const long long HW = (long long)a.W * a.H;
-    const int lx = tid % TW, ly = (tid / TW) * kPPT;
+    int lx, ly;
+    thread_pixel<TW>(tid, lx, ly);
     if (tid == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);

@@ -206,8 +206,8 @@ def test_decision_chain_is_fp32_and_brute_force_membership():
     for k in range(len(xs)):
         x, y = xs[k], ys[k]
         d = F(dep[y, x])
-        xn = F(F(F(F(x) + F(0.5)) - cam_s[14]) / cam_s[12])
-        yn = F(F(F(F(y) + F(0.5)) - cam_s[15]) / cam_s[13])
+        xn = F(F(F(F(x) + F(0.5)) - cam_s[14]) * F(F(1) / cam_s[12]))
+        yn = F(F(F(F(y) + F(0.5)) - cam_s[15]) * F(F(1) / cam_s[13]))
         pc = [F(F(xn * d) - cam_s[9]), F(F(yn * d) - cam_s[10]), F(d - cam_s[11])]
         Rs = cam_s[:9].reshape(3, 3)
         p = [F(F(F(Rs[0, i] * pc[0]) + F(Rs[1, i] * pc[1])) + F(Rs[2, i] * pc[2])) for i in range(3)]
@@ -215,11 +215,12 @@ def test_decision_chain_is_fp32_and_brute_force_membership():
         w = [F(F(sim_s[2] * rp[i]) + sim_s[1][i]) for i in range(3)]
         dw = [F(w[i] - sim_t[1][i]) for i in range(3)]
         rq = [F(F(F(Q2[0, i] * dw[0]) + F(Q2[1, i] * dw[1])) + F(Q2[2, i] * dw[2])) for i in range(3)]
-        q = [F(rq[i] / sim_t[2]) for i in range(3)]
+        q = [F(rq[i] * F(F(1) / sim_t[2])) for i in range(3)]
         Ra = cam_t[:9].reshape(3, 3)
         c = [F(F(F(F(Ra[i, 0] * q[0]) + F(Ra[i, 1] * q[1])) + F(Ra[i, 2] * q[2])) + cam_t[9 + i]) for i in range(3)]
-        px = F(F(cam_t[12] * F(c[0] / c[2])) + cam_t[14])
-        py = F(F(cam_t[13] * F(c[1] / c[2])) + cam_t[15])
+        iz = F(F(1) / c[2])
+        px = F(F(cam_t[12] * F(c[0] * iz)) + cam_t[14])
+        py = F(F(cam_t[13] * F(c[1] * iz)) + cam_t[15])
         assert px - F(0.5) == sx[k] and py - F(0.5) == sy[k]
         ok = d > 0 and np.isfinite(d) and c[2] > F(0.2) and 0 <= F(px - F(0.5)) < W_ - 1 and 0 <= F(py - F(0.5)) < H_ - 1
         assert bool(ok) == bool(valid[k])
