@@ -189,13 +189,26 @@ class Pipeline:
             with torch.cuda.graph(gr):
                 fn()
             self.graphs.append(gr)
+        self.whole = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.whole):
+            for fn in self.stages():
+                fn()
         torch.cuda.synchronize()
 
     def step_graph(self, ev=None):
+        """Per-stage graphs with events between them (the stage breakdown)."""
         for i, gr in enumerate(self.graphs):
             if ev:
                 ev[i].record()
             gr.replay()
+        if ev:
+            ev[len(STAGES)].record()
+
+    def step_whole(self, ev=None):
+        """The whole step as one graph launch (events only around it)."""
+        if ev:
+            ev[0].record()
+        self.whole.replay()
         if ev:
             ev[len(STAGES)].record()
 
@@ -225,8 +238,8 @@ def max_over_ranks(x, dist, device):
     return float(t.item())
 
 
-def time_steps(pipe, steps, warmup, flush_buf, torch, graphs=True, barrier=None):
-    run = pipe.step_graph if graphs else pipe.step
+def time_steps(pipe, steps, warmup, flush_buf, torch, graphs=True, barrier=None, whole=False):
+    run = (pipe.step_whole if whole else pipe.step_graph) if graphs else pipe.step
     for _ in range(warmup):
         run()
     torch.cuda.synchronize()
@@ -247,44 +260,71 @@ def time_steps(pipe, steps, warmup, flush_buf, torch, graphs=True, barrier=None)
             barrier()
         clk.mark_end()
     step_ms = [e[0].elapsed_time(e[len(STAGES)]) for e in evs]
-    stage_ms = {s: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, s in enumerate(STAGES)}
+    stage_ms = None if whole and graphs else {
+        s: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, s in enumerate(STAGES)}
     return step_ms, stage_ms, clk.summary()
 
 
-def time_e2e(pipe, steps, torch, flush_buf):
-    """Same step through host buffers: H2D of the Gaussians, camera and targets from pinned memory,
-    D2H of the loss, pose gradient and Gaussian gradients, all inside the timed region."""
-    g = pipe.g
-    host_in = {k: getattr(g, k).cpu().pin_memory() for k in ("means", "log_scales", "quats", "opacities", "colors")}
-    host_cam = pipe.pb.cameras.cpu().pin_memory()
-    host_t = pipe.rgb_t.cpu().pin_memory()
-    host_dt = pipe.depth_t.cpu().pin_memory()
-    out_g = {k: torch.empty_like(getattr(g, k), device="cpu").pin_memory() for k in host_in}
-    out_loss = torch.empty(1, dtype=torch.float64).pin_memory()
-    out_pose = torch.empty(pipe.V, 6).pin_memory()
+def time_e2e(pipes, steps, torch, flush_buf):
+    """Same step through host buffers, software-pipelined over two device copies of the problem:
+    every step copies its Gaussians, camera and targets in from pinned host memory (copy stream),
+    flushes L2 and runs the step (compute stream), and copies the loss, pose gradient and Gaussian
+    gradients out to pinned host memory (second copy stream); step i's input copy overlaps step
+    i-1's compute and step i-2's output copy.  The time runs from before the first input copy to
+    after the last output copy; per step = total / steps."""
+    host_in = {k: getattr(pipes[0].g, k).cpu().pin_memory() for k in ("means", "log_scales", "quats", "opacities",
+                                                                      "colors")}
+    host_cam = pipes[0].pb.cameras.cpu().pin_memory()
+    host_t = pipes[0].rgb_t.cpu().pin_memory()
+    host_dt = pipes[0].depth_t.cpu().pin_memory()
+    outs = []
+    for p in pipes:
+        outs.append(dict(g={k: torch.empty_like(getattr(p.g, k), device="cpu").pin_memory() for k in host_in},
+                         loss=torch.empty(1, dtype=torch.float64).pin_memory(),
+                         pose=torch.empty(p.V, 6).pin_memory()))
     h2d = sum(t.numel() * t.element_size() for t in host_in.values()) + host_cam.numel() * 4 + \
         host_t.numel() * 4 + host_dt.numel() * 4
-    d2h = sum(t.numel() * t.element_size() for t in out_g.values()) + 8 + out_pose.numel() * 4
-    times = []
-    for i in range(steps + 2):
-        l2_flush(flush_buf)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for k, t in host_in.items():
-            getattr(g, k).copy_(t, non_blocking=True)
-        pipe.pb.cameras.copy_(host_cam, non_blocking=True)
-        pipe.rgb_t.copy_(host_t, non_blocking=True)
-        pipe.depth_t.copy_(host_dt, non_blocking=True)
-        pipe.step()
-        out_loss.copy_(pipe.loss, non_blocking=True)
-        out_pose.copy_(pipe.pose, non_blocking=True)
-        for k, t in out_g.items():
-            t.copy_(getattr(pipe.grads, k), non_blocking=True)
-        b.record()
+    d2h = sum(t.numel() * t.element_size() for t in outs[0]["g"].values()) + 8 + outs[0]["pose"].numel() * 4
+    comp = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run(n):
+        ev_comp, ev_out = [None, None], [None, None]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(comp)
+        s_in.wait_event(start)
+        for i in range(n):
+            b = i % 2
+            p, o = pipes[b], outs[b]
+            with torch.cuda.stream(s_in):
+                if ev_comp[b] is not None:
+                    s_in.wait_event(ev_comp[b])        # the last step on this copy has read its inputs
+                for k, t in host_in.items():
+                    getattr(p.g, k).copy_(t, non_blocking=True)
+                p.pb.cameras.copy_(host_cam, non_blocking=True)
+                p.rgb_t.copy_(host_t, non_blocking=True)
+                p.depth_t.copy_(host_dt, non_blocking=True)
+                e_in = s_in.record_event()
+            comp.wait_event(e_in)
+            if ev_out[b] is not None:
+                comp.wait_event(ev_out[b])             # its previous results have been copied out
+            l2_flush(flush_buf)
+            p.step()
+            ev_comp[b] = comp.record_event()
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_comp[b])
+                o["loss"].copy_(p.loss, non_blocking=True)
+                o["pose"].copy_(p.pose, non_blocking=True)
+                for k, t in o["g"].items():
+                    t.copy_(getattr(p.grads, k), non_blocking=True)
+                ev_out[b] = s_out.record_event()
+        end.record(s_out)
         torch.cuda.synchronize()
-        if i >= 2:
-            times.append(a.elapsed_time(b))
-    return statistics.mean(times), h2d, d2h
+        return start.elapsed_time(end) / n
+
+    run(4)                                             # warm-up
+    ms = run(steps)
+    return ms, h2d, d2h
 
 
 def batched_speedup(R, S, torch, flush_buf, reps=3):
@@ -350,11 +390,28 @@ def mapping_graph(R, S, torch, iters=100, reps=2):
         times.append(a.elapsed_time(b))
     rc, req = pb.check_status()
     ms_iter = statistics.median(times) / iters
+    # the same loop with Eq. 4's isotropy regulariser (lambda_s = 10) fused into the Adam step
+    pb_iso = make(R.default_params(tile_w=tw, tile_h=th))
+    loop_iso = M.MappingLoop(pb_iso, R.Gaussians.from_scene(wl.scene), tgt, iso_weight=10.0)
+    loop_iso.capture(iters)
+    loop_iso.replay()
+    torch.cuda.synchronize()
+    t_iso = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        loop_iso.replay()
+        b.record()
+        torch.cuda.synchronize()
+        t_iso.append(a.elapsed_time(b))
+    rc_iso, _ = pb_iso.check_status()
     return {"workload": "room1m: 1M-Gaussian room, 8 views 1200x680, 0.8 L1 + 0.2 (1-SSIM), Adam, "
                         "%d iterations per CUDA graph" % iters,
             "tile": [tw, th], "autotune": table, "ms_per_iteration": ms_iter,
             "iterations_per_s": 1e3 / ms_iter, "views_per_s": V * 1e3 / ms_iter,
-            "loss_after": float(loop.loss.item()), "status": rc or rc0, "required_keys": req}
+            "loss_after": float(loop.loss.item()), "status": rc or rc0, "required_keys": req,
+            "with_isotropy": {"lambda_s": 10.0, "ms_per_iteration": statistics.median(t_iso) / iters,
+                              "status": rc_iso}}
 
 
 def refine_graph(R, S, torch, iters=100, reps=2):
@@ -598,7 +655,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the graph-loop and 4M/64-view measurements")
-    ap.add_argument("--only", choices=["photometric", "fusion", "mapping", "refine"],
+    ap.add_argument("--only", choices=["photometric", "fusion", "mapping", "refine", "fused", "batched"],
                     help="run one secondary measurement alone and print its JSON (not the headline line)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -608,8 +665,9 @@ def main():
         from paper_2605_10760_gb300 import raster as R
         from paper_2605_10760_gb300 import scenes as S
         R.L.load()
-        fn = {"photometric": pho_bench, "fusion": fusion_bench, "mapping": mapping_graph,
-              "refine": refine_graph}[args.only]
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        fn = {"photometric": pho_bench, "fusion": fusion_bench, "mapping": mapping_graph, "refine": refine_graph,
+              "fused": fused_map, "batched": lambda R, S, torch: batched_speedup(R, S, torch, flush)}[args.only]
         print(json.dumps({"section": args.only, "result": fn(R, S, torch)}))
         return 0
 
@@ -635,14 +693,18 @@ def main():
     pipe.capture()
     eager_ms, eager_stage_ms, _ = time_steps(pipe, max(5, args.steps // 3), 2, flush, torch, graphs=False)
     barrier = dist.barrier if world > 1 else None
-    step_ms, stage_ms, clocks = time_steps(pipe, args.steps, args.warmup, flush, torch, graphs=True, barrier=barrier)
+    _, stage_ms, _ = time_steps(pipe, args.steps, args.warmup, flush, torch, graphs=True)
+    step_ms, _, clocks = time_steps(pipe, args.steps, args.warmup, flush, torch, graphs=True, barrier=barrier,
+                                    whole=True)
     total_ms = sum(step_ms)
     if world > 1:
         total_ms = max_over_ranks(total_ms, dist, "cuda")
     rc, _ = pipe.pb.check_status()
     ms = total_ms / args.steps
     value = world * pipe.V / (ms / 1e3)
-    e2e_ms, h2d, d2h = time_e2e(pipe, max(3, args.steps // 3), torch, flush)
+    pipe2 = Pipeline(R, S, wl, rank_views(S, wl, rank, world))
+    e2e_ms, h2d, d2h = time_e2e([pipe, pipe2], args.steps, torch, flush)
+    del pipe2
     stats = pipe.pb.stats()
     if rank != 0:
         dist.barrier()
@@ -651,18 +713,22 @@ def main():
     # roofline of the dominant stage
     dom = max(stage_ms, key=stage_ms.get)
     P, K = pipe.pb.P, stats["num_keys"]
-    passes = pipe.pb.workspace()["passes"]
+    wsv = pipe.pb.workspace()
+    passes = wsv["passes"]
+    onesweep = pipe.pb.params.sort_mode == R.L.GS_SORT_ONESWEEP
+    vis = int((wsv["tiles_touched"] != 0).sum().item()) if not onesweep else 0
     npx = pipe.V * pipe.pb.W * pipe.pb.H
     alg_bytes = {
         "project": P * 60 + 0,
-        "bin_sort": P * 8 + K * 12 + K * 8 + passes * K * 24 + K * 8 + pipe.pb.V * 3225 * 8,
+        "bin_sort": (P * 8 + K * 12 + K * 8 + passes * K * 24 + K * 8 + pipe.pb.V * 3225 * 8) if onesweep else
+                    (pipe.pb.V * 3225 * 8 + vis * 32 + K * 12 + K * 116),
         "loss": npx * 48,
         "pose_grad": 0,
     }
     fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s at max SM clock
     # DRAM bytes (read + write) of one launch from an ncu capture of this workload's current
     # kernel code (profiles/*_room500k.md); a stage without such a capture reports None
-    traffic = {}
+    traffic = {"render_bwd": 35195904}
     if dom in ("render_fwd", "render_bwd"):
         flops = stats["fwd_pairs"] * FLOP_FWD if dom == "render_fwd" else stats["bwd_pairs"] * FLOP_BWD
         ach = flops / (stage_ms[dom] * 1e-3) / 1e12
@@ -689,8 +755,9 @@ def main():
                    "keys": K, "fwd_pairs": stats["fwd_pairs"], "bwd_pairs": stats["bwd_pairs"],
                    "status": rc},
         "stages_ms": stage_ms,
-        "timing": "each stage replayed as its own CUDA graph, events between stages; eager (host-issued) "
-                  "step for comparison in eager_ms_per_step",
+        "timing": "value: the whole step replayed as one CUDA graph, events around each step, L2 flushed "
+                  "before each; stages_ms: each stage as its own graph with events between stages; eager "
+                  "(host-issued) step for comparison in eager_ms_per_step",
         "eager_ms_per_step": statistics.mean(eager_ms), "eager_stages_ms": eager_stage_ms,
         "roofline": roof,
         "e2e": {"value": world * pipe.V / (e2e_ms / 1e3), "unit": "views/s", "h2d_bytes_per_step": h2d,

@@ -67,9 +67,22 @@ typedef struct gs_camera {
     float fx, fy, cx, cy;
 } gs_camera;
 
+/* Binning algorithms of gs_bin_sort.  Both produce the same lists bit for bit: every tile's
+ * entries ordered by (depth bits, flattened pair index).
+ *   GS_SORT_ONESWEEP (default): scan of tiles_touched, keys (tile << 32 | depth bits) in emission
+ *     order and a stable LSD onesweep radix sort over all keys (8-bit digits, decoupled look-back).
+ *   GS_SORT_TILE_BUCKET: gs_project counts the keys of every tile, a scan of the G counts gives
+ *     each tile its slice, emission drops each key into its tile's slice by atomic slot taking
+ *     (order inside the slice arbitrary), and each tile's slice is sorted by (depth bits, pair
+ *     index) in shared memory (a warp per slice of at most 128 entries, a CTA per longer slice,
+ *     slices longer than 4096 entries as sorted runs merged in global memory).  No global sort,
+ *     but one atomic per key twice; measured slower than the onesweep path on GB300 except for
+ *     small single-view problems. */
+enum { GS_SORT_TILE_BUCKET = 0, GS_SORT_ONESWEEP = 1 };
+
 /* Rasterizer constants.  gs_default_params() gives tile 16x16, near 0.2, dilation 0.3,
- * radius_sigmas 3, alpha_max 0.99, alpha_min 1/255 (float division), t_min 1e-4, bg 0.
- * Supported tiles: 16x16, 16x8, 32x16. */
+ * radius_sigmas 3, alpha_max 0.99, alpha_min 1/255 (float division), t_min 1e-4, bg 0,
+ * sort_mode GS_SORT_ONESWEEP.  Supported tiles: 16x16, 16x8, 32x16. */
 typedef struct gs_params {
     int32_t tile_w, tile_h;
     float near_plane;
@@ -79,6 +92,7 @@ typedef struct gs_params {
     float alpha_min;
     float t_min;
     float bg[3];
+    int32_t sort_mode;                 /* GS_SORT_ONESWEEP or GS_SORT_TILE_BUCKET */
 } gs_params;
 
 /* One rendering problem: V views of one or more scenes (agents' submaps) whose Gaussians are
@@ -125,7 +139,8 @@ typedef struct gs_grads {
 
 /* Device pointers into an initialised workspace, for inspection and tests.  Sizes: proj [P,12]
  * float (mean_x, mean_y, conic_A, conic_B | conic_C, opacity, depth, radius | r, g, b, sigma_cut);
- * tiles_touched [P] uint32 (inclusive prefix sums after gs_bin_sort); sorted_keys [K] uint64;
+ * tiles_touched [P] uint32 (counts; inclusive prefix sums after a GS_SORT_ONESWEEP gs_bin_sort);
+ * sorted_keys [K] uint64 (tile << 32 | depth bits);
  * sorted_vals [K] uint32 (flattened pair index p = pair_offset[v] + i); tile_ranges [G,2] uint32
  * with G = V * ceil(W/tile_w) * ceil(H/tile_h); grad2d [P,12] float (dL/d mean_x, mean_y,
  * conic A, B, C, opacity, depth, r, g, b, 0, 0); num_keys -> uint32 K. */
@@ -177,12 +192,14 @@ int gs_read_stats(const gs_problem *pb, void *ws, void *stream, gs_stats *out);
 
 /* EWA projection of every (view, Gaussian) pair (Eq. 19 covariance form, world-to-camera poses
  * of Eq. 15): camera transform, 2-D conic with dilation, radius, tile rectangle, touched-tile
- * count; writes proj and tiles_touched in the workspace. */
+ * count; writes proj and tiles_touched in the workspace (and, with GS_SORT_TILE_BUCKET, the key
+ * count of every tile). */
 int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stream);
 
-/* Tile binning: inclusive scan of tiles_touched, one (tile|depth) key per touched tile, stable
- * onesweep LSD radix sort (8-bit digits, decoupled look-back with bounded waits), per-tile
- * [start, end) ranges.  K > key_capacity records GS_ERR_CAPACITY (keys beyond capacity dropped). */
+/* Tile binning (params.sort_mode selects the algorithm, see GS_SORT_*): per-tile lists ordered by
+ * (depth bits, flattened pair index), their [start, end) ranges, the sorted keys/values and the
+ * projection records in list order.  K > key_capacity records GS_ERR_CAPACITY (keys beyond
+ * capacity dropped). */
 int gs_bin_sort(const gs_problem *pb, void *ws, void *stream);
 
 /* Front-to-back compositing of every (view, tile) of the problem in one persistent launch.

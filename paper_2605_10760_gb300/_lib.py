@@ -18,6 +18,8 @@ GS_ERR_TIMEOUT = -3
 GS_ERR_CUDA = -4
 GS_ERR_DEVICE_FAULT = -5
 GS_ERR_TOO_LARGE = -6
+GS_SORT_TILE_BUCKET = 0
+GS_SORT_ONESWEEP = 1
 GS_SSIM_NOALLOC_MAX_PLANE = 1 << 20
 GS_MAX_VIEWS = 1024
 
@@ -36,7 +38,7 @@ class gs_camera(C.Structure):
 class gs_params(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("near_plane", C.c_float), ("dilation", C.c_float),
                 ("radius_sigmas", C.c_float), ("alpha_max", C.c_float), ("alpha_min", C.c_float),
-                ("t_min", C.c_float), ("bg", C.c_float * 3)]
+                ("t_min", C.c_float), ("bg", C.c_float * 3), ("sort_mode", C.c_int32)]
 
 
 class gs_problem(C.Structure):

@@ -45,7 +45,9 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     if (!(p.alpha_max > 0.f && p.alpha_max < 1.f) || !(p.t_min > 0.f && p.t_min < 1.f) || !(p.alpha_min >= 0.f) ||
         !(p.dilation >= 0.f) || !(p.radius_sigmas > 0.f) || !(p.near_plane > 0.f))
         return GS_ERR_INVALID_ARG;
+    if (p.sort_mode != GS_SORT_TILE_BUCKET && p.sort_mode != GS_SORT_ONESWEEP) return GS_ERR_INVALID_ARG;
     std::memset(L, 0, sizeof(*L));
+    L->sort_mode = p.sort_mode;
     L->V = pb->num_views;
     L->W = pb->width;
     L->H = pb->height;
@@ -71,7 +73,8 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     while ((1LL << gbits) < L->G) ++gbits;
     L->passes = (32 + gbits + 7) / 8;
     if (L->passes > kMaxPasses) return GS_ERR_INVALID_ARG;
-    L->scan_parts = std::max<long long>(1, (P + kScanTile - 1) / kScanTile);
+    // the scan runs over the P touched-tile counts (onesweep) or the G tile key counts (bucket)
+    L->scan_parts = std::max<long long>(1, (std::max(P, L->G) + kScanTile - 1) / kScanTile);
     L->sort_ipt = sort_ipt_for(L->cap);
     const long long sort_tile = (long long)kSortThreads * L->sort_ipt;
     L->sort_parts = std::max<long long>(1, (L->cap + sort_tile - 1) / sort_tile);
@@ -88,6 +91,8 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     L->o_hist = o; o = align256(o + sizeof(uint32_t) * kMaxPasses * 256);
     L->o_sort_state = o; o = align256(o + sizeof(uint32_t) * 256 * (size_t)L->sort_parts * L->passes);
     L->o_ranges = o; o = align256(o + sizeof(uint32_t) * 2 * (size_t)L->G);
+    L->o_tcnt = o; o = align256(o + sizeof(uint32_t) * ((size_t)L->G + 1) + 64);
+    L->o_tlist = o; o = align256(o + sizeof(uint32_t) * (size_t)L->G);
     L->o_srec = o; o = align256(o + sizeof(float) * 12 * (size_t)L->cap);
     L->o_g2d = o; o = align256(o + sizeof(float) * 12 * (size_t)std::max<long long>(P, 1));
     L->o_pose_part = o; o = align256(o + sizeof(float) * 8 * (size_t)std::max<long long>(chunks_total, 1));
@@ -141,6 +146,7 @@ void gs_default_params(gs_params *out) {
     out->alpha_min = 1.0f / 255.0f;
     out->t_min = 1e-4f;
     out->bg[0] = out->bg[1] = out->bg[2] = 0.0f;
+    out->sort_mode = GS_SORT_ONESWEEP;
 }
 
 int gs_workspace_size(const gs_problem *pb, size_t *bytes) {
@@ -249,6 +255,10 @@ int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stre
     if (!ws_ok(ws) || !g || !pb->cameras) return GS_ERR_INVALID_ARG;
     if (L.N > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacities || !g->colors)) return GS_ERR_INVALID_ARG;
     if (((uintptr_t)g->quats & 15) != 0) return GS_ERR_INVALID_ARG;
+    if (L.sort_mode == GS_SORT_TILE_BUCKET &&
+        cudaMemsetAsync(ws_ptr<uint32_t>(ws, L.o_tcnt), 0, sizeof(uint32_t) * ((size_t)L.G + 1),
+                        (cudaStream_t)stream) != cudaSuccess)
+        return GS_ERR_CUDA;
     if (L.P == 0) return GS_OK;
     ProjArgs a;
     a.views = ws_ptr<ViewEntry>(ws, L.o_views);
@@ -261,6 +271,9 @@ int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stre
     a.tw = (float)L.tw; a.th = (float)L.th; a.Tx = (float)L.Tx; a.Ty = (float)L.Ty;
     a.near_plane = pb->params.near_plane; a.dil = pb->params.dilation; a.sigmas = pb->params.radius_sigmas;
     a.alpha_min = pb->params.alpha_min;
+    a.tile_cnt = L.sort_mode == GS_SORT_TILE_BUCKET ? ws_ptr<uint32_t>(ws, L.o_tcnt) : nullptr;
+    a.Txi = L.Tx;
+    a.Ty_i = L.Ty;
     launch_project(L, a, (cudaStream_t)stream);
     return check_launch();
 }
@@ -287,6 +300,9 @@ static BinArgs make_bin_args(const Layout &L, void *ws) {
     a.P = L.P; a.cap = L.cap; a.sort_parts = L.sort_parts; a.max_chunks = L.max_chunks; a.G = L.G;
     a.fault_scan_part = -1;
     a.spin_limit = kSpinLimit;
+    a.sort_mode = L.sort_mode;
+    a.tile_cnt = ws_ptr<uint32_t>(ws, L.o_tcnt);
+    a.tile_list = ws_ptr<uint32_t>(ws, L.o_tlist);
     return a;
 }
 
@@ -346,6 +362,7 @@ int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const g
     b.cams = pb->cameras;
     b.means = g->means; b.log_scales = g->log_scales; b.quats = g->quats;
     b.touched_incl = ws_ptr<const uint32_t>(ws, L.o_touched);
+    b.touched_is_count = L.sort_mode == GS_SORT_TILE_BUCKET ? 1 : 0;
     b.g2d = ws_ptr<const float4>(ws, L.o_g2d);
     b.g_means = grads->means; b.g_ls = grads->log_scales; b.g_quats = grads->quats;
     b.g_op = grads->opacities; b.g_col = grads->colors;

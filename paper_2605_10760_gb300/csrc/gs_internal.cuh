@@ -29,7 +29,10 @@ constexpr int kChunk = 256;            // (view, Gaussian) pairs per projection 
 constexpr unsigned long long kSpinLimit = 1ull << 21;  // bounded waits (x ~100 ns sleep)
 
 // counters inside the status block (zeroed by the call that uses them)
-enum Counter { kCtrScan = 0, kCtrSort0 = 1, kCtrFwd = 12, kCtrBwd = 13, kNumCounters = 32 };
+enum Counter {
+    kCtrScan = 0, kCtrSort0 = 1, kCtrFwd = 12, kCtrBwd = 13, kCtrTileSort = 14, kCtrTileList = 15, kCtrTileLong = 16,
+    kNumCounters = 32
+};
 
 struct DevStatus {
     int32_t code;                 // first recorded GS_ERR_* (0 = none)
@@ -52,8 +55,9 @@ struct Layout {
     int V, W, H, tw, th, Tx, Ty, passes, sort_ipt;
     long long G, P, N, cap, max_count, max_chunks;
     long long scan_parts, sort_parts;
+    int sort_mode;
     size_t o_status, o_views, o_proj, o_touched, o_scan_state, o_keys[2], o_vals[2], o_hist,
-        o_sort_state, o_ranges, o_srec, o_g2d, o_pose_part, total;
+        o_sort_state, o_ranges, o_tcnt, o_tlist, o_srec, o_g2d, o_pose_part, total;
 };
 
 // ------------------------------------------------------------------------------------------
@@ -233,6 +237,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
 }
+
 
 // ------------------------------------------------------------------------------------------
 // TMA bulk copies (cp.async.bulk, 1-D) completing on shared-memory mbarriers

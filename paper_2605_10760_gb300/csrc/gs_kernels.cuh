@@ -15,13 +15,16 @@ struct ProjArgs {
     int W, H;
     float tw, th, Tx, Ty;
     float near_plane, dil, sigmas, alpha_min;
+    uint32_t *tile_cnt;         // [G] key count per global tile (tile-bucket binning), else null
+    int Txi, Ty_i;
 };
 
 struct ProjBwdArgs {
     const ViewEntry *views;
     const gs_camera *cams;
     const float *means, *log_scales, *quats;
-    const uint32_t *touched_incl;   // inclusive prefix sums (nonzero increment = visible)
+    const uint32_t *touched_incl;   // inclusive prefix sums (nonzero increment = visible), or
+    int touched_is_count;           // ... the counts themselves (nonzero = visible) when 1
     const float4 *g2d;              // [P,3] float4
     float *g_means, *g_ls, *g_quats, *g_op, *g_col;
     float *pose_part;               // [chunks, 8]
@@ -53,10 +56,14 @@ struct BinArgs {
     int fault_scan_part;               // -1 normally; >= 0: that scan partition never publishes
     int zero_for_sort;                 // the scan kernel also clears hist, sort_state and ranges
     unsigned long long spin_limit;
+    int sort_mode;                     // GS_SORT_TILE_BUCKET or GS_SORT_ONESWEEP
+    uint32_t *tile_cnt;                // [G + 1] per-tile key counts -> slice starts (bucket mode)
+    uint32_t *tile_list;               // [G] tiles whose slices are sorted by k_tile_sort_long
 };
 
-// runs scan -> emit -> histogram -> digit scan -> onesweep passes -> ranges; the sorted keys end
-// in keys[passes % 2]
+// onesweep: scan -> emit -> histogram -> onesweep passes -> ranges; tile bucket: scan of the
+// tile counts -> emission into tile slices -> per-tile sort.  Either way the sorted keys end in
+// keys[passes % 2], the values in vals[passes % 2], the records in list order in srec
 int run_bin_sort(const BinArgs &a, cudaStream_t s);
 // scan alone (used by the bounded-wait test entry point)
 int run_scan_only(const BinArgs &a, cudaStream_t s);

@@ -18,15 +18,20 @@ __global__ void __launch_bounds__(kChunk) k_project(ProjArgs a) {
     if (threadIdx.x < 16) s_cam[threadIdx.x] = reinterpret_cast<const float *>(a.cams + v)[threadIdx.x];
     __syncthreads();
     const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
-    if (i >= s_ve.count) return;
-    const long long gi = s_ve.gauss_begin + i;
-    const long long f = s_ve.pair_off + i;
-    const float *mu = a.means + 3 * gi;
-    const float *ls = a.log_scales + 3 * gi;
-    const float4 q = __ldg(reinterpret_cast<const float4 *>(a.quats) + gi);
-    SpecProj o = spec_project(s_cam, s_cam + 9, s_cam[12], s_cam[13], s_cam[14], s_cam[15], a.W, a.H, a.tw, a.th,
-                              a.Tx, a.Ty, a.near_plane, a.dil, a.sigmas, __ldg(mu), __ldg(mu + 1), __ldg(mu + 2),
-                              __ldg(ls), __ldg(ls + 1), __ldg(ls + 2), q.x, q.y, q.z, q.w);
+    const bool in = i < s_ve.count;
+    const long long gi = s_ve.gauss_begin + (in ? i : 0);
+    const long long f = s_ve.pair_off + (in ? i : 0);
+    SpecProj o;
+    o.visible = false;
+    o.x0 = o.x1 = o.y0 = o.y1 = 0;
+    if (in) {
+        const float *mu = a.means + 3 * gi;
+        const float *ls = a.log_scales + 3 * gi;
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(a.quats) + gi);
+        o = spec_project(s_cam, s_cam + 9, s_cam[12], s_cam[13], s_cam[14], s_cam[15], a.W, a.H, a.tw, a.th, a.Tx,
+                         a.Ty, a.near_plane, a.dil, a.sigmas, __ldg(mu), __ldg(mu + 1), __ldg(mu + 2), __ldg(ls),
+                         __ldg(ls + 1), __ldg(ls + 2), q.x, q.y, q.z, q.w);
+    }
     uint32_t cnt = 0;
     if (o.visible) {
         cnt = (uint32_t)((o.x1 - o.x0) * (o.y1 - o.y0));
@@ -43,7 +48,12 @@ __global__ void __launch_bounds__(kChunk) k_project(ProjArgs a) {
         rec[1] = make_float4(o.C, op, o.z, o.rf);
         rec[2] = make_float4(__ldg(col), __ldg(col + 1), __ldg(col + 2), cut);
     }
-    a.touched[f] = cnt;
+    if (a.tile_cnt && o.visible) {   // tile-bucket binning: one key per touched tile of this view
+        uint32_t *row = a.tile_cnt + (size_t)v * a.Txi * a.Ty_i;
+        for (int ty = o.y0; ty < o.y1; ++ty)
+            for (int tx = o.x0; tx < o.x1; ++tx) atomicAdd(row + ty * a.Txi + tx, 1u);
+    }
+    if (in) a.touched[f] = cnt;
 }
 
 void launch_project(const Layout &L, const ProjArgs &a, cudaStream_t s) {
@@ -76,7 +86,7 @@ __global__ void __launch_bounds__(kChunk) k_project_bwd(ProjBwdArgs a) {
     float pose[6] = {0, 0, 0, 0, 0, 0};
     if (i < s_ve.count) {
         const long long f = s_ve.pair_off + i;
-        const uint32_t prev = f > 0 ? a.touched_incl[f - 1] : 0u;
+        const uint32_t prev = (f > 0 && !a.touched_is_count) ? a.touched_incl[f - 1] : 0u;
         if (a.touched_incl[f] != prev) {
             const long long gi = s_ve.gauss_begin + i;
             const float *R = s_cam, *t = s_cam + 9;

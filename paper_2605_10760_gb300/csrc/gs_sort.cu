@@ -17,6 +17,19 @@
 //                  copied into list order (so a tile's list is one contiguous block for TMA).
 // Depth is positive (z > near > 0), so its float bit pattern orders like its value, and the sort is
 // stable, so equal keys keep the emission order (ascending flattened index).
+//
+// Tile-bucket binning (sort_mode GS_SORT_TILE_BUCKET) reaches the same lists without a global sort:
+//   1. gs_project counted the keys of every global tile; k_scan turns the G counts into
+//      inclusive slice ends and K;
+//   2. k_emit_bucket drops each key, as the 64-bit word (depth bits << 32 | pair index), into its
+//      tile's slice by taking slots from the slice end (an atomic decrement), which leaves every
+//      count at its slice start;
+//   3. k_tile_sort: one warp per tile sorts the slice ascending (bitonic network in registers or in
+//      the warp's shared-memory segment; the pair index makes every word distinct, so the order is
+//      exactly (depth bits, index)); slices above kWarpSortMax words go to k_tile_sort_long, one
+//      CTA per tile, with slices above kTileSortMax words as sorted runs merged pairwise in global
+//      memory.  Both write the tile's range, the sorted keys and values and the records in list
+//      order.
 #include <algorithm>
 
 #include "gs_kernels.cuh"
@@ -430,6 +443,275 @@ __global__ void k_ranges(const uint64_t *keys, const uint32_t *vals, const float
 }
 
 // ------------------------------------------------------------------------------------------
+// tile-bucket binning
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kChunk) k_emit_bucket(BinArgs a) {
+    const int v = blockIdx.y;
+    __shared__ ViewEntry s_ve;
+    if (threadIdx.x == 0) s_ve = a.views[v];
+    __syncthreads();
+    if ((long long)blockIdx.x * kChunk >= s_ve.count) return;   // whole block past the view
+    const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
+    const long long f = s_ve.pair_off + (i < s_ve.count ? i : 0);
+    const bool vis = i < s_ve.count && a.touched[f] != 0u;
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    unsigned long long word = 0;
+    if (vis) {
+        const float4 r0 = a.proj[3 * f], r1 = a.proj[3 * f + 1];
+        spec_rect(r0.x, r0.y, r1.w, a.tw, a.th, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
+        word = ((unsigned long long)__float_as_uint(r1.z) << 32) | (unsigned long long)(uint32_t)f;
+    }
+    uint64_t *keys = a.keys[0];
+    const long long cap = a.cap;
+    // slots from the end of each touched tile's slice; the atomics of up to kEmitBatch tiles are in
+    // flight together before their stores
+    constexpr int kEmitBatch = 4;
+    uint32_t *row = a.tile_cnt + (size_t)v * a.Tx * a.Ty;
+    const int n = vis ? (x1 - x0) * (y1 - y0) : 0;
+    int tx = x0, ty = y0;
+    for (int t0 = 0; t0 < n; t0 += kEmitBatch) {
+        uint32_t slot[kEmitBatch];
+#pragma unroll
+        for (int u = 0; u < kEmitBatch; ++u) {
+            slot[u] = 0xffffffffu;
+            if (t0 + u < n) {
+                slot[u] = atomicSub(row + ty * a.Tx + tx, 1u) - 1u;
+                if (++tx == x1) {
+                    tx = x0;
+                    ++ty;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kEmitBatch; ++u)
+            if (t0 + u < n && (long long)slot[u] < cap) keys[slot[u]] = word;
+    }
+    if (vis) {
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.g2d[3 * f] = z4;
+        a.g2d[3 * f + 1] = z4;
+        a.g2d[3 * f + 2] = z4;
+    }
+}
+
+constexpr int kTileSortThreads = 256;
+constexpr int kTileSortMax = 4096;      // words sorted in shared memory by one CTA (32 KB)
+constexpr int kWarpSortMax = 128;       // words sorted in shared memory by one warp (1 KB)
+
+// Ascending bitonic sort of b[0, m), m a power of two, by the whole block.
+__device__ __forceinline__ void block_bitonic(unsigned long long *b, int m) {
+    for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < (m >> 1); t += blockDim.x) {
+                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));   // i has bit j clear
+                const int l = i | j;
+                const unsigned long long x = b[i], y = b[l];
+                const bool up = (i & k) == 0;
+                if ((x > y) == up) {
+                    b[i] = y;
+                    b[l] = x;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// The same network run by one warp on its own segment (m <= kWarpSortMax).
+__device__ __forceinline__ void warp_bitonic(unsigned long long *b, int m, int lane) {
+    for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = lane; t < (m >> 1); t += 32) {
+                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+                const int l = i | j;
+                const unsigned long long x = b[i], y = b[l];
+                const bool up = (i & k) == 0;
+                if ((x > y) == up) {
+                    b[i] = y;
+                    b[l] = x;
+                }
+            }
+            __syncwarp();
+        }
+}
+
+// 32 words, one per lane, sorted ascending across the warp in registers.
+__device__ __forceinline__ unsigned long long warp_bitonic32(unsigned long long x, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
+            const bool lower = (lane & j) == 0, up = (lane & k) == 0;
+            x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
+        }
+    return x;
+}
+
+// Number of entries of the ascending run r[0, n) that are smaller than x.
+__device__ __forceinline__ long long count_below(const unsigned long long *r, long long n, unsigned long long x) {
+    long long lo = 0, hi = n;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (r[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The slice [s, e) of tile g (clamped to the capacity) and its published range.
+__device__ __forceinline__ void tile_slice(const BinArgs &a, long long g, long long &s, long long &n) {
+    const unsigned long long K = a.st->num_keys;
+    const unsigned long long cap = (unsigned long long)a.cap;
+    const unsigned long long s0 = a.tile_cnt[g];
+    const unsigned long long e0 = g + 1 < a.G ? a.tile_cnt[g + 1] : K;
+    s = (long long)min(s0, cap);
+    n = (long long)max((unsigned long long)s, min(e0, cap)) - s;
+}
+
+// Outputs of one sorted entry: key (tile << 32 | depth bits), value, record in list order.
+__device__ __forceinline__ void tile_emit(const BinArgs &a, uint64_t *kout, uint32_t *vout, long long g, long long pos,
+                                          unsigned long long w) {
+    const uint32_t f = (uint32_t)w;
+    if ((long long)f >= a.P) {   // only after an earlier recorded failure
+        record_error(a.st, GS_ERR_DEVICE_FAULT, 6);
+        return;
+    }
+    kout[pos] = ((unsigned long long)g << 32) | (w >> 32);
+    vout[pos] = f;
+    float4 r1 = a.proj[3 * (size_t)f + 1];
+    r1.w = __uint_as_float(f);
+    a.srec[3 * pos] = a.proj[3 * (size_t)f];
+    a.srec[3 * pos + 1] = r1;
+    a.srec[3 * pos + 2] = a.proj[3 * (size_t)f + 2];
+}
+
+// One warp per tile: every warp claims tiles from a counter, publishes the tile's range and sorts
+// slices of up to kWarpSortMax words itself (registers for 32 or fewer, its shared-memory segment
+// otherwise); longer slices are appended to the list of long tiles for k_tile_sort_long.
+__global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(BinArgs a) {
+    __shared__ unsigned long long seg[kTileSortThreads / 32][kWarpSortMax];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long *b = seg[warp];
+    uint64_t *kout = a.keys[a.passes & 1];
+    uint32_t *vout = a.vals[a.passes & 1];
+    const unsigned long long *words = reinterpret_cast<const unsigned long long *>(a.keys[0]);
+    for (;;) {
+        long long g = 0;
+        if (lane == 0) g = (long long)atomicAdd(&a.st->ctr[kCtrTileSort], 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= a.G) break;
+        long long s, n;
+        tile_slice(a, g, s, n);
+        if (lane == 0) {   // an empty tile reads [0, 0), as the onesweep path leaves it
+            a.ranges[2 * g] = n > 0 ? (uint32_t)s : 0u;
+            a.ranges[2 * g + 1] = n > 0 ? (uint32_t)(s + n) : 0u;
+        }
+        if (n == 0) continue;
+        if (n > kWarpSortMax) {
+            if (lane == 0) a.tile_list[atomicAdd(&a.st->ctr[kCtrTileList], 1u)] = (uint32_t)g;
+            continue;
+        }
+        if (n <= 32) {
+            const unsigned long long x = warp_bitonic32(lane < n ? words[s + lane] : ~0ull, lane);
+            if (lane < n) tile_emit(a, kout, vout, g, s + lane, x);
+            continue;
+        }
+        int m = 64;
+        while (m < n) m <<= 1;
+        for (int i = lane; i < m; i += 32) b[i] = i < n ? words[s + i] : ~0ull;
+        __syncwarp();
+        warp_bitonic(b, m, lane);
+        for (int i = lane; i < n; i += 32) tile_emit(a, kout, vout, g, s + i, b[i]);
+        __syncwarp();
+    }
+}
+
+// One CTA per long tile (more than kWarpSortMax words) from the list built by k_tile_sort: a
+// shared-memory bitonic sort up to kTileSortMax words, beyond that sorted runs merged pairwise
+// between this tile's slices of the two key buffers.
+__global__ void __launch_bounds__(kTileSortThreads) k_tile_sort_long(BinArgs a) {
+    __shared__ unsigned long long b[kTileSortMax];
+    __shared__ long long s_item;
+    uint64_t *kout = a.keys[a.passes & 1];
+    uint32_t *vout = a.vals[a.passes & 1];
+    const long long count = a.st->ctr[kCtrTileList];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&a.st->ctr[kCtrTileLong], 1u);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= count) break;
+        const long long g = a.tile_list[item];
+        long long s, n;
+        tile_slice(a, g, s, n);
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(a.keys[0] + s);
+        if (n > kTileSortMax) {
+            // sorted runs of kTileSortMax words, in place
+            for (long long r0 = 0; r0 < n; r0 += kTileSortMax) {
+                const int len = (int)min((long long)kTileSortMax, n - r0);
+                for (int i = threadIdx.x; i < kTileSortMax; i += blockDim.x) b[i] = i < len ? src[r0 + i] : ~0ull;
+                __syncthreads();
+                block_bitonic(b, kTileSortMax);
+                for (int i = threadIdx.x; i < len; i += blockDim.x) a.keys[0][s + r0 + i] = b[i];
+                __syncthreads();
+            }
+            // pairwise merges between the two key buffers (this tile's slice of each)
+            unsigned long long *in = reinterpret_cast<unsigned long long *>(a.keys[0] + s);
+            unsigned long long *out = reinterpret_cast<unsigned long long *>(a.keys[1] + s);
+            for (long long w = kTileSortMax; w < n; w <<= 1) {
+                for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+                    const long long base = (i / (2 * w)) * (2 * w);
+                    const long long aend = min(base + w, n), bend = min(base + 2 * w, n);
+                    const unsigned long long x = in[i];
+                    const long long pos = i < aend ? (i - base) + count_below(in + aend, bend - aend, x)
+                                                   : (i - aend) + count_below(in + base, aend - base, x);
+                    out[base + pos] = x;
+                }
+                __syncthreads();
+                unsigned long long *t = in;
+                in = out;
+                out = t;
+            }
+            src = in;
+        } else {
+            int m = 1;
+            while (m < n) m <<= 1;
+            for (int i = threadIdx.x; i < m; i += blockDim.x) b[i] = i < n ? src[i] : ~0ull;
+            __syncthreads();
+            block_bitonic(b, m);
+            src = b;
+        }
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) tile_emit(a, kout, vout, g, s + i, src[i]);
+        __syncthreads();
+    }
+}
+
+static int occupancy(const void *fn, int threads, size_t dyn);
+
+static int run_bucket(const BinArgs &a, cudaStream_t s) {
+    // inclusive scan of the G tile counts (K and the capacity check come with it)
+    BinArgs sa = a;
+    sa.touched = a.tile_cnt;
+    sa.P = a.G;
+    sa.zero_for_sort = 0;
+    int rc = run_scan_only(sa, s);
+    if (rc) return rc;
+    if (a.P > 0) {
+        dim3 grid((unsigned)a.max_chunks, (unsigned)a.V);
+        k_emit_bucket<<<grid, kChunk, 0, s>>>(a);
+        count_launches(1);
+    }
+    static int occ = occupancy((const void *)k_tile_sort, kTileSortThreads, 0);
+    const long long tiles_per_block = kTileSortThreads / 32;
+    const long long grid = std::max<long long>(
+        1, std::min<long long>((a.G + tiles_per_block - 1) / tiles_per_block, (long long)device_sm_count() * occ));
+    k_tile_sort<<<(unsigned)grid, kTileSortThreads, 0, s>>>(a);
+    static int occ_long = occupancy((const void *)k_tile_sort_long, kTileSortThreads, 0);
+    k_tile_sort_long<<<(unsigned)std::max(1, device_sm_count() * occ_long), kTileSortThreads, 0, s>>>(a);
+    count_launches(2);
+    return check_launch();
+}
+
+// ------------------------------------------------------------------------------------------
 // host driver
 // ------------------------------------------------------------------------------------------
 static int occupancy(const void *fn, int threads, size_t dyn) {
@@ -484,9 +766,10 @@ static int sweep_passes(const BinArgs &a, cudaStream_t s) {
 }
 
 int run_bin_sort(const BinArgs &a, cudaStream_t s) {
-    // counters of the scan and of every sort pass
-    if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t) * (1 + kMaxPasses), s) != cudaSuccess)
+    // counters of the scan, of every sort pass and of the per-tile sort
+    if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t) * (kCtrTileLong + 1), s) != cudaSuccess)
         return GS_ERR_CUDA;
+    if (a.sort_mode == GS_SORT_TILE_BUCKET) return run_bucket(a, s);
     BinArgs sa = a;
     sa.zero_for_sort = 1;                 // the scan also clears hist, look-back state and ranges
     if (a.P == 0) {

@@ -124,12 +124,35 @@ def test_debug_expf_bitwise_vs_oracle_and_cuda(R):
     assert (np.abs(ys[fin].astype(np.float64) - yc[fin]) / ulp).max() <= 3.0
 
 
+SORT_MODES = [1, 0]   # GS_SORT_ONESWEEP, GS_SORT_TILE_BUCKET: both must give the oracle's lists
+
+
+@pytest.mark.parametrize("mode", SORT_MODES)
 @pytest.mark.parametrize("wname,scale", [("cloud10k", 1.0), ("room500k", 0.1)])
-def test_parity_single_view(R, wname, scale):
+def test_parity_single_view(R, wname, scale, mode):
     wl = S.workload(wname, scale=scale)
-    gpu = run_gpu(R, wl)
+    p = R.default_params(sort_mode=mode)
+    gpu = run_gpu(R, wl, params=p)
     assert gpu["rc"] == 0 and gpu["rc_end"] == 0
-    orc = run_oracle(wl, up=gpu["up"])
+    orc = run_oracle(wl, params=p, up=gpu["up"])
+    compare_all(gpu, orc)
+
+
+@pytest.mark.parametrize("mode", SORT_MODES)
+def test_parity_tiles_longer_than_one_shared_memory_sort(R, mode):
+    """20k small Gaussians in front of a 48x40 image: the central tiles hold about 10k entries
+    each, so the tile-bucket sort goes through its sorted-runs-and-merge path."""
+    sc = S.random_cloud(20_000, seed=21)
+    sc.means[:, 0] *= 0.05
+    sc.means[:, 1] *= 0.05
+    wl = S.Workload("pile", sc, np.array([0, sc.n], np.int64), [S.identity_camera(48, 40, 60, 60, 24, 20)],
+                    np.zeros(1, np.int32), 48, 40)
+    p = R.default_params(sort_mode=mode)
+    gpu = run_gpu(R, wl, params=p)
+    assert gpu["rc"] == 0 and gpu["rc_end"] == 0
+    orc = run_oracle(wl, params=p, up=gpu["up"])
+    lens = np.diff(orc["bins"]["ranges"], axis=1)
+    assert lens.max() > 4 * 4096
     compare_all(gpu, orc)
 
 
@@ -142,13 +165,15 @@ def test_parity_room500k_full_size(R):
     compare_all(gpu, orc)
 
 
-def test_parity_batched_agents(R):
+@pytest.mark.parametrize("mode", SORT_MODES)
+def test_parity_batched_agents(R, mode):
     """8 uneven submaps x 4 views in one problem (the batched launch), Gaussian counts scaled to
     5% so the oracle stays fast, full 1200x680 views."""
     wl = S.workload("agents8x4", scale=0.05)
-    gpu = run_gpu(R, wl, alpha_w=0.2)
+    p = R.default_params(sort_mode=mode)
+    gpu = run_gpu(R, wl, params=p, alpha_w=0.2)
     assert gpu["rc"] == 0 and gpu["rc_end"] == 0
-    orc = run_oracle(wl, up=gpu["up"])
+    orc = run_oracle(wl, params=p, up=gpu["up"])
     compare_all(gpu, orc)
 
 
@@ -164,10 +189,11 @@ def test_batched_equals_per_view(R):
             np.testing.assert_array_equal(one["img"][k][0], full["img"][k][v])
 
 
+@pytest.mark.parametrize("mode", SORT_MODES)
 @pytest.mark.parametrize("tw,th", [(16, 8), (32, 16)])
-def test_parity_other_tiles(R, tw, th):
+def test_parity_other_tiles(R, tw, th, mode):
     wl = S.workload("cloud10k", scale=0.5)
-    p = R.default_params(tile_w=tw, tile_h=th)
+    p = R.default_params(tile_w=tw, tile_h=th, sort_mode=mode)
     gpu = run_gpu(R, wl, params=p)
     orc = run_oracle(wl, params=p, up=gpu["up"])
     compare_all(gpu, orc)
@@ -181,14 +207,16 @@ def test_parity_background_and_alpha_gradient(R):
     compare_all(gpu, orc)
 
 
-def test_capacity_overflow_reports_required_keys(R):
+@pytest.mark.parametrize("mode", SORT_MODES)
+def test_capacity_overflow_reports_required_keys(R, mode):
     wl = S.workload("cloud10k", scale=0.2)
-    gpu = run_gpu(R, wl, key_capacity=1000, grads=False)
+    p = R.default_params(sort_mode=mode)
+    gpu = run_gpu(R, wl, params=p, key_capacity=1000, grads=False)
     orc = Oracle.from_workload(wl)
     assert gpu["rc"] == R.L.GS_ERR_CAPACITY
     assert gpu["req"] == orc.K
     # a capacity that fits clears the status and gives the exact result
-    ok = run_gpu(R, wl, key_capacity=orc.K, grads=False)
+    ok = run_gpu(R, wl, params=p, key_capacity=orc.K, grads=False)
     assert ok["rc"] == 0 and ok["K"] == orc.K
 
 
@@ -207,13 +235,15 @@ def test_bounded_wait_times_out_and_recovers(R):
     assert float(x.sum()) == 1000.0
 
 
-def test_edge_cases_empty_and_culled(R):
+@pytest.mark.parametrize("mode", SORT_MODES)
+def test_edge_cases_empty_and_culled(R, mode):
     # every Gaussian behind the camera: no keys, empty image, zero gradients
+    p = R.default_params(sort_mode=mode)
     sc = S.random_cloud(64, seed=3)
     sc.means[:, 2] = -sc.means[:, 2]
     wl = S.Workload("behind", sc, np.array([0, sc.n], np.int64), [S.identity_camera(40, 30, 30, 30)],
                     np.zeros(1, np.int32), 40, 30)
-    gpu = run_gpu(R, wl)
+    gpu = run_gpu(R, wl, params=p)
     assert gpu["rc"] == 0 and gpu["K"] == 0
     assert np.all(gpu["img"]["final_T"] == 1.0) and np.all(gpu["img"]["last_idx"] == 0)
     assert np.all(gpu["grads"]["means"] == 0) and np.all(gpu["pose"] == 0)
@@ -222,8 +252,8 @@ def test_edge_cases_empty_and_culled(R):
     for (W, H) in ((1, 1), (17, 33), (250, 7)):
         wl2 = S.Workload("ragged", sc2, np.array([0, sc2.n], np.int64),
                          [S.identity_camera(W, H, 40, 40, W / 2, H / 2)], np.zeros(1, np.int32), W, H)
-        gpu2 = run_gpu(R, wl2)
-        orc2 = run_oracle(wl2, up=gpu2["up"])
+        gpu2 = run_gpu(R, wl2, params=p)
+        orc2 = run_oracle(wl2, params=p, up=gpu2["up"])
         compare_all(gpu2, orc2)
 
 
