@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
     constexpr int NB = batch_records<TW, TH>();   // records per staged batch
     constexpr int NT = TW * TH / kPPT;            // threads
     __shared__ RenderSmem<TW, TH> sm;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t wbit = 1u << (tid >> 5);
     const long long tpv = (long long)a.Tx * a.Ty;
     const long long HW = (long long)a.W * a.H;
@@ -193,9 +193,15 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
             }
             __syncthreads();
             const uint8_t *msk = sm.mask[buf];
-            for (int k = 0; k < cnt; ++k) {
-                if (done[0] && done[1]) break;
-                if (!(msk[k] & wbit)) continue;     // no pixel of this warp can blend the entry
+            // entries whose region bit is clear for this warp are dropped 32 at a time: a ballot over
+            // the mask bytes gives the entries to visit, walked front to back
+            for (int k0 = 0; k0 < cnt; k0 += 32) {
+              const int kk = k0 + lane;
+              uint32_t bits = __ballot_sync(0xffffffffu, kk < cnt && (msk[kk] & wbit));
+              if (done[0] && done[1]) continue;   // after the ballot, which every lane takes part in
+              while (bits) {
+                const int k = k0 + __ffs(bits) - 1;
+                bits &= bits - 1u;
                 const float4 r0 = rec[3 * k];
                 const float4 r1 = rec[3 * k + 1];
                 const float cut = rec[3 * k + 2].w;
@@ -229,6 +235,8 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
                     T[p] = Tn;
                     last[p] = b + k + 1;
                 }
+                if (done[0] && done[1]) break;
+              }
             }
             const bool all_done = __syncthreads_and(done[0] && done[1]);   // also: buffer reads finished
             if (all_done) {
@@ -412,10 +420,16 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
             }
             __syncthreads();
             const uint8_t *msk = sm.mask[buf];
-            // entries at or beyond the warp's largest last_idx contribute nothing to this warp
+            // entries at or beyond the warp's largest last_idx contribute nothing to this warp; entries
+            // whose region bit is clear are dropped 32 at a time (a ballot over the mask bytes), and
+            // the rest walked back to front
             const int kend = min(hi, wmax) - lo;
-            for (int k = kend - 1; k >= 0; --k) {
-                if (!(msk[k] & wbit)) continue;       // every pixel of this warp skips the entry
+            for (int k0 = ((kend - 1) >> 5) << 5; k0 >= 0 && kend > 0; k0 -= 32) {
+              const int kk = k0 + lane;
+              uint32_t bits = __ballot_sync(0xffffffffu, kk < kend && (msk[kk] & wbit));
+              while (bits) {
+                const int k = k0 + 31 - __clz(bits);
+                bits &= ~(1u << (k - k0));
                 const int pos = lo + k;
                 const float4 r0 = rec[3 * k];
                 const float4 r1 = rec[3 * k + 1];
@@ -474,6 +488,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
                     const uint32_t f = __float_as_uint(r1.w);
                     if (issuer) atomicAdd(a.g2d + 12 * (size_t)f + comp, gv[0]);
                 }
+              }
             }
             __syncthreads();                          // buffer reads finished before its refill
             buf ^= 1;
