@@ -278,7 +278,8 @@ def time_steps(pipe, steps, warmup, flush_buf, torch, graphs=True, barrier=None,
 def time_e2e(pipes, steps, torch, flush_buf):
     """Same step through host buffers, software-pipelined over two device copies of the problem:
     every step copies its Gaussians, camera and targets in from pinned host memory (copy stream),
-    flushes L2 and runs the step (compute stream), and copies the loss, pose gradient and Gaussian
+    flushes L2 and runs the step (compute stream; the step's libgs calls replayed as one captured
+    graph when the pipeline has one), and copies the loss, pose gradient and Gaussian
     gradients out to pinned host memory (second copy stream); step i's input copy overlaps step
     i-1's compute and step i-2's output copy.  The time runs from before the first input copy to
     after the last output copy; per step = total / steps."""
@@ -319,7 +320,10 @@ def time_e2e(pipes, steps, torch, flush_buf):
             if ev_out[b] is not None:
                 comp.wait_event(ev_out[b])             # its previous results have been copied out
             l2_flush(flush_buf)
-            p.step()
+            if getattr(p, "whole", None) is not None:
+                p.step_whole()                         # the step's libgs calls, captured as one graph
+            else:
+                p.step()
             ev_comp[b] = comp.record_event()
             with torch.cuda.stream(s_out):
                 s_out.wait_event(ev_comp[b])
@@ -713,6 +717,7 @@ def main():
     ms = total_ms / args.steps
     value = world * pipe.V / (ms / 1e3)
     pipe2 = Pipeline(R, S, wl, rank_views(S, wl, rank, world))
+    pipe2.capture()
     e2e_ms, h2d, d2h = time_e2e([pipe, pipe2], args.steps, torch, flush)
     del pipe2
     stats = pipe.pb.stats()

@@ -91,3 +91,25 @@ def test_calls_reject_bad_arguments_without_launching(lib):
     assert lib.gs_adam_step(-1, None, None, None, 0, None) == L.GS_ERR_INVALID_ARG
     assert lib.gs_debug_scan_timeout(None, 10, 0, None, None) == L.GS_ERR_INVALID_ARG
     assert lib.gs_error_string(L.GS_ERR_CAPACITY) == b"key capacity exceeded"
+
+
+def test_follow_up_calls_reject_bad_arguments_without_launching(lib):
+    p = lib.gs_default_pho_params()
+    assert p.stride == 1 and p.near_plane == np.float32(0.2) and p.huber_delta == np.float32(9.0 / 255.0)
+    one = C.c_void_p(1 << 20)
+    args = [one, 1, 16, 16, one, one, one, 1, one, C.byref(p), one, one, one, one, one, 1 << 30, None]
+    assert lib.gs_pho_residual(0, *args) == L.GS_OK                    # no edges: nothing to do
+    assert lib.gs_pho_residual(-1, *args) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_pho_residual(70000, *args) == L.GS_ERR_INVALID_ARG
+    bad = list(args)
+    bad[0] = None                                                      # edges
+    assert lib.gs_pho_residual(1, *bad) == L.GS_ERR_INVALID_ARG
+    bad = list(args)
+    bad[15] = lib.gs_pho_scratch_size(4) - 1                           # scratch too small
+    assert lib.gs_pho_residual(4, *bad) == L.GS_ERR_INVALID_ARG
+    p.stride = 0
+    assert lib.gs_pho_residual(1, *args) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_voxset_bytes(100) == 0 and lib.gs_voxset_bytes(128) == 256 + 8 * 128   # power of two
+    assert lib.gs_voxset_clear(one, 100, None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_voxset_add_boxes(one, 128, 1, None, None, 3.0, 0.05, None) == L.GS_ERR_INVALID_ARG
+    assert lib.gs_voxset_keep(1, one, one, 128, None, 0, 0.0, one, None) == L.GS_ERR_INVALID_ARG   # voxel 0
