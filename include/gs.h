@@ -409,7 +409,7 @@ int gs_pho_residual(int32_t num_edges, const gs_pho_edge *edges, int32_t num_ima
                     const gs_sim3 *corrections, const gs_pho_params *params, double *cost, int64_t *count,
                     double *H, double *g, void *scratch, size_t scratch_bytes, void *stream);
 
-/* Zeroes the five gradient arrays of n Gaussians (stream-ordered memsets). */
+/* Zeroes the five gradient arrays of n Gaussians (one stream-ordered kernel launch). */
 int gs_grads_zero(int64_t n, const gs_grads *grads, void *stream);
 
 /* Number of kernels this library has launched in the calling process since it was loaded

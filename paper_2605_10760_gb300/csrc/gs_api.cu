@@ -598,12 +598,7 @@ int gs_grads_zero(int64_t n, const gs_grads *g, void *stream) {
     if (n < 0 || !g) return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
     if (!g->means || !g->log_scales || !g->quats || !g->opacities || !g->colors) return GS_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t sz[5] = {12, 12, 16, 4, 12};
-    float *p[5] = {g->means, g->log_scales, g->quats, g->opacities, g->colors};
-    for (int k = 0; k < 5; ++k)
-        if (cudaMemsetAsync(p[k], 0, sz[k] * (size_t)n, s) != cudaSuccess) return GS_ERR_CUDA;
-    return GS_OK;
+    return launch_grads_zero(n, *g, (cudaStream_t)stream);
 }
 
 int64_t gs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }

@@ -30,7 +30,7 @@ constexpr unsigned long long kSpinLimit = 1ull << 21;  // bounded waits (x ~100 
 
 // counters inside the status block (zeroed by the call that uses them)
 enum Counter {
-    kCtrScan = 0, kCtrSort0 = 1, kCtrFwd = 12, kCtrBwd = 13, kCtrTileSort = 14, kCtrTileList = 15, kCtrTileLong = 16,
+    kCtrScan = 0, kCtrSort0 = 1, kCtrTileSort = 14, kCtrTileList = 15, kCtrTileLong = 16,
     kNumCounters = 32
 };
 
@@ -39,8 +39,12 @@ struct DevStatus {
     int32_t where;                // stage tag of that error
     unsigned long long required_keys;
     unsigned long long num_keys;  // K written by the scan
+    // each compositing kernel's pair counter and work-queue counter sit in one 16-byte block,
+    // cleared together by one memset before the launch
     unsigned long long fwd_pairs;
+    uint32_t fwd_items, fwd_pad;
     unsigned long long bwd_pairs;
+    uint32_t bwd_items, bwd_pad;
     uint32_t ctr[kNumCounters];
 };
 

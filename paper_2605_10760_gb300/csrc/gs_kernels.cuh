@@ -123,6 +123,7 @@ int launch_voxset_keep(long long n, const float *means, void *occ, long long occ
                        float v, uint8_t *keep, cudaStream_t s);
 int launch_sim3(long long n, const gs_gaussians &in, const float q[4], const float t[3], float sc,
                 const gs_gaussian_arrays &out, cudaStream_t s);
+int launch_grads_zero(long long n, const gs_grads &g, cudaStream_t s);
 int launch_adam(long long n, const gs_adam_state &st, const gs_grads &g, const float lr[5], int zero_grads,
                 cudaStream_t s, float iso_weight = 0.f, double *iso_loss = nullptr);
 

@@ -9,6 +9,7 @@
 //          and combines dSSIM/dx = blur(dS/dmu_x) + 2 x blur(dS/dE[x^2]) + y blur(dS/dE[xy]),
 //          fused with the L1 gradient.
 // Adam: one thread per Gaussian, 14 parameters, bias-corrected, opacity through its logit.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -758,6 +759,45 @@ int launch_view_adam(int V, const gs_view_adam_state &st, const float *pose_grad
                                                  lr_pose, lr_expo);
     k_step_inc<<<1, 1, 0, s>>>(st.step);
     count_launches(2);
+    return check_launch();
+}
+
+// ------------------------------------------------------------------------------------------
+// zeroing of the five gradient arrays in one launch
+// ------------------------------------------------------------------------------------------
+struct ZeroArgs {
+    float *p[5];
+    long long len[5];     // floats per array
+};
+
+// grid (blocks, 5): row y clears array y, 16 bytes per store where the pointer allows it.
+__global__ void k_zero_grads(ZeroArgs a) {
+    float *p = a.p[blockIdx.y];
+    const long long n = a.len[blockIdx.y];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long head = 0;
+    if (((uintptr_t)p & 15u) == 0) {
+        const long long n4 = n >> 2;
+        float4 *q = reinterpret_cast<float4 *>(p);
+        for (long long i = t0; i < n4; i += stride) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        head = n4 << 2;
+    }
+    for (long long i = head + t0; i < n; i += stride) p[i] = 0.f;
+}
+
+int launch_grads_zero(long long n, const gs_grads &g, cudaStream_t s) {
+    ZeroArgs a;
+    float *ptr[5] = {g.means, g.log_scales, g.quats, g.opacities, g.colors};
+    const long long per[5] = {3, 3, 4, 1, 3};
+    for (int k = 0; k < 5; ++k) {
+        a.p[k] = ptr[k];
+        a.len[k] = per[k] * n;
+    }
+    const long long blocks = std::max<long long>(1, std::min<long long>((4 * n + 1023) / 1024,
+                                                                        (long long)device_sm_count() * 2));
+    k_zero_grads<<<dim3((unsigned)blocks, 5), 256, 0, s>>>(a);
+    count_launches(1);
     return check_launch();
 }
 

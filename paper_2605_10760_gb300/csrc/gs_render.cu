@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
     uint32_t parity[2] = {0u, 0u};
     unsigned long long pairs = 0;
     for (;;) {
-        if (tid == 0) sm.item = (long long)atomicAdd(&a.st->ctr[kCtrFwd], 1u);
+        if (tid == 0) sm.item = (long long)atomicAdd(&a.st->fwd_items, 1u);
         __syncthreads();
         const long long g = sm.item;
         if (g >= a.G) break;
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
     unsigned long long pairs = 0;
     for (;;) {
         if (tid == 0) {
-            sm.item = (long long)atomicAdd(&a.st->ctr[kCtrBwd], 1u);
+            sm.item = (long long)atomicAdd(&a.st->bwd_items, 1u);
             sm.maxlast = 0;
         }
         __syncthreads();
@@ -511,8 +511,7 @@ template <int TW, int TH>
 static int fwd_t(const FwdArgs &a, cudaStream_t s) {
     constexpr int NT = TW * TH / kPPT;
     static int grid = persistent_grid(k_render_fwd<TW, TH>, NT);
-    if (cudaMemsetAsync(&a.st->ctr[kCtrFwd], 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
-    if (cudaMemsetAsync(&a.st->fwd_pairs, 0, sizeof(unsigned long long), s) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaMemsetAsync(&a.st->fwd_pairs, 0, 16, s) != cudaSuccess) return GS_ERR_CUDA;   // pairs + items
     const long long g = std::min<long long>(grid, std::max<long long>(1, a.G));
     k_render_fwd<TW, TH><<<(unsigned)g, NT, 0, s>>>(a);
     count_launches(1);
@@ -523,8 +522,7 @@ template <int TW, int TH>
 static int bwd_t(const BwdArgs &a, cudaStream_t s) {
     constexpr int NT = TW * TH / kPPT;
     static int grid = persistent_grid(k_render_bwd<TW, TH>, NT);
-    if (cudaMemsetAsync(&a.st->ctr[kCtrBwd], 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
-    if (cudaMemsetAsync(&a.st->bwd_pairs, 0, sizeof(unsigned long long), s) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaMemsetAsync(&a.st->bwd_pairs, 0, 16, s) != cudaSuccess) return GS_ERR_CUDA;   // pairs + items
     const long long g = std::min<long long>(grid, std::max<long long>(1, a.G));
     k_render_bwd<TW, TH><<<(unsigned)g, NT, 0, s>>>(a);
     count_launches(1);

@@ -213,15 +213,25 @@ __global__ void __launch_bounds__(256) k_hist(BinArgs a) {
     const unsigned long long K = min(a.st->num_keys, (unsigned long long)a.cap);
     const uint64_t *keys = a.keys[0];
     const int lane = threadIdx.x & 31;
-    for (unsigned long long i0 = (unsigned long long)blockIdx.x * 256; i0 < K; i0 += (unsigned long long)gridDim.x * 256) {
-        const unsigned long long i = i0 + threadIdx.x;
-        const bool valid = i < K;
-        const uint64_t key = valid ? keys[i] : 0ull;
-        for (int p = 0; p < a.passes; ++p) {
-            const uint32_t d = valid ? (uint32_t)((key >> (8 * p)) & 255u) : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&sh[p][d], (uint32_t)__popc(peers));
+    // kHistBatch keys per thread are loaded before any is counted, so their loads overlap
+    constexpr int kHistBatch = 4;
+    const unsigned long long step = (unsigned long long)gridDim.x * 256;
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * 256; i0 < K; i0 += step * kHistBatch) {
+        uint64_t key[kHistBatch];
+        bool valid[kHistBatch];
+#pragma unroll
+        for (int b = 0; b < kHistBatch; ++b) {
+            const unsigned long long i = i0 + b * step + threadIdx.x;
+            valid[b] = i < K;
+            key[b] = valid[b] ? keys[i] : 0ull;
         }
+#pragma unroll
+        for (int b = 0; b < kHistBatch; ++b)
+            for (int p = 0; p < a.passes; ++p) {
+                const uint32_t d = valid[b] ? (uint32_t)((key[b] >> (8 * p)) & 255u) : 256u;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&sh[p][d], (uint32_t)__popc(peers));
+            }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < a.passes * 256; i += 256) {
@@ -686,6 +696,7 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort_long(BinArgs a) 
 }
 
 static int occupancy(const void *fn, int threads, size_t dyn);
+static int run_scan(const BinArgs &a, cudaStream_t s, bool counter_cleared);
 
 static int run_bucket(const BinArgs &a, cudaStream_t s) {
     // inclusive scan of the G tile counts (K and the capacity check come with it)
@@ -693,7 +704,7 @@ static int run_bucket(const BinArgs &a, cudaStream_t s) {
     sa.touched = a.tile_cnt;
     sa.P = a.G;
     sa.zero_for_sort = 0;
-    int rc = run_scan_only(sa, s);
+    int rc = run_scan(sa, s, true);   // run_bin_sort cleared the scan counter
     if (rc) return rc;
     if (a.P > 0) {
         dim3 grid((unsigned)a.max_chunks, (unsigned)a.V);
@@ -720,8 +731,9 @@ static int occupancy(const void *fn, int threads, size_t dyn) {
     return b;
 }
 
-int run_scan_only(const BinArgs &a, cudaStream_t s) {
-    if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
+static int run_scan(const BinArgs &a, cudaStream_t s, bool counter_cleared) {
+    if (!counter_cleared && cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t), s) != cudaSuccess)
+        return GS_ERR_CUDA;
     const long long parts = (a.P + kScanTile - 1) / kScanTile;
     if (parts > 0) {
         if (cudaMemsetAsync(a.scan_state, 0, sizeof(unsigned long long) * parts, s) != cudaSuccess) return GS_ERR_CUDA;
@@ -735,6 +747,8 @@ int run_scan_only(const BinArgs &a, cudaStream_t s) {
     }
     return check_launch();
 }
+
+int run_scan_only(const BinArgs &a, cudaStream_t s) { return run_scan(a, s, false); }
 
 template <int IPT>
 static int sweep_passes(const BinArgs &a, cudaStream_t s) {
@@ -776,7 +790,7 @@ int run_bin_sort(const BinArgs &a, cudaStream_t s) {
         if (cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, s) != cudaSuccess) return GS_ERR_CUDA;
         if (cudaMemsetAsync(a.ranges, 0, sizeof(uint32_t) * 2 * (size_t)a.G, s) != cudaSuccess) return GS_ERR_CUDA;
     }
-    int rc = run_scan_only(sa, s);
+    int rc = run_scan(sa, s, true);   // run_bin_sort cleared the scan counter
     if (rc) return rc;
     if (a.P > 0) {
         dim3 grid((unsigned)a.max_chunks, (unsigned)a.V);
