@@ -206,6 +206,23 @@ int gs_bin_sort(const gs_problem *pb, void *ws, void *stream);
  * g supplies nothing here but is kept for symmetry (colours were captured by gs_project). */
 int gs_render_fwd(const gs_problem *pb, void *ws, const gs_image *out, void *stream);
 
+/* Targets and outputs of the L1 terms of the mapping loss (Eq. 4), as gs_loss_l1 defines them:
+ * L = w_rgb mean|rgb - rgb_t| + w_depth mean|depth - depth_t| (sign(0) = 0); d_rgb [V,3,H,W] and
+ * d_depth [V,H,W] receive dL/drgb and dL/ddepth, *loss (device double) receives L.  depth_t and
+ * d_depth may be NULL when w_depth = 0. */
+typedef struct gs_l1_target {
+    const float *rgb_t, *depth_t;
+    float w_rgb, w_depth;
+    float *d_rgb, *d_depth;
+    double *loss;
+} gs_l1_target;
+
+/* gs_render_fwd with the L1 terms fused into its per-pixel epilogue: the same outputs as
+ * gs_render_fwd followed by gs_loss_l1 on its rgb and depth (which may then be NULL in *out),
+ * without a second pass over the images.  The loss is summed in a different order than
+ * gs_loss_l1 (per warp, then one double atomic per warp). */
+int gs_render_fwd_l1(const gs_problem *pb, void *ws, const gs_image *out, const gs_l1_target *l1, void *stream);
+
 /* Adjoint of the compositing, back to front from final_T and last_idx (no per-pixel lists),
  * followed by the projection adjoint: accumulates dL/d(means, log_scales, quats, opacities,
  * colors) into `grads` (+=) and leaves per-view pose partial sums in the workspace. */

@@ -92,6 +92,11 @@ class gs_sim3(C.Structure):
     _fields_ = [("q", C.c_float * 4), ("t", C.c_float * 3), ("s", C.c_float)]
 
 
+class gs_l1_target(C.Structure):
+    _fields_ = [("rgb_t", C.c_void_p), ("depth_t", C.c_void_p), ("w_rgb", C.c_float), ("w_depth", C.c_float),
+                ("d_rgb", C.c_void_p), ("d_depth", C.c_void_p), ("loss", C.c_void_p)]
+
+
 class gs_pho_edge(C.Structure):
     _fields_ = [("src_image", C.c_int32), ("tgt_image", C.c_int32), ("src_corr", C.c_int32), ("tgt_corr", C.c_int32),
                 ("weight", C.c_float), ("reserved", C.c_float * 3)]
@@ -121,6 +126,7 @@ _SIGS = {
     "gs_project": (C.c_int, [C.POINTER(gs_problem), C.POINTER(gs_gaussians), _P, _P]),
     "gs_bin_sort": (C.c_int, [C.POINTER(gs_problem), _P, _P]),
     "gs_render_fwd": (C.c_int, [C.POINTER(gs_problem), _P, C.POINTER(gs_image), _P]),
+    "gs_render_fwd_l1": (C.c_int, [C.POINTER(gs_problem), _P, C.POINTER(gs_image), C.POINTER(gs_l1_target), _P]),
     "gs_render_bwd": (C.c_int, [C.POINTER(gs_problem), C.POINTER(gs_gaussians), _P, C.POINTER(gs_image),
                                 C.POINTER(gs_image_grad), C.POINTER(gs_grads), _P]),
     "gs_pose_grad": (C.c_int, [C.POINTER(gs_problem), _P, _P, _P]),

@@ -315,7 +315,8 @@ int gs_bin_sort(const gs_problem *pb, void *ws, void *stream) {
     return run_bin_sort(a, (cudaStream_t)stream);
 }
 
-int gs_render_fwd(const gs_problem *pb, void *ws, const gs_image *out, void *stream) {
+static int render_fwd_impl(const gs_problem *pb, void *ws, const gs_image *out, const gs_l1_target *l1,
+                           void *stream) {
     Layout L;
     int rc = compute_layout(pb, &L);
     if (rc) return rc;
@@ -330,7 +331,31 @@ int gs_render_fwd(const gs_problem *pb, void *ws, const gs_image *out, void *str
     const gs_params &p = pb->params;
     a.amax = p.alpha_max; a.amin = p.alpha_min; a.tmin = p.t_min;
     a.bg0 = p.bg[0]; a.bg1 = p.bg[1]; a.bg2 = p.bg[2];
+    a.rgb_t = nullptr; a.depth_t = nullptr; a.d_rgb = nullptr; a.d_depth = nullptr; a.loss = nullptr;
+    a.sc_rgb = a.sc_d = 0.f;
+    if (l1) {
+        const double HWn = (double)L.W * L.H;
+        a.rgb_t = l1->rgb_t;
+        a.d_rgb = l1->d_rgb;
+        a.loss = l1->loss;
+        a.sc_rgb = (float)((double)l1->w_rgb / (3.0 * L.V * HWn));
+        if (l1->w_depth != 0.f) {
+            a.depth_t = l1->depth_t;
+            a.d_depth = l1->d_depth;
+            a.sc_d = (float)((double)l1->w_depth / ((double)L.V * HWn));
+        }
+    }
     return launch_render_fwd(L.tw, L.th, a, s);
+}
+
+int gs_render_fwd(const gs_problem *pb, void *ws, const gs_image *out, void *stream) {
+    return render_fwd_impl(pb, ws, out, nullptr, stream);
+}
+
+int gs_render_fwd_l1(const gs_problem *pb, void *ws, const gs_image *out, const gs_l1_target *l1, void *stream) {
+    if (!l1 || !l1->rgb_t || !l1->d_rgb || !l1->loss) return GS_ERR_INVALID_ARG;
+    if (l1->w_depth != 0.f && (!l1->depth_t || !l1->d_depth)) return GS_ERR_INVALID_ARG;
+    return render_fwd_impl(pb, ws, out, l1, stream);
 }
 
 int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const gs_image *fwd,

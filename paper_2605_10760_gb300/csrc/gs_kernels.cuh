@@ -78,6 +78,11 @@ struct FwdArgs {
     int W, H, Tx, Ty;
     long long G, P;
     float amax, amin, tmin, bg0, bg1, bg2;
+    // optional L1 epilogue (Eq. 4's photometric and depth terms): null rgb_t = none
+    const float *rgb_t, *depth_t;
+    float sc_rgb, sc_d;                // w / element count of each term
+    float *d_rgb, *d_depth;
+    double *loss;
 };
 
 struct BwdArgs {

@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
     __syncthreads();
     uint32_t parity[2] = {0u, 0u};
     unsigned long long pairs = 0;
+    float l1_rgb = 0.f, l1_d = 0.f;      // per-thread sums of |rendered - target| (L1 epilogue)
     for (;;) {
         if (tid == 0) sm.item = (long long)atomicAdd(&a.st->fwd_items, 1u);
         __syncthreads();
@@ -258,15 +259,30 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
             pairs += (unsigned long long)visited[p];
             if (x < a.W && y0 + p < a.H) {
                 const long long pix = (long long)(y0 + p) * a.W + x;
+                const float c[3] = {C0[p] + T[p] * a.bg0, C1[p] + T[p] * a.bg1, C2[p] + T[p] * a.bg2};
                 if (a.rgb) {
-                    a.rgb[(3 * (long long)v + 0) * HW + pix] = C0[p] + T[p] * a.bg0;
-                    a.rgb[(3 * (long long)v + 1) * HW + pix] = C1[p] + T[p] * a.bg1;
-                    a.rgb[(3 * (long long)v + 2) * HW + pix] = C2[p] + T[p] * a.bg2;
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) a.rgb[(3 * (long long)v + ch) * HW + pix] = c[ch];
                 }
                 if (a.depth) a.depth[(long long)v * HW + pix] = D[p];
                 if (a.alpha) a.alpha[(long long)v * HW + pix] = 1.0f - T[p];
                 a.finalT[(long long)v * HW + pix] = T[p];
                 a.last[(long long)v * HW + pix] = last[p];
+                if (a.rgb_t) {   // L1 terms and their gradient, as gs_loss_l1 computes them
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        const long long idx = (3 * (long long)v + ch) * HW + pix;
+                        const float d = c[ch] - a.rgb_t[idx];
+                        l1_rgb += fabsf(d);
+                        a.d_rgb[idx] = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * a.sc_rgb;
+                    }
+                    if (a.depth_t) {
+                        const long long idx = (long long)v * HW + pix;
+                        const float d = D[p] - a.depth_t[idx];
+                        l1_d += fabsf(d);
+                        a.d_depth[idx] = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * a.sc_d;
+                    }
+                }
             }
         }
         __syncthreads();
@@ -274,6 +290,12 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
     if ((tid & 31) == 0 && pairs) atomicAdd(&a.st->fwd_pairs, pairs);
+    if (a.rgb_t) {   // one double atomic per warp for the loss
+        double l = (double)l1_rgb * a.sc_rgb + (double)l1_d * a.sc_d;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if ((tid & 31) == 0 && l != 0.0) atomicAdd(a.loss, l);
+    }
 }
 
 // Transposed butterfly over 16 slots: after the call lane l holds, in v[0], the warp sum of slot
@@ -512,6 +534,7 @@ static int fwd_t(const FwdArgs &a, cudaStream_t s) {
     constexpr int NT = TW * TH / kPPT;
     static int grid = persistent_grid(k_render_fwd<TW, TH>, NT);
     if (cudaMemsetAsync(&a.st->fwd_pairs, 0, 16, s) != cudaSuccess) return GS_ERR_CUDA;   // pairs + items
+    if (a.rgb_t && cudaMemsetAsync(a.loss, 0, sizeof(double), s) != cudaSuccess) return GS_ERR_CUDA;
     const long long g = std::min<long long>(grid, std::max<long long>(1, a.G));
     k_render_fwd<TW, TH><<<(unsigned)g, NT, 0, s>>>(a);
     count_launches(1);

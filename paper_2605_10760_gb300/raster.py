@@ -186,6 +186,23 @@ class Problem:
         L.check(self.lib.gs_render_fwd(self.pb, _ptr(self.ws), C.byref(s), _stream()), "gs_render_fwd")
         return img
 
+    def render_fwd_l1(self, img: dict, rgb_t, depth_t=None, w_rgb=1.0, w_depth=0.0, d_rgb=None, d_depth=None,
+                      loss=None):
+        """gs_render_fwd with the L1 loss terms fused into its epilogue.  Returns (img, loss, d_rgb,
+        d_depth); img's rgb / depth may be absent (not written)."""
+        V, H, W = self.V, self.H, self.W
+        d_rgb = d_rgb if d_rgb is not None else torch.empty(V, 3, H, W, device=self.device)
+        if w_depth != 0.0 and d_depth is None:
+            d_depth = torch.empty(V, H, W, device=self.device)
+        loss = loss if loss is not None else torch.zeros(1, dtype=torch.float64, device=self.device)
+        s = L.gs_image(_ptr(img.get("rgb")), _ptr(img.get("depth")), _ptr(img.get("alpha")),
+                       _ptr(img["final_T"]), _ptr(img["last_idx"]))
+        t = L.gs_l1_target(_ptr(rgb_t), _ptr(depth_t) if w_depth != 0.0 else None, float(w_rgb), float(w_depth),
+                           _ptr(d_rgb), _ptr(d_depth) if w_depth != 0.0 else None, _ptr(loss))
+        L.check(self.lib.gs_render_fwd_l1(self.pb, _ptr(self.ws), C.byref(s), C.byref(t), _stream()),
+                "gs_render_fwd_l1")
+        return img, loss, d_rgb, d_depth
+
     def render_bwd(self, g: Gaussians, img: dict, d_rgb=None, d_depth=None, d_alpha=None,
                    grads: Gaussians | None = None) -> Gaussians:
         grads = grads if grads is not None else zeros_like_grads(g)

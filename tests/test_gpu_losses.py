@@ -97,3 +97,28 @@ def test_adam_with_isotropy_regulariser_matches_oracle(R):
         assert abs(iso.item() - val) <= 1e-5 * val
         ls, m, v = OL.adam_step(ls, gls + giso, m, v, step, 5e-3)
     np.testing.assert_allclose(g.log_scales.cpu().numpy(), ls, rtol=1e-5, atol=2e-6)
+
+
+def test_render_fwd_with_fused_l1_matches_separate_calls(R):
+    """gs_render_fwd_l1 = gs_render_fwd followed by gs_loss_l1 on its outputs."""
+    from helpers import gpu_problem
+    wl = S.workload("room500k", scale=0.1)
+    pb, g = gpu_problem(wl)
+    img = pb.forward_checked(g)
+    H, W = wl.height, wl.width
+    tgt = torch.from_numpy(S.smooth_image(W, H, 41)[None]).cuda()
+    dtg = torch.from_numpy(S.smooth_image(W, H, 42, channels=1, lo=0.5, hi=5.0)).cuda()
+    loss_a, d_rgb_a, d_d_a = R.loss_l1(img["rgb"], tgt, img["depth"], dtg, 1.0, 0.1)
+    img2 = pb.alloc_image()
+    img2, loss_b, d_rgb_b, d_d_b = pb.render_fwd_l1(img2, tgt, dtg, 1.0, 0.1)
+    torch.cuda.synchronize()
+    for k in ("rgb", "depth", "alpha", "final_T", "last_idx"):
+        assert torch.equal(img[k], img2[k]), k
+    assert torch.equal(d_rgb_a, d_rgb_b) and torch.equal(d_d_a, d_d_b)
+    assert abs(loss_a.item() - loss_b.item()) <= 1e-6 * abs(loss_a.item())
+    # rgb-only loss, images not requested
+    img3 = {"final_T": torch.empty_like(img["final_T"]), "last_idx": torch.empty_like(img["last_idx"])}
+    _, loss_c, d_rgb_c, _ = pb.render_fwd_l1(img3, tgt, None, 1.0, 0.0)
+    loss_r, d_rgb_r, _ = R.loss_l1(img["rgb"], tgt, None, None, 1.0, 0.0)
+    torch.cuda.synchronize()
+    assert torch.equal(d_rgb_c, d_rgb_r) and abs(loss_c.item() - loss_r.item()) <= 1e-6 * abs(loss_r.item())
