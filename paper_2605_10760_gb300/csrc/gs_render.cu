@@ -22,10 +22,14 @@
 // recovering T_j = T_{j+1} / (1 - alpha_j) and one running scalar Q (the upstream-weighted colour
 // and depth accumulated behind each entry, with the background and alpha-output terms), so no
 // per-pixel list is stored.  Each thread sums the 10 per-Gaussian gradient components of its two
-// pixels, then the warp reduces them with a transposed butterfly (16 shuffles instead of 50) after
+// pixels, then the warp reduces them with a transposed butterfly (13 shuffles instead of 50) after
 // which 10 lanes issue one atomic add each: a (Gaussian, warp) pair costs one warp-wide atomic
 // instruction; warps whose 64 pixels all skip the entry issue nothing, and entries past the
 // warp's last blended position are not visited at all.
+//
+// In both kernels each warp drops the entries whose region bit is clear 32 at a time (a ballot
+// over the mask bytes) and visits only the rest.  The forward can also evaluate the L1 terms of
+// the mapping loss and their gradient in its per-pixel epilogue (gs_render_fwd_l1).
 #include "gs_kernels.cuh"
 
 namespace gs {
