@@ -375,7 +375,7 @@ def batched_speedup(R, S, torch, flush_buf, reps=3):
 def mapping_graph(R, S, torch, iters=100, reps=2):
     """room1m: 1M-Gaussian room, 8 views; `iters` mapping iterations (project, bin + sort, forward,
     0.8 L1 + 0.2 (1 - SSIM), backward, pose gradient, Adam) captured in one CUDA graph; the tile
-    shape is picked first by the autotuner."""
+    shape and the staged batch size are picked first by the autotuner."""
     from paper_2605_10760_gb300 import mapping as M
     wl = workload(S, "room1m")
     V, H, W = len(wl.cameras), wl.height, wl.width
@@ -387,8 +387,9 @@ def mapping_graph(R, S, torch, iters=100, reps=2):
         return R.Problem(np.zeros(V, np.int64), np.full(V, wl.scene.n, np.int64), wl.scene.n, W, H, cams,
                          params=params)
 
-    tw, th, _, table = M.autotune(make, g0, tgt, iters=3, reps=2, cache_key="room1m_8views")
-    pb = make(R.default_params(tile_w=tw, tile_h=th))
+    kw, _, table = M.autotune(make, g0, tgt, iters=3, reps=2, cache_key="room1m_8views")
+    tw, th = kw["tile_w"], kw["tile_h"]
+    pb = make(R.default_params(**kw))
     loop = M.MappingLoop(pb, g0, tgt)
     loop.capture(iters)
     loop.replay()
@@ -405,7 +406,7 @@ def mapping_graph(R, S, torch, iters=100, reps=2):
     rc, req = pb.check_status()
     ms_iter = statistics.median(times) / iters
     # the same loop with Eq. 4's isotropy regulariser (lambda_s = 10) fused into the Adam step
-    pb_iso = make(R.default_params(tile_w=tw, tile_h=th))
+    pb_iso = make(R.default_params(**kw))
     loop_iso = M.MappingLoop(pb_iso, R.Gaussians.from_scene(wl.scene), tgt, iso_weight=10.0)
     loop_iso.capture(iters)
     loop_iso.replay()
@@ -421,7 +422,7 @@ def mapping_graph(R, S, torch, iters=100, reps=2):
     rc_iso, _ = pb_iso.check_status()
     return {"workload": "room1m: 1M-Gaussian room, 8 views 1200x680, 0.8 L1 + 0.2 (1-SSIM), Adam, "
                         "%d iterations per CUDA graph" % iters,
-            "tile": [tw, th], "autotune": table, "ms_per_iteration": ms_iter,
+            "tile": [tw, th], "batch_records": kw["batch_records"], "autotune": table, "ms_per_iteration": ms_iter,
             "iterations_per_s": 1e3 / ms_iter, "views_per_s": V * 1e3 / ms_iter,
             "loss_after": float(loop.loss.item()), "status": rc or rc0, "required_keys": req,
             "with_isotropy": {"lambda_s": 10.0, "ms_per_iteration": statistics.median(t_iso) / iters,

@@ -82,7 +82,7 @@ enum { GS_SORT_TILE_BUCKET = 0, GS_SORT_ONESWEEP = 1 };
 
 /* Rasterizer constants.  gs_default_params() gives tile 16x16, near 0.2, dilation 0.3,
  * radius_sigmas 3, alpha_max 0.99, alpha_min 1/255 (float division), t_min 1e-4, bg 0,
- * sort_mode GS_SORT_ONESWEEP.  Supported tiles: 16x16, 16x8, 32x16. */
+ * sort_mode GS_SORT_ONESWEEP, batch_records 0.  Supported tiles: 16x16, 16x8, 32x16. */
 typedef struct gs_params {
     int32_t tile_w, tile_h;
     float near_plane;
@@ -93,6 +93,9 @@ typedef struct gs_params {
     float t_min;
     float bg[3];
     int32_t sort_mode;                 /* GS_SORT_ONESWEEP or GS_SORT_TILE_BUCKET */
+    int32_t batch_records;             /* list entries staged per TMA batch by the compositing kernels:
+                                          0 = min(256, tile pixels); else 64, 128 or 256, at most the
+                                          tile's pixel count (a tuning knob: results do not change) */
 } gs_params;
 
 /* One rendering problem: V views of one or more scenes (agents' submaps) whose Gaussians are

@@ -38,7 +38,8 @@ class gs_camera(C.Structure):
 class gs_params(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("near_plane", C.c_float), ("dilation", C.c_float),
                 ("radius_sigmas", C.c_float), ("alpha_max", C.c_float), ("alpha_min", C.c_float),
-                ("t_min", C.c_float), ("bg", C.c_float * 3), ("sort_mode", C.c_int32)]
+                ("t_min", C.c_float), ("bg", C.c_float * 3), ("sort_mode", C.c_int32),
+                ("batch_records", C.c_int32)]
 
 
 class gs_problem(C.Structure):

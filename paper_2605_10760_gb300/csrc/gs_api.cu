@@ -46,8 +46,12 @@ int compute_layout(const gs_problem *pb, Layout *L) {
         !(p.dilation >= 0.f) || !(p.radius_sigmas > 0.f) || !(p.near_plane > 0.f))
         return GS_ERR_INVALID_ARG;
     if (p.sort_mode != GS_SORT_TILE_BUCKET && p.sort_mode != GS_SORT_ONESWEEP) return GS_ERR_INVALID_ARG;
+    const int pix = p.tile_w * p.tile_h;
+    const int nb = p.batch_records == 0 ? std::min(256, pix) : p.batch_records;
+    if ((nb != 64 && nb != 128 && nb != 256) || nb > pix) return GS_ERR_INVALID_ARG;
     std::memset(L, 0, sizeof(*L));
     L->sort_mode = p.sort_mode;
+    L->nb = nb;
     L->V = pb->num_views;
     L->W = pb->width;
     L->H = pb->height;
@@ -147,6 +151,7 @@ void gs_default_params(gs_params *out) {
     out->t_min = 1e-4f;
     out->bg[0] = out->bg[1] = out->bg[2] = 0.0f;
     out->sort_mode = GS_SORT_ONESWEEP;
+    out->batch_records = 0;
 }
 
 int gs_workspace_size(const gs_problem *pb, size_t *bytes) {
@@ -345,7 +350,7 @@ static int render_fwd_impl(const gs_problem *pb, void *ws, const gs_image *out, 
             a.sc_d = (float)((double)l1->w_depth / ((double)L.V * HWn));
         }
     }
-    return launch_render_fwd(L.tw, L.th, a, s);
+    return launch_render_fwd(L.tw, L.th, L.nb, a, s);
 }
 
 int gs_render_fwd(const gs_problem *pb, void *ws, const gs_image *out, void *stream) {
@@ -379,7 +384,7 @@ int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const g
     const gs_params &p = pb->params;
     a.amax = p.alpha_max; a.amin = p.alpha_min;
     a.bg0 = p.bg[0]; a.bg1 = p.bg[1]; a.bg2 = p.bg[2];
-    rc = launch_render_bwd(L.tw, L.th, a, s);
+    rc = launch_render_bwd(L.tw, L.th, L.nb, a, s);
     if (rc) return rc;
     if (L.P == 0) return GS_OK;
     ProjBwdArgs b;

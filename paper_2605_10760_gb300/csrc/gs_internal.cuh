@@ -59,7 +59,7 @@ struct Layout {
     int V, W, H, tw, th, Tx, Ty, passes, sort_ipt;
     long long G, P, N, cap, max_count, max_chunks;
     long long scan_parts, sort_parts;
-    int sort_mode;
+    int sort_mode, nb;                 // binning mode; records per staged render batch
     size_t o_status, o_views, o_proj, o_touched, o_scan_state, o_keys[2], o_vals[2], o_hist,
         o_sort_state, o_ranges, o_tcnt, o_tlist, o_srec, o_g2d, o_pose_part, total;
 };

@@ -98,8 +98,8 @@ struct BwdArgs {
     float amax, amin, bg0, bg1, bg2;
 };
 
-int launch_render_fwd(int tw, int th, const FwdArgs &a, cudaStream_t s);
-int launch_render_bwd(int tw, int th, const BwdArgs &a, cudaStream_t s);
+int launch_render_fwd(int tw, int th, int nb, const FwdArgs &a, cudaStream_t s);
+int launch_render_bwd(int tw, int th, int nb, const BwdArgs &a, cudaStream_t s);
 
 // ---------------- losses / optimiser ----------------
 int launch_loss_l1(int V, int W, int H, const float *rgb, const float *rgb_t, const float *depth,

@@ -99,14 +99,12 @@ constexpr unsigned long long kTmaWaitLimit = 1ull << 22;   // polls of a batch's
 
 // Shared memory of one render CTA: two batches of records (double buffer filled by TMA), the
 // per-entry warp-region masks of each batch, one mbarrier per buffer.
-// records per staged batch: one per pixel, at most 256 (keeps two buffers within 25 KB)
-template <int TW, int TH>
-__host__ __device__ constexpr int batch_records() { return TW * TH < 256 ? TW * TH : 256; }
-
-template <int TW, int TH>
+// NB records per staged batch: 64, 128 or 256, at most one per pixel of the tile (two buffers of
+// 256 records take 24 KB)
+template <int NB>
 struct __align__(128) RenderSmem {
-    float4 rec[2][3 * batch_records<TW, TH>()];
-    uint8_t mask[2][batch_records<TW, TH>()];
+    float4 rec[2][3 * NB];
+    uint8_t mask[2][NB];
     uint64_t bar[2];
     long long item;
     int maxlast;
@@ -114,8 +112,8 @@ struct __align__(128) RenderSmem {
 
 // Waits for both buffers' outstanding copies (bounded) after a failed wait, so that the CTA never
 // leaves with a copy still targeting its shared memory unless that copy is itself stuck.
-template <int TW, int TH>
-__device__ __forceinline__ void drain_after_timeout(RenderSmem<TW, TH> &sm, const uint32_t (&parity)[2],
+template <int NB>
+__device__ __forceinline__ void drain_after_timeout(RenderSmem<NB> &sm, const uint32_t (&parity)[2],
                                                     const bool (&pending)[2], DevStatus *st) {
     if (threadIdx.x == 0) {
         record_error(st, GS_ERR_TIMEOUT, 8);
@@ -125,11 +123,11 @@ __device__ __forceinline__ void drain_after_timeout(RenderSmem<TW, TH> &sm, cons
     __syncthreads();
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int NB>
 __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
-    constexpr int NB = batch_records<TW, TH>();   // records per staged batch
+    static_assert(NB <= TW * TH, "at most one staged record per pixel of the tile");
     constexpr int NT = TW * TH / kPPT;            // threads
-    __shared__ RenderSmem<TW, TH> sm;
+    __shared__ RenderSmem<NB> sm;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t wbit = 1u << (tid >> 5);
     const long long tpv = (long long)a.Tx * a.Ty;
@@ -184,7 +182,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
             const bool ok = mbar_wait_bounded(&sm.bar[buf], parity[buf], kTmaWaitLimit);
             if (__syncthreads_or(!ok)) {
                 const bool pending[2] = {buf == 0 || bi + 1 < nb, buf == 1 || bi + 1 < nb};
-                drain_after_timeout<TW, TH>(sm, parity, pending, a.st);
+                drain_after_timeout<NB>(sm, parity, pending, a.st);
                 return;
             }
             parity[buf] ^= 1u;
@@ -249,7 +247,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
                     const bool ok2 = mbar_wait_bounded(&sm.bar[buf ^ 1], parity[buf ^ 1], kTmaWaitLimit);
                     if (__syncthreads_or(!ok2)) {
                         const bool pending[2] = {buf == 1, buf == 0};
-                        drain_after_timeout<TW, TH>(sm, parity, pending, a.st);
+                        drain_after_timeout<NB>(sm, parity, pending, a.st);
                         return;
                     }
                     parity[buf ^ 1] ^= 1u;
@@ -347,11 +345,11 @@ __device__ __forceinline__ void warp_transpose_reduce16(float (&v)[16], int lane
 // slot of each gradient component (mean_x, mean_y, A, B, C, opacity, depth, r, g, b)
 enum : int { kSMx = 0, kSMy = 1, kSA = 2, kSB = 3, kSC = 4, kSO = 8, kSZ = 9, kSR = 10, kSG = 11, kSBl = 12 };
 
-template <int TW, int TH>
+template <int TW, int TH, int NB>
 __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
-    constexpr int NB = batch_records<TW, TH>();
+    static_assert(NB <= TW * TH, "at most one staged record per pixel of the tile");
     constexpr int NT = TW * TH / kPPT;
-    __shared__ RenderSmem<TW, TH> sm;
+    __shared__ RenderSmem<NB> sm;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t wbit = 1u << (tid >> 5);
     const int slot = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
@@ -432,7 +430,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
             const bool ok = mbar_wait_bounded(&sm.bar[buf], parity[buf], kTmaWaitLimit);
             if (__syncthreads_or(!ok)) {
                 const bool pending[2] = {buf == 0 || bi + 1 < nb, buf == 1 || bi + 1 < nb};
-                drain_after_timeout<TW, TH>(sm, parity, pending, a.st);
+                drain_after_timeout<NB>(sm, parity, pending, a.st);
                 return;
             }
             parity[buf] ^= 1u;
@@ -533,40 +531,45 @@ static int persistent_grid(F fn, int threads) {
     return b * device_sm_count();
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int NB>
 static int fwd_t(const FwdArgs &a, cudaStream_t s) {
     constexpr int NT = TW * TH / kPPT;
-    static int grid = persistent_grid(k_render_fwd<TW, TH>, NT);
+    static int grid = persistent_grid(k_render_fwd<TW, TH, NB>, NT);
     if (cudaMemsetAsync(&a.st->fwd_pairs, 0, 16, s) != cudaSuccess) return GS_ERR_CUDA;   // pairs + items
     if (a.rgb_t && cudaMemsetAsync(a.loss, 0, sizeof(double), s) != cudaSuccess) return GS_ERR_CUDA;
     const long long g = std::min<long long>(grid, std::max<long long>(1, a.G));
-    k_render_fwd<TW, TH><<<(unsigned)g, NT, 0, s>>>(a);
+    k_render_fwd<TW, TH, NB><<<(unsigned)g, NT, 0, s>>>(a);
     count_launches(1);
     return check_launch();
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int NB>
 static int bwd_t(const BwdArgs &a, cudaStream_t s) {
     constexpr int NT = TW * TH / kPPT;
-    static int grid = persistent_grid(k_render_bwd<TW, TH>, NT);
+    static int grid = persistent_grid(k_render_bwd<TW, TH, NB>, NT);
     if (cudaMemsetAsync(&a.st->bwd_pairs, 0, 16, s) != cudaSuccess) return GS_ERR_CUDA;   // pairs + items
     const long long g = std::min<long long>(grid, std::max<long long>(1, a.G));
-    k_render_bwd<TW, TH><<<(unsigned)g, NT, 0, s>>>(a);
+    k_render_bwd<TW, TH, NB><<<(unsigned)g, NT, 0, s>>>(a);
     count_launches(1);
     return check_launch();
 }
 
-int launch_render_fwd(int tw, int th, const FwdArgs &a, cudaStream_t s) {
-    if (tw == 16 && th == 16) return fwd_t<16, 16>(a, s);
-    if (tw == 16 && th == 8) return fwd_t<16, 8>(a, s);
-    if (tw == 32 && th == 16) return fwd_t<32, 16>(a, s);
+// (tile, records per batch) pairs with a compiled kernel; the API layer validates the values
+int launch_render_fwd(int tw, int th, int nb, const FwdArgs &a, cudaStream_t s) {
+    if (tw == 16 && th == 16)
+        return nb == 64 ? fwd_t<16, 16, 64>(a, s) : nb == 128 ? fwd_t<16, 16, 128>(a, s) : fwd_t<16, 16, 256>(a, s);
+    if (tw == 16 && th == 8) return nb == 64 ? fwd_t<16, 8, 64>(a, s) : fwd_t<16, 8, 128>(a, s);
+    if (tw == 32 && th == 16)
+        return nb == 64 ? fwd_t<32, 16, 64>(a, s) : nb == 128 ? fwd_t<32, 16, 128>(a, s) : fwd_t<32, 16, 256>(a, s);
     return GS_ERR_INVALID_ARG;
 }
 
-int launch_render_bwd(int tw, int th, const BwdArgs &a, cudaStream_t s) {
-    if (tw == 16 && th == 16) return bwd_t<16, 16>(a, s);
-    if (tw == 16 && th == 8) return bwd_t<16, 8>(a, s);
-    if (tw == 32 && th == 16) return bwd_t<32, 16>(a, s);
+int launch_render_bwd(int tw, int th, int nb, const BwdArgs &a, cudaStream_t s) {
+    if (tw == 16 && th == 16)
+        return nb == 64 ? bwd_t<16, 16, 64>(a, s) : nb == 128 ? bwd_t<16, 16, 128>(a, s) : bwd_t<16, 16, 256>(a, s);
+    if (tw == 16 && th == 8) return nb == 64 ? bwd_t<16, 8, 64>(a, s) : bwd_t<16, 8, 128>(a, s);
+    if (tw == 32 && th == 16)
+        return nb == 64 ? bwd_t<32, 16, 64>(a, s) : nb == 128 ? bwd_t<32, 16, 128>(a, s) : bwd_t<32, 16, 256>(a, s);
     return GS_ERR_INVALID_ARG;
 }
 

@@ -82,14 +82,18 @@ class MappingLoop:
         return 0, 0
 
 
-def autotune(make_problem, g: R.Gaussians, rgb_target, candidates=((16, 16), (16, 8), (32, 16)), iters=5,
-             reps=3, cache_key=None):
-    """Time `iters` eager mapping iterations for each tile shape and return the fastest as
-    (tile_w, tile_h, ms_per_iteration, table).  `make_problem(params)` builds a Problem.  The
-    choice is recorded in _build/autotune.json under cache_key."""
+# (tile_w, tile_h, records per staged render batch) candidates of the autotuner
+TUNE_CANDIDATES = ((16, 16, 256), (16, 16, 128), (16, 8, 128), (16, 8, 64), (32, 16, 256), (32, 16, 128))
+
+
+def autotune(make_problem, g: R.Gaussians, rgb_target, candidates=TUNE_CANDIDATES, iters=5, reps=3,
+             cache_key=None):
+    """Time `iters` eager mapping iterations for each (tile shape, staged batch size) and return the
+    fastest as (params kwargs, ms_per_iteration, table).  `make_problem(params)` builds a Problem.
+    The choice is recorded in _build/autotune.json under cache_key."""
     table = []
-    for tw, th in candidates:
-        params = R.default_params(tile_w=tw, tile_h=th)
+    for tw, th, nb in candidates:
+        params = R.default_params(tile_w=tw, tile_h=th, batch_records=nb)
         pb = make_problem(params)
         gg = R.Gaussians(*[getattr(g, k).clone() for k in ("means", "log_scales", "quats", "opacities", "colors")])
         loop = MappingLoop(pb, gg, rgb_target)
@@ -105,7 +109,7 @@ def autotune(make_problem, g: R.Gaussians, rgb_target, candidates=((16, 16), (16
             torch.cuda.synchronize()
             best = min(best, a.elapsed_time(b) / iters)
         rc, _ = pb.check_status()
-        table.append({"tile": [tw, th], "ms_per_iter": best, "status": rc})
+        table.append({"tile": [tw, th], "batch_records": nb, "ms_per_iter": best, "status": rc})
         del loop, pb, gg
     ok = [t for t in table if t["status"] == 0]
     pick = min(ok, key=lambda t: t["ms_per_iter"])
@@ -119,7 +123,8 @@ def autotune(make_problem, g: R.Gaussians, rgb_target, candidates=((16, 16), (16
                 data = {}
         data[cache_key] = {"pick": pick, "table": table, "when": time.time()}
         json.dump(data, open(_CACHE, "w"), indent=1)
-    return pick["tile"][0], pick["tile"][1], pick["ms_per_iter"], table
+    kw = dict(tile_w=pick["tile"][0], tile_h=pick["tile"][1], batch_records=pick["batch_records"])
+    return kw, pick["ms_per_iter"], table
 
 
 class RefineLoop:

@@ -50,7 +50,7 @@ def test_default_params(lib):
     assert (p.tile_w, p.tile_h) == (16, 16)
     assert p.alpha_max == np.float32(0.99) and p.alpha_min == np.float32(1) / np.float32(255)
     assert p.t_min == np.float32(1e-4) and p.dilation == np.float32(0.3)
-    assert p.sort_mode == L.GS_SORT_ONESWEEP
+    assert p.sort_mode == L.GS_SORT_ONESWEEP and p.batch_records == 0
 
 
 def test_workspace_size_and_validation(lib):
@@ -61,7 +61,8 @@ def test_workspace_size_and_validation(lib):
     # order (48 B per key) dominate
     assert 500_000 * 96 + (1 << 21) * 72 < n.value < 500_000 * 140 + (1 << 21) * 90
     bad = [_problem(V=0), _problem(W=0), _problem(cap=0), _problem(cap=1 << 30), _problem(tile_w=8),
-           _problem(alpha_max=1.5), _problem(t_min=0.0), _problem(near_plane=0.0), _problem(sort_mode=2)]
+           _problem(alpha_max=1.5), _problem(t_min=0.0), _problem(near_plane=0.0), _problem(sort_mode=2),
+           _problem(batch_records=100), _problem(batch_records=256, tile_h=8)]
     for b in bad:
         assert lib.gs_workspace_size(C.byref(b), C.byref(n)) == L.GS_ERR_INVALID_ARG
     pb = _problem(V=2)

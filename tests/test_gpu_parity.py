@@ -190,10 +190,11 @@ def test_batched_equals_per_view(R):
 
 
 @pytest.mark.parametrize("mode", SORT_MODES)
-@pytest.mark.parametrize("tw,th", [(16, 8), (32, 16)])
-def test_parity_other_tiles(R, tw, th, mode):
+@pytest.mark.parametrize("tw,th,nb", [(16, 8, 0), (32, 16, 0), (16, 16, 64), (16, 8, 64), (32, 16, 128)])
+def test_parity_other_tiles(R, tw, th, nb, mode):
+    """Other tile shapes and staged batch sizes (batch 0 = one record per pixel, at most 256)."""
     wl = S.workload("cloud10k", scale=0.5)
-    p = R.default_params(tile_w=tw, tile_h=th, sort_mode=mode)
+    p = R.default_params(tile_w=tw, tile_h=th, sort_mode=mode, batch_records=nb)
     gpu = run_gpu(R, wl, params=p)
     orc = run_oracle(wl, params=p, up=gpu["up"])
     compare_all(gpu, orc)
