@@ -280,8 +280,9 @@ int gs_loss_l1_ssim_noalloc(int32_t views, int32_t width, int32_t height, const 
  * with per-group learning rates lr[5] = {means, log_scales, quats, opacity_logits, colors}.
  * The opacity group steps logit(o): its gradient is dL/do * o (1 - o), and `opacities` is
  * rewritten as sigmoid(logit).  `step` is a device int32 incremented by the kernel (bias
- * correction uses the incremented value).  Moments m, v are [N,14] each (layout: means 3,
- * log_scales 3, quats 4, logit 1, colors 3).  If zero_grads != 0 the gradients are cleared. */
+ * correction uses the incremented value).  Moments m, v hold 14 N floats each, group-major in the
+ * parameters' own layout: [N,3] means, [N,3] log_scales, [N,4] quats, [N] logits, [N,3] colors.
+ * If zero_grads != 0 the gradients are cleared. */
 typedef struct gs_adam_state {
     float *means, *log_scales, *quats, *opacity_logits, *opacities, *colors;
     float *m, *v;

@@ -350,24 +350,26 @@ struct AdamArgs {
     double *iso_loss;       // optional: receives lambda_s L_iso (overwritten)
 };
 
+// One thread per Gaussian.  Moments are stored group-major, in the same layout as the parameters
+// ([N,3] means | [N,3] log-scales | [N,4] quats | [N] logits | [N,3] colours), so a warp's moment
+// accesses are as contiguous as its parameter accesses.
 __global__ void __launch_bounds__(256) k_adam(AdamArgs a) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    const bool in = i < a.n;
     const int t = *a.step + 1;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-15f;
     const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
     const int dims[5] = {3, 3, 4, 1, 3};
-    int col = 0;
-    float *m = a.m + 14 * i, *v = a.v + 14 * i;
+    const long long goff[5] = {0, 3 * a.n, 6 * a.n, 10 * a.n, 11 * a.n};   // group offsets in m, v
     // isotropy regulariser (Eq. 4): lambda_s sum_axes |s - mean(s)|, s = exp(log-scale); its
     // gradient with respect to log-scale b is lambda_s (sg_b - mean(sg)) s_b, sg = sign(s - mean)
     float giso[3] = {0.f, 0.f, 0.f};
-    if (a.iso_weight != 0.f) {
+    float lsum = 0.f;
+    if (a.iso_weight != 0.f && in) {
         float sc[3], sg[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) sc[k] = expf(a.p[1][3 * i + k]);
         const float sbar = (sc[0] + sc[1] + sc[2]) * (1.f / 3.f);
-        float lsum = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float d = sc[k] - sbar;
@@ -377,8 +379,14 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs a) {
         const float sgm = (sg[0] + sg[1] + sg[2]) * (1.f / 3.f);
 #pragma unroll
         for (int k = 0; k < 3; ++k) giso[k] = a.iso_weight * (sg[k] - sgm) * sc[k];
-        if (a.iso_loss) atomicAdd(a.iso_loss, (double)(a.iso_weight * lsum));
     }
+    if (a.iso_loss && a.iso_weight != 0.f) {   // one double atomic per warp
+        double l = (double)(a.iso_weight * lsum);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(a.iso_loss, l);
+    }
+    if (!in) return;
 #pragma unroll
     for (int grp = 0; grp < 5; ++grp) {
 #pragma unroll
@@ -391,16 +399,16 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs a) {
                 const float o = a.opac[i];
                 gr *= o * (1.f - o);
             }
-            const float mm = b1 * m[col] + (1.f - b1) * gr;
-            const float vv = b2 * v[col] + (1.f - b2) * gr * gr;
-            m[col] = mm;
-            v[col] = vv;
+            float *mp = a.m + goff[grp] + idx, *vp = a.v + goff[grp] + idx;
+            const float mm = b1 * *mp + (1.f - b1) * gr;
+            const float vv = b2 * *vp + (1.f - b2) * gr * gr;
+            *mp = mm;
+            *vp = vv;
             const float upd = a.lr[grp] * (mm / c1) / (sqrtf(vv / c2) + eps);
             const float np = a.p[grp][idx] - upd;
             a.p[grp][idx] = np;
             if (grp == 3) a.opac[i] = 1.f / (1.f + __expf(-np));
             if (a.zero) a.g[grp][idx] = 0.f;
-            ++col;
         }
     }
 }

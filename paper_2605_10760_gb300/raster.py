@@ -277,8 +277,8 @@ class AdamState:
         o = g.opacities.clamp(1e-6, 1 - 1e-6)
         self.logits = torch.log(o / (1 - o)).contiguous()
         n = g.n
-        self.m = torch.zeros(n, 14, device=g.means.device)
-        self.v = torch.zeros(n, 14, device=g.means.device)
+        self.m = torch.zeros(14 * n, device=g.means.device)   # group-major, the parameters' layout
+        self.v = torch.zeros(14 * n, device=g.means.device)
         self.step = torch.zeros(1, dtype=torch.int32, device=g.means.device)
         self.lr = (C.c_float * 5)(*lr)
 
