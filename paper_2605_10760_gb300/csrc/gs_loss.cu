@@ -134,64 +134,137 @@ static SsimTaps make_taps() {
     return t;
 }
 
-// pass 1: per image plane (view * 3 + channel), tile (bx, by)
-__global__ void __launch_bounds__(256) k_ssim1(int W, int H, const float *x, const float *y, SsimTaps tp,
-                                               float inv_n, float *dmu, float *dexx, float *dexy, double *ssim_sum) {
-    __shared__ float sx[kSI][kSI], sy[kSI][kSI];
-    __shared__ float h[5][kSI][kSB];
-    const long long plane = blockIdx.z;
-    const float *xp = x + plane * (long long)W * H;
-    const float *yp = y + plane * (long long)W * H;
-    const int x0 = blockIdx.x * kSB - kR, y0 = blockIdx.y * kSB - kR;
-    for (int i = threadIdx.x; i < kSI * kSI; i += 256) {
-        const int r = i / kSI, c = i % kSI;
-        const int gx = x0 + c, gy = y0 + r;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        sx[r][c] = in ? xp[(long long)gy * W + gx] : 0.f;
-        sy[r][c] = in ? yp[(long long)gy * W + gx] : 0.f;
+// Both passes map the 256 threads of a CTA as 32 columns x 8 rows: loads and the horizontal
+// filter walk rows ty, ty + 8, ... of column tx; the vertical filter gives each thread kVRows
+// consecutive output rows of its column and slides over the kVRows + 10 filtered rows they need,
+// so every filtered value is read from shared memory once per thread instead of once per tap.
+constexpr int kVRows = kSB / 8;
+
+struct Ssim1Smem {
+    float sx[kSI][kSI], sy[kSI][kSI];
+    float h[5][kSI][kSB];
+};
+struct Ssim2Smem {
+    float s[3][kSI][kSI];
+    float h[3][kSI][kSB];
+};
+
+template <int M>
+__device__ __forceinline__ void ssim_vpass(const float (&h)[M][kSI][kSB], const SsimTaps &tp, int tx, int ty,
+                                           float (&out)[M][kVRows]) {
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int q = 0; q < kVRows; ++q) out[m][q] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kVRows + 2 * kR; ++j) {
+        float hv[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) hv[m] = h[m][ty * kVRows + j][tx];
+#pragma unroll
+        for (int q = 0; q < kVRows; ++q) {
+            const int k = j - q;
+            if (k >= 0 && k <= 2 * kR) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) out[m][q] += tp.w[k] * hv[m];
+            }
+        }
     }
+}
+
+// Pass 1 of one tile of one plane: x, y (x optionally as fl(fl(ea x) + eb)), zero padding; the
+// five blurred moments, the SSIM map summed into the return value and the three per-pixel
+// derivatives dS/dmu_x, dS/dE[x^2], dS/dE[xy] (scaled by inv_n) written for pass 2.
+__device__ __forceinline__ double ssim_pass1_tile(Ssim1Smem &sm, int W, int H, const float *xp, const float *yp,
+                                                  bool expo, float ea, float eb, const SsimTaps &tp, float inv_n,
+                                                  float *dmu, float *dexx, float *dexy) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * kSB - kR, y0 = blockIdx.y * kSB - kR;
+    for (int r = ty; r < kSI; r += 8)
+        for (int c = tx; c < kSI; c += 32) {
+            const int gx = x0 + c, gy = y0 + r;
+            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const long long o = (long long)gy * W + gx;
+            const float xv = in ? xp[o] : 0.f;
+            sm.sx[r][c] = in ? (expo ? fp::add(fp::mul(ea, xv), eb) : xv) : 0.f;   // zero padding
+            sm.sy[r][c] = in ? yp[o] : 0.f;
+        }
     __syncthreads();
-    for (int i = threadIdx.x; i < kSI * kSB; i += 256) {
-        const int r = i / kSB, c = i % kSB;
+    for (int r = ty; r < kSI; r += 8) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float xv = sx[r][c + k], yv = sy[r][c + k], w = tp.w[k];
+        for (int k = 0; k <= 2 * kR; ++k) {
+            const float xv = sm.sx[r][tx + k], yv = sm.sy[r][tx + k], w = tp.w[k];
             a0 += w * xv;
             a1 += w * yv;
             a2 += w * xv * xv;
             a3 += w * yv * yv;
             a4 += w * xv * yv;
         }
-        h[0][r][c] = a0; h[1][r][c] = a1; h[2][r][c] = a2; h[3][r][c] = a3; h[4][r][c] = a4;
+        sm.h[0][r][tx] = a0; sm.h[1][r][tx] = a1; sm.h[2][r][tx] = a2; sm.h[3][r][tx] = a3; sm.h[4][r][tx] = a4;
     }
     __syncthreads();
+    float v5[5][kVRows];
+    ssim_vpass<5>(sm.h, tp, tx, ty, v5);
     double acc = 0.0;
-    for (int i = threadIdx.x; i < kSB * kSB; i += 256) {
-        const int r = i / kSB, c = i % kSB;
-        const int gx = blockIdx.x * kSB + c, gy = blockIdx.y * kSB + r;
-        if (gx >= W || gy >= H) continue;
-        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = tp.w[k];
-            mx += w * h[0][r + k][c];
-            my += w * h[1][r + k][c];
-            exx += w * h[2][r + k][c];
-            eyy += w * h[3][r + k][c];
-            exy += w * h[4][r + k][c];
-        }
+    for (int q = 0; q < kVRows; ++q) {
+        const int gx = blockIdx.x * kSB + tx, gy = blockIdx.y * kSB + ty * kVRows + q;
+        if (gx >= W || gy >= H) continue;
+        const float mx = v5[0][q], my = v5[1][q], exx = v5[2][q], eyy = v5[3][q], exy = v5[4][q];
         const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
         const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
         const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
         const float iB = 1.f / (B1 * B2);
         const float S = A1 * A2 * iB;
         acc += (double)S;
-        const long long o = plane * (long long)W * H + (long long)gy * W + gx;
+        const long long o = (long long)gy * W + gx;
         dmu[o] = inv_n * ((2.f * my * A2 - 2.f * my * A1) * iB - S * (2.f * mx / B1 - 2.f * mx / B2));
         dexx[o] = inv_n * (-S / B2);
         dexy[o] = inv_n * (2.f * A1 * iB);
     }
+    return acc;
+}
+
+// Pass 2 of one tile: the three derivative maps blurred (the adjoint of a zero-padded symmetric
+// blur is the same blur); out[0..2] = blur(dS/dmu_x), blur(dS/dE[x^2]), blur(dS/dE[xy]) for the
+// thread's kVRows outputs.
+__device__ __forceinline__ void ssim_pass2_tile(Ssim2Smem &sm, int W, int H, const float *dmu, const float *dexx,
+                                                const float *dexy, const SsimTaps &tp, float (&out)[3][kVRows]) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * kSB - kR, y0 = blockIdx.y * kSB - kR;
+    for (int r = ty; r < kSI; r += 8)
+        for (int c = tx; c < kSI; c += 32) {
+            const int gx = x0 + c, gy = y0 + r;
+            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const long long o = (long long)gy * W + gx;
+            sm.s[0][r][c] = in ? dmu[o] : 0.f;
+            sm.s[1][r][c] = in ? dexx[o] : 0.f;
+            sm.s[2][r][c] = in ? dexy[o] : 0.f;
+        }
+    __syncthreads();
+    for (int r = ty; r < kSI; r += 8) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int k = 0; k <= 2 * kR; ++k) {
+            const float w = tp.w[k];
+            a0 += w * sm.s[0][r][tx + k];
+            a1 += w * sm.s[1][r][tx + k];
+            a2 += w * sm.s[2][r][tx + k];
+        }
+        sm.h[0][r][tx] = a0; sm.h[1][r][tx] = a1; sm.h[2][r][tx] = a2;
+    }
+    __syncthreads();
+    ssim_vpass<3>(sm.h, tp, tx, ty, out);
+}
+
+// pass 1: per image plane (view * 3 + channel) = blockIdx.z, tile (bx, by)
+__global__ void __launch_bounds__(256) k_ssim1(int W, int H, const float *x, const float *y, SsimTaps tp,
+                                               float inv_n, float *dmu, float *dexx, float *dexy, double *ssim_sum) {
+    __shared__ Ssim1Smem sm;
+    const long long off = (long long)blockIdx.z * W * H;
+    const double acc = ssim_pass1_tile(sm, W, H, x + off, y + off, false, 1.f, 0.f, tp, inv_n, dmu + off, dexx + off,
+                                       dexy + off);
     block_add_double(acc, ssim_sum);
 }
 
@@ -199,49 +272,18 @@ __global__ void __launch_bounds__(256) k_ssim1(int W, int H, const float *x, con
 __global__ void __launch_bounds__(256) k_ssim2(int W, int H, const float *x, const float *y, SsimTaps tp,
                                                const float *dmu, const float *dexx, const float *dexy, float l1_scale,
                                                float w_ssim, float *d_rgb) {
-    __shared__ float s[3][kSI][kSI];
-    __shared__ float h[3][kSI][kSB];
-    const long long plane = blockIdx.z;
-    const long long off = plane * (long long)W * H;
-    const int x0 = blockIdx.x * kSB - kR, y0 = blockIdx.y * kSB - kR;
-    for (int i = threadIdx.x; i < kSI * kSI; i += 256) {
-        const int r = i / kSI, c = i % kSI;
-        const int gx = x0 + c, gy = y0 + r;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const long long o = off + (long long)gy * W + gx;
-        s[0][r][c] = in ? dmu[o] : 0.f;
-        s[1][r][c] = in ? dexx[o] : 0.f;
-        s[2][r][c] = in ? dexy[o] : 0.f;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kSI * kSB; i += 256) {
-        const int r = i / kSB, c = i % kSB;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    __shared__ Ssim2Smem sm;
+    const long long off = (long long)blockIdx.z * W * H;
+    float b[3][kVRows];
+    ssim_pass2_tile(sm, W, H, dmu + off, dexx + off, dexy + off, tp, b);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = tp.w[k];
-            a0 += w * s[0][r][c + k];
-            a1 += w * s[1][r][c + k];
-            a2 += w * s[2][r][c + k];
-        }
-        h[0][r][c] = a0; h[1][r][c] = a1; h[2][r][c] = a2;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kSB * kSB; i += 256) {
-        const int r = i / kSB, c = i % kSB;
-        const int gx = blockIdx.x * kSB + c, gy = blockIdx.y * kSB + r;
+    for (int q = 0; q < kVRows; ++q) {
+        const int gx = blockIdx.x * kSB + tx, gy = blockIdx.y * kSB + ty * kVRows + q;
         if (gx >= W || gy >= H) continue;
-        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
-#pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = tp.w[k];
-            b0 += w * h[0][r + k][c];
-            b1 += w * h[1][r + k][c];
-            b2 += w * h[2][r + k][c];
-        }
         const long long o = off + (long long)gy * W + gx;
         const float xv = x[o], yv = y[o];
-        const float gs = b0 + 2.f * xv * b1 + yv * b2;
+        const float gs = b[0][q] + 2.f * xv * b[1][q] + yv * b[2][q];
         d_rgb[o] = l1_scale * sgnf(xv - yv) - w_ssim * gs;
     }
 }
@@ -483,117 +525,36 @@ __global__ void k_refine_l1(RefineArgs a) {
 }
 
 __global__ void __launch_bounds__(256) k_refine_ssim1(RefineArgs a, SsimTaps tp, float inv_n) {
-    __shared__ float sx[kSI][kSI], sy[kSI][kSI];
-    __shared__ float h[5][kSI][kSB];
-    const int W = a.W, H = a.H;
+    __shared__ Ssim1Smem sm;
     const long long plane = blockIdx.z;
     const int v = (int)(plane / 3);
     const float ea = spec_expf(a.expo[2 * v]), eb = a.expo[2 * v + 1];
-    const float *xp = a.rgb + plane * (long long)W * H;
-    const float *yp = a.rgb_t + plane * (long long)W * H;
-    const int x0 = blockIdx.x * kSB - kR, y0 = blockIdx.y * kSB - kR;
-    for (int i = threadIdx.x; i < kSI * kSI; i += 256) {
-        const int r = i / kSI, c = i % kSI;
-        const int gx = x0 + c, gy = y0 + r;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        sx[r][c] = in ? fp::add(fp::mul(ea, xp[(long long)gy * W + gx]), eb) : 0.f;   // zero padding of I~
-        sy[r][c] = in ? yp[(long long)gy * W + gx] : 0.f;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kSI * kSB; i += 256) {
-        const int r = i / kSB, c = i % kSB;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
-#pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float xv = sx[r][c + k], yv = sy[r][c + k], w = tp.w[k];
-            a0 += w * xv;
-            a1 += w * yv;
-            a2 += w * xv * xv;
-            a3 += w * yv * yv;
-            a4 += w * xv * yv;
-        }
-        h[0][r][c] = a0; h[1][r][c] = a1; h[2][r][c] = a2; h[3][r][c] = a3; h[4][r][c] = a4;
-    }
-    __syncthreads();
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < kSB * kSB; i += 256) {
-        const int r = i / kSB, c = i % kSB;
-        const int gx = blockIdx.x * kSB + c, gy = blockIdx.y * kSB + r;
-        if (gx >= W || gy >= H) continue;
-        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
-#pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = tp.w[k];
-            mx += w * h[0][r + k][c];
-            my += w * h[1][r + k][c];
-            exx += w * h[2][r + k][c];
-            eyy += w * h[3][r + k][c];
-            exy += w * h[4][r + k][c];
-        }
-        const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
-        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
-        const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-        const float iB = 1.f / (B1 * B2);
-        const float S = A1 * A2 * iB;
-        acc += (double)S;
-        const long long o = plane * (long long)W * H + (long long)gy * W + gx;
-        a.dmu[o] = inv_n * ((2.f * my * A2 - 2.f * my * A1) * iB - S * (2.f * mx / B1 - 2.f * mx / B2));
-        a.dexx[o] = inv_n * (-S / B2);
-        a.dexy[o] = inv_n * (2.f * A1 * iB);
-    }
+    const long long off = plane * (long long)a.W * a.H;
+    const double acc = ssim_pass1_tile(sm, a.W, a.H, a.rgb + off, a.rgb_t + off, true, ea, eb, tp, inv_n,
+                                       a.dmu + off, a.dexx + off, a.dexy + off);
     block_add_double(acc, a.sums + 1);
 }
 
 __global__ void __launch_bounds__(256) k_refine_ssim2(RefineArgs a, SsimTaps tp, float l1_scale) {
-    __shared__ float s[3][kSI][kSI];
-    __shared__ float h[3][kSI][kSB];
+    __shared__ Ssim2Smem sm;
     const int W = a.W, H = a.H;
     const long long plane = blockIdx.z;
     const int v = (int)(plane / 3);
     const float ea = spec_expf(a.expo[2 * v]), eb = a.expo[2 * v + 1];
     const long long off = plane * (long long)W * H;
-    const int x0 = blockIdx.x * kSB - kR, y0 = blockIdx.y * kSB - kR;
-    for (int i = threadIdx.x; i < kSI * kSI; i += 256) {
-        const int r = i / kSI, c = i % kSI;
-        const int gx = x0 + c, gy = y0 + r;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const long long o = off + (long long)gy * W + gx;
-        s[0][r][c] = in ? a.dmu[o] : 0.f;
-        s[1][r][c] = in ? a.dexx[o] : 0.f;
-        s[2][r][c] = in ? a.dexy[o] : 0.f;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kSI * kSB; i += 256) {
-        const int r = i / kSB, c = i % kSB;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-#pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = tp.w[k];
-            a0 += w * s[0][r][c + k];
-            a1 += w * s[1][r][c + k];
-            a2 += w * s[2][r][c + k];
-        }
-        h[0][r][c] = a0; h[1][r][c] = a1; h[2][r][c] = a2;
-    }
-    __syncthreads();
+    float b[3][kVRows];
+    ssim_pass2_tile(sm, W, H, a.dmu + off, a.dexx + off, a.dexy + off, tp, b);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     float ga = 0.f, gb = 0.f;
-    for (int i = threadIdx.x; i < kSB * kSB; i += 256) {
-        const int r = i / kSB, c = i % kSB;
-        const int gx = blockIdx.x * kSB + c, gy = blockIdx.y * kSB + r;
-        if (gx >= W || gy >= H) continue;
-        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = tp.w[k];
-            b0 += w * h[0][r + k][c];
-            b1 += w * h[1][r + k][c];
-            b2 += w * h[2][r + k][c];
-        }
+    for (int q = 0; q < kVRows; ++q) {
+        const int gx = blockIdx.x * kSB + tx, gy = blockIdx.y * kSB + ty * kVRows + q;
+        if (gx >= W || gy >= H) continue;
         const long long o = off + (long long)gy * W + gx;
         const float xv = a.rgb[o], yv = a.rgb_t[o];
         const float xt = fp::add(fp::mul(ea, xv), eb);       // I~ exactly as the FP32 L1 sign decision takes it
-        const float g = l1_scale * sgnf(xt - yv) - a.w_ssim * (b0 + 2.f * xt * b1 + yv * b2);   // dL/dI~
-        a.d_rgb[o] = ea * g;
+        const float g = l1_scale * sgnf(xt - yv) - a.w_ssim * (b[0][q] + 2.f * xt * b[1][q] + yv * b[2][q]);
+        a.d_rgb[o] = ea * g;                                 // dL/dI^ = e^a dL/dI~
         ga += g * ea * xv;
         gb += g;
     }
