@@ -1,5 +1,7 @@
 // gs_api.cu -- the C ABI of libgs: argument validation, workspace layout, stage launches.
 #include <algorithm>
+
+#include <nvtx3/nvToolsExt.h>
 #include <atomic>
 #include <cstring>
 #include <vector>
@@ -7,6 +9,14 @@
 #include "gs_kernels.cuh"
 
 namespace gs {
+
+// One NVTX range per library call (visible under a profiler; a no-op without one).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+#define GS_RANGE(name) NvtxRange gs_nvtx_range_(name)
+
 
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -254,6 +264,7 @@ int gs_read_stats(const gs_problem *pb, void *ws, void *stream, gs_stats *out) {
 }
 
 int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stream) {
+    GS_RANGE("gs_project");
     Layout L;
     int rc = compute_layout(pb, &L);
     if (rc) return rc;
@@ -312,6 +323,7 @@ static BinArgs make_bin_args(const Layout &L, void *ws) {
 }
 
 int gs_bin_sort(const gs_problem *pb, void *ws, void *stream) {
+    GS_RANGE("gs_bin_sort");
     Layout L;
     int rc = compute_layout(pb, &L);
     if (rc) return rc;
@@ -354,10 +366,12 @@ static int render_fwd_impl(const gs_problem *pb, void *ws, const gs_image *out, 
 }
 
 int gs_render_fwd(const gs_problem *pb, void *ws, const gs_image *out, void *stream) {
+    GS_RANGE("gs_render_fwd");
     return render_fwd_impl(pb, ws, out, nullptr, stream);
 }
 
 int gs_render_fwd_l1(const gs_problem *pb, void *ws, const gs_image *out, const gs_l1_target *l1, void *stream) {
+    GS_RANGE("gs_render_fwd_l1");
     if (!l1 || !l1->rgb_t || !l1->d_rgb || !l1->loss) return GS_ERR_INVALID_ARG;
     if (l1->w_depth != 0.f && (!l1->depth_t || !l1->d_depth)) return GS_ERR_INVALID_ARG;
     return render_fwd_impl(pb, ws, out, l1, stream);
@@ -365,6 +379,7 @@ int gs_render_fwd_l1(const gs_problem *pb, void *ws, const gs_image *out, const 
 
 int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const gs_image *fwd,
                   const gs_image_grad *dimg, const gs_grads *grads, void *stream) {
+    GS_RANGE("gs_render_bwd");
     Layout L;
     int rc = compute_layout(pb, &L);
     if (rc) return rc;
@@ -404,6 +419,7 @@ int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const g
 }
 
 int gs_pose_grad(const gs_problem *pb, void *ws, float *pose_grad, void *stream) {
+    GS_RANGE("gs_pose_grad");
     Layout L;
     int rc = compute_layout(pb, &L);
     if (rc) return rc;
@@ -416,6 +432,7 @@ int gs_pose_grad(const gs_problem *pb, void *ws, float *pose_grad, void *stream)
 int gs_loss_l1(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
                const float *depth, const float *depth_t, float w_rgb, float w_depth, float *d_rgb, float *d_depth,
                double *loss, void *stream) {
+    GS_RANGE("gs_loss_l1");
     if (views < 1 || views > 65535 || width < 1 || height < 1 || !rgb || !rgb_t || !d_rgb || !loss)
         return GS_ERR_INVALID_ARG;
     if (w_depth != 0.f && (!depth || !depth_t || !d_depth)) return GS_ERR_INVALID_ARG;
@@ -430,6 +447,7 @@ size_t gs_ssim_scratch_size(int32_t views, int32_t width, int32_t height) {
 
 int gs_loss_l1_ssim(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t, float w_l1,
                     float w_ssim, float *d_rgb, double *loss, void *scratch, void *stream) {
+    GS_RANGE("gs_loss_l1_ssim");
     if (views < 1 || width < 1 || height < 1 || !rgb || !rgb_t || !d_rgb || !loss || !ws_ok(scratch))
         return GS_ERR_INVALID_ARG;
     return launch_loss_l1_ssim(views, width, height, rgb, rgb_t, w_l1, w_ssim, d_rgb, loss, scratch,
@@ -438,6 +456,7 @@ int gs_loss_l1_ssim(int32_t views, int32_t width, int32_t height, const float *r
 
 int gs_loss_l1_ssim_noalloc(int32_t views, int32_t width, int32_t height, const float *rgb, const float *rgb_t,
                             float w_l1, float w_ssim, float *d_rgb, double *loss, void *stream) {
+    GS_RANGE("gs_loss_l1_ssim_noalloc");
     if (views < 1 || width < 1 || height < 1 || !rgb || !rgb_t || !d_rgb || !loss) return GS_ERR_INVALID_ARG;
     if ((long long)width * height > GS_SSIM_NOALLOC_MAX_PLANE) return GS_ERR_TOO_LARGE;
     return launch_loss_l1_ssim_noalloc(views, width, height, rgb, rgb_t, w_l1, w_ssim, d_rgb, loss,
@@ -453,6 +472,7 @@ int gs_loss_refine(int32_t views, int32_t width, int32_t height, const float *rg
                    const float *depth, const float *depth_t, const float *expo, float w_l1, float w_ssim,
                    float w_depth, float *d_rgb, float *d_depth, float *d_expo, double *loss, void *scratch,
                    void *stream) {
+    GS_RANGE("gs_loss_refine");
     if (views < 1 || views > GS_MAX_VIEWS || width < 1 || height < 1 || !rgb || !rgb_t || !expo || !d_rgb ||
         !loss || !ws_ok(scratch))
         return GS_ERR_INVALID_ARG;
@@ -465,6 +485,7 @@ size_t gs_prune_scratch_size(int64_t n) { return n < 1 ? 0 : prune_scratch_bytes
 
 int gs_prune(int64_t n, const gs_gaussians *in, float threshold, const gs_gaussian_arrays *out, int64_t *kept,
              void *scratch, void *stream) {
+    GS_RANGE("gs_prune");
     if (n < 1 || n >= (1LL << 30) || !in || !out || !kept || !ws_ok(scratch)) return GS_ERR_INVALID_ARG;
     if (!in->means || !in->log_scales || !in->quats || !in->opacities || !in->colors || !out->means ||
         !out->log_scales || !out->quats || !out->opacities || !out->colors)
@@ -474,6 +495,7 @@ int gs_prune(int64_t n, const gs_gaussians *in, float threshold, const gs_gaussi
 
 int gs_view_adam_step(int32_t views, const gs_view_adam_state *st, const float *pose_grad, const float *expo_grad,
                       float lr_pose, float lr_expo, void *stream) {
+    GS_RANGE("gs_view_adam_step");
     if (views < 1 || views > GS_MAX_VIEWS || !st || !st->cameras || !st->expo || !st->m || !st->v || !st->step ||
         !pose_grad || !expo_grad)
         return GS_ERR_INVALID_ARG;
@@ -483,6 +505,7 @@ int gs_view_adam_step(int32_t views, const gs_view_adam_state *st, const float *
 static bool pow2(long long c) { return c >= 2 && (c & (c - 1)) == 0; }
 
 int gs_sim3_apply(int64_t n, const gs_gaussians *in, const gs_sim3 *C, const gs_gaussian_arrays *out, void *stream) {
+    GS_RANGE("gs_sim3_apply");
     if (n < 0 || !in || !C || !out || !(C->s > 0.f)) return GS_ERR_INVALID_ARG;
     const float nq = C->q[0] * C->q[0] + C->q[1] * C->q[1] + C->q[2] * C->q[2] + C->q[3] * C->q[3];
     if (!(nq > 0.f)) return GS_ERR_INVALID_ARG;
@@ -531,6 +554,7 @@ int gs_voxset_status(void *set, void *stream, int64_t *count, int64_t capacity) 
 
 int gs_voxset_add_boxes(void *set, int64_t capacity, int64_t n, const float *means, const float *log_scales, float k,
                         float voxel, void *stream) {
+    GS_RANGE("gs_voxset_add_boxes");
     if (!ws_ok(set) || !pow2(capacity) || n < 0 || (n > 0 && (!means || !log_scales)) || !(voxel > 0.f) || !(k >= 0.f))
         return GS_ERR_INVALID_ARG;
     return launch_voxset_add_boxes(set, capacity, n, means, log_scales, k, voxel, (cudaStream_t)stream);
@@ -538,6 +562,7 @@ int gs_voxset_add_boxes(void *set, int64_t capacity, int64_t n, const float *mea
 
 int gs_voxset_add_rays(void *set, int64_t capacity, int32_t views, int32_t width, int32_t height,
                        const gs_camera *cams, const float *depth, int32_t stride, float voxel, void *stream) {
+    GS_RANGE("gs_voxset_add_rays");
     if (!ws_ok(set) || !pow2(capacity) || views < 1 || width < 1 || height < 1 || !cams || !depth || stride < 1 ||
         !(voxel > 0.f))
         return GS_ERR_INVALID_ARG;
@@ -546,6 +571,7 @@ int gs_voxset_add_rays(void *set, int64_t capacity, int32_t views, int32_t width
 
 int gs_voxset_keep(int64_t n, const float *means, void *occ, int64_t occ_capacity, void *free_set,
                    int64_t free_capacity, float voxel, uint8_t *keep, void *stream) {
+    GS_RANGE("gs_voxset_keep");
     if (n < 0 || (n > 0 && (!means || !keep)) || !ws_ok(occ) || !pow2(occ_capacity) || !(voxel > 0.f))
         return GS_ERR_INVALID_ARG;
     if (free_set && (!ws_ok(free_set) || !pow2(free_capacity))) return GS_ERR_INVALID_ARG;
@@ -567,6 +593,7 @@ int gs_pho_residual(int32_t num_edges, const gs_pho_edge *edges, int32_t num_ima
                     const float *images, const float *depths, const gs_camera *cameras, int32_t num_corr,
                     const gs_sim3 *corrections, const gs_pho_params *params, double *cost, int64_t *count,
                     double *H, double *g, void *scratch, size_t scratch_bytes, void *stream) {
+    GS_RANGE("gs_pho_residual");
     if (num_edges < 0 || num_edges > 65535 || !params) return GS_ERR_INVALID_ARG;
     if (num_edges == 0) return GS_OK;
     if (!edges || !images || !depths || !cameras || !corrections || !cost || !count || !H || !g || !scratch)
@@ -598,6 +625,7 @@ int gs_pho_residual(int32_t num_edges, const gs_pho_edge *edges, int32_t num_ima
 
 int gs_adam_step(int64_t n, const gs_adam_state *st, const gs_grads *grads, const float lr[5], int32_t zero_grads,
                  void *stream) {
+    GS_RANGE("gs_adam_step");
     if (n < 0 || !st || !grads || !lr || !st->step || !st->m || !st->v) return GS_ERR_INVALID_ARG;
     if (n > 0 && (!st->means || !st->log_scales || !st->quats || !st->opacity_logits || !st->opacities ||
                   !st->colors || !grads->means || !grads->log_scales || !grads->quats || !grads->opacities ||
@@ -608,6 +636,7 @@ int gs_adam_step(int64_t n, const gs_adam_state *st, const gs_grads *grads, cons
 
 int gs_adam_step_reg(int64_t n, const gs_adam_state *st, const gs_grads *grads, const float lr[5], float iso_weight,
                      int32_t zero_grads, double *iso_loss, void *stream) {
+    GS_RANGE("gs_adam_step_reg");
     if (n < 0 || !st || !grads || !lr || !st->step || !st->m || !st->v) return GS_ERR_INVALID_ARG;
     if (n > 0 && (!st->means || !st->log_scales || !st->quats || !st->opacity_logits || !st->opacities ||
                   !st->colors || !grads->means || !grads->log_scales || !grads->quats || !grads->opacities ||
@@ -625,6 +654,7 @@ __global__ void k_debug_expf(const float *x, float *ys, float *yc, long long n) 
 }
 
 int gs_grads_zero(int64_t n, const gs_grads *g, void *stream) {
+    GS_RANGE("gs_grads_zero");
     if (n < 0 || !g) return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
     if (!g->means || !g->log_scales || !g->quats || !g->opacities || !g->colors) return GS_ERR_INVALID_ARG;

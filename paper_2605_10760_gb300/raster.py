@@ -294,6 +294,41 @@ class AdamState:
 
 
 # ------------------------------------------------------------------------------------------
+# checkpoint / resume
+# ------------------------------------------------------------------------------------------
+
+_GFIELDS = ("means", "log_scales", "quats", "opacities", "colors")
+
+
+def save_checkpoint(path, g: Gaussians, adam: AdamState | None = None, extra: dict | None = None):
+    """Write the Gaussian parameters (and, with `adam`, its logits, moments, step counter and
+    learning rates) to `path` as a dict of CPU tensors."""
+    state = {"gaussians": {k: getattr(g, k).detach().cpu() for k in _GFIELDS}}
+    if adam is not None:
+        state["adam"] = {"logits": adam.logits.detach().cpu(), "m": adam.m.detach().cpu(),
+                         "v": adam.v.detach().cpu(), "step": adam.step.detach().cpu(), "lr": list(adam.lr)}
+    if extra:
+        state["extra"] = {k: (v.detach().cpu() if torch.is_tensor(v) else v) for k, v in extra.items()}
+    torch.save(state, path)
+
+
+def load_checkpoint(path, device="cuda"):
+    """Read a checkpoint written by save_checkpoint: returns (Gaussians, AdamState or None, extra).
+    The optimiser resumes exactly: same moments, step counter and learning rates."""
+    state = torch.load(path, map_location="cpu", weights_only=False)
+    g = Gaussians(*[state["gaussians"][k].to(device).contiguous() for k in _GFIELDS])
+    adam = None
+    if "adam" in state:
+        a = state["adam"]
+        adam = AdamState(g, tuple(a["lr"]))
+        adam.logits.copy_(a["logits"].to(device))
+        adam.m.copy_(a["m"].to(device))
+        adam.v.copy_(a["v"].to(device))
+        adam.step.copy_(a["step"].to(device))
+    return g, adam, state.get("extra", {})
+
+
+# ------------------------------------------------------------------------------------------
 # autograd
 # ------------------------------------------------------------------------------------------
 

@@ -122,3 +122,26 @@ def test_render_fwd_with_fused_l1_matches_separate_calls(R):
     loss_r, d_rgb_r, _ = R.loss_l1(img["rgb"], tgt, None, None, 1.0, 0.0)
     torch.cuda.synchronize()
     assert torch.equal(d_rgb_c, d_rgb_r) and abs(loss_c.item() - loss_r.item()) <= 1e-6 * abs(loss_r.item())
+
+
+def test_resume_from_checkpoint_continues_adam_exactly(R, tmp_path):
+    """Two Adam steps, checkpoint, two more steps == reload, two more steps (bit for bit)."""
+    sc = S.random_cloud(1000, seed=13)
+    rng = np.random.default_rng(13)
+    grads = [R.Gaussians(*[torch.from_numpy(rng.normal(0, 1, getattr(sc, k).shape).astype(np.float32)).cuda()
+                           for k in ("means", "log_scales", "quats", "opacities", "colors")]) for _ in range(4)]
+    g = R.Gaussians.from_scene(sc)
+    st = R.AdamState(g)
+    for i in range(2):
+        st.apply(R.Gaussians(*[t.clone() for t in (grads[i].means, grads[i].log_scales, grads[i].quats,
+                                                   grads[i].opacities, grads[i].colors)]), zero_grads=True)
+    R.save_checkpoint(tmp_path / "c.pt", g, st)
+    g2, st2, _ = R.load_checkpoint(tmp_path / "c.pt")
+    for gg, ss in ((g, st), (g2, st2)):
+        for i in range(2, 4):
+            ss.apply(R.Gaussians(*[t.clone() for t in (grads[i].means, grads[i].log_scales, grads[i].quats,
+                                                       grads[i].opacities, grads[i].colors)]), zero_grads=True)
+    torch.cuda.synchronize()
+    for k in ("means", "log_scales", "quats", "opacities", "colors"):
+        assert torch.equal(getattr(g, k), getattr(g2, k)), k
+    assert int(st.step.item()) == int(st2.step.item()) == 4
