@@ -566,11 +566,23 @@ def fusion_bench(R, S, torch, voxel=0.05, k=3.0, stride=2, reps=3):
     rc_f, n_f = fre.status()
     kept = int(keep.sum().item())
     ms = {key: statistics.median(val) for key, val in t.items()}
+    hbm = _peaks()["hbm_gbs"]
+    # streaming kernels: Sim(3) reads and writes 56 B per Gaussian; the keep pass reads a mean (12 B)
+    # and writes a flag (1 B) per Gaussian besides its two hash lookups
+    sim3_gbs = bor.n * 112 / (ms["sim3"] * 1e-3) / 1e9
+    keep_gbs = bor.n * 13 / (ms["keep"] * 1e-3) / 1e9
+    rays = 8 * ((wl.width + stride - 1) // stride) * ((wl.height + stride - 1) // stride)
     return {"workload": "floor4m halves: 2M target / 2M borrowed Gaussians, 8 keyframes 1200x680 (stride 2), "
                         "voxel %.2f m, k = %g" % (voxel, k),
             "ms": ms, "total_ms": sum(ms.values()), "borrowed": bor.n, "kept": kept,
-            "occupied_voxels": n_o, "free_voxels": n_f, "status": [rc_o, rc_f],
-            "rays": 8 * ((wl.width + stride - 1) // stride) * ((wl.height + stride - 1) // stride)}
+            "occupied_voxels": n_o, "free_voxels": n_f, "status": [rc_o, rc_f], "rays": rays,
+            "roofline": {"sim3": {"bound": "hbm", "achieved": sim3_gbs, "peak": hbm, "unit": "GB/s",
+                                  "frac": sim3_gbs / hbm},
+                         "keep": {"bound": "hbm", "achieved": keep_gbs, "peak": hbm, "unit": "GB/s",
+                                  "frac": keep_gbs / hbm},
+                         "occupied_gaussians_per_s": tgt.n / (ms["occupied"] * 1e-3),
+                         "free_rays_per_s": rays / (ms["free"] * 1e-3),
+                         "note": "hash insertion (occupied, free) is bound by L2 compare-and-swap traffic"}}
 
 
 def fused_map(R, S, torch, steps=3):
