@@ -89,8 +89,7 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     if (L->passes > kMaxPasses) return GS_ERR_INVALID_ARG;
     // the scan runs over the P touched-tile counts (onesweep) or the G tile key counts (bucket)
     L->scan_parts = std::max<long long>(1, (std::max(P, L->G) + kScanTile - 1) / kScanTile);
-    L->sort_ipt = sort_ipt_for(L->cap);
-    const long long sort_tile = (long long)kSortThreads * L->sort_ipt;
+    const long long sort_tile = (long long)kSortThreads * kSortIPT;
     L->sort_parts = std::max<long long>(1, (L->cap + sort_tile - 1) / sort_tile);
     long long chunks_total = 0;
     for (int v = 0; v < L->V; ++v) chunks_total += (pb->view_gauss_count[v] + kChunk - 1) / kChunk;
@@ -311,7 +310,7 @@ static BinArgs make_bin_args(const Layout &L, void *ws) {
     a.ranges = ws_ptr<uint32_t>(ws, L.o_ranges);
     a.srec = ws_ptr<float4>(ws, L.o_srec);
     a.st = ws_ptr<DevStatus>(ws, L.o_status);
-    a.V = L.V; a.Tx = L.Tx; a.Ty = L.Ty; a.passes = L.passes; a.sort_ipt = L.sort_ipt;
+    a.V = L.V; a.Tx = L.Tx; a.Ty = L.Ty; a.passes = L.passes;
     a.tw = (float)L.tw; a.th = (float)L.th;
     a.P = L.P; a.cap = L.cap; a.sort_parts = L.sort_parts; a.max_chunks = L.max_chunks; a.G = L.G;
     a.fault_scan_part = -1;

@@ -16,12 +16,10 @@ namespace gs {
 
 constexpr int kMaxPasses = 8;          // 8-bit digits of a 64-bit key
 constexpr int kSortThreads = 256;
-// keys per thread of a onesweep partition.  4096-key partitions (16 per thread) throughout: with
-// 1024-key partitions the per-digit look-back chains grow four times longer and a 270k-key sort
-// was measured slower on GB300, so the small variant is only compiled, not selected.
-constexpr int kSortIPTSmall = 4, kSortIPTLarge = 16;
-constexpr long long kSmallSortCap = 0;
-inline int sort_ipt_for(long long cap) { return cap <= kSmallSortCap ? kSortIPTSmall : kSortIPTLarge; }
+// keys per thread of a onesweep partition: 4096-key partitions (16 per thread).  Smaller
+// partitions (4 or 8 keys per thread) make the per-digit look-back chains longer and measured
+// slower on GB300 for every problem size of the benchmark.
+constexpr int kSortIPT = 16;
 constexpr int kScanThreads = 256;
 constexpr int kScanIPT = 16;
 constexpr int kScanTile = kScanThreads * kScanIPT;
@@ -56,7 +54,7 @@ struct ViewEntry {                // per-view table in the workspace (32 bytes)
 };
 
 struct Layout {
-    int V, W, H, tw, th, Tx, Ty, passes, sort_ipt;
+    int V, W, H, tw, th, Tx, Ty, passes;
     long long G, P, N, cap, max_count, max_chunks;
     long long scan_parts, sort_parts;
     int sort_mode, nb;                 // binning mode; records per staged render batch

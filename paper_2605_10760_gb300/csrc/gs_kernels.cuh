@@ -50,7 +50,7 @@ struct BinArgs {
     uint32_t *ranges;                  // [G,2]
     float4 *srec;                      // [cap,3] records in list order
     DevStatus *st;
-    int V, Tx, Ty, passes, sort_ipt;
+    int V, Tx, Ty, passes;
     float tw, th;
     long long P, cap, sort_parts, max_chunks, G;
     int fault_scan_part;               // -1 normally; >= 0: that scan partition never publishes

@@ -801,7 +801,7 @@ int run_bin_sort(const BinArgs &a, cudaStream_t s) {
     const int hist_grid = (int)std::min<long long>(sms * 4, std::max<long long>(sms, (a.cap + 2047) / 2048));
     k_hist<<<hist_grid, 256, 0, s>>>(a);
     count_launches(1);
-    const int rc2 = a.sort_ipt == kSortIPTSmall ? sweep_passes<kSortIPTSmall>(a, s) : sweep_passes<kSortIPTLarge>(a, s);
+    const int rc2 = sweep_passes<kSortIPT>(a, s);
     if (rc2) return rc2;
     k_ranges<<<sms * 8, 256, 0, s>>>(a.keys[a.passes & 1], a.vals[a.passes & 1], a.proj, a.srec, a.st, a.cap, a.G,
                                       a.P, a.ranges);
