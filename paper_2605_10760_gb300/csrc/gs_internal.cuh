@@ -17,8 +17,8 @@ namespace gs {
 constexpr int kMaxPasses = 8;          // 8-bit digits of a 64-bit key
 constexpr int kSortThreads = 256;
 // keys per thread of a onesweep partition: 4096-key partitions (16 per thread).  Smaller
-// partitions (4 or 8 keys per thread) make the per-digit look-back chains longer and measured
-// slower on GB300 for every problem size of the benchmark.
+// partitions (4 or 8 keys per thread) make the per-digit look-back chains longer, larger ones
+// (32 keys per thread, 255 registers) lengthen each CTA's ranking: both measured slower on GB300.
 constexpr int kSortIPT = 16;
 constexpr int kScanThreads = 256;
 constexpr int kScanIPT = 16;
