@@ -22,9 +22,9 @@
 // recovering T_j = T_{j+1} / (1 - alpha_j) and one running scalar Q (the upstream-weighted colour
 // and depth accumulated behind each entry, with the background and alpha-output terms), so no
 // per-pixel list is stored.  Each thread sums the 10 per-Gaussian gradient components of its two
-// pixels, then the warp reduces them with a transposed butterfly (13 shuffles instead of 50) after
-// which 10 lanes issue one atomic add each: a (Gaussian, warp) pair costs one warp-wide atomic
-// instruction; warps whose 64 pixels all skip the entry issue nothing, and entries past the
+// pixels, then the warp reduces them with a transposed butterfly (12 shuffles instead of 50) after
+// which 20 lanes issue one atomic add each (two halves per component): a (Gaussian, warp) pair
+// costs one warp-wide atomic instruction; warps whose 64 pixels all skip the entry issue nothing, and entries past the
 // warp's last blended position are not visited at all.
 //
 // In both kernels each warp drops the entries whose region bit is clear 32 at a time (a ballot
@@ -300,10 +300,11 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
     }
 }
 
-// Transposed butterfly over 16 slots: after the call lane l holds, in v[0], the warp sum of slot
-// s(l) = 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of l).  The 10 gradient components live in slots
-// 0..4 and 8..12 (kSlot); slots 5..7 and 13..15 are zero in every lane, so the first stage skips
-// their three all-zero pairs: 13 shuffles in total.
+// Transposed butterfly over 16 slots: after the call lanes 2s and 2s + 1 hold, in v[0], two
+// halves of the warp sum of slot s(l) = 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of l); both add
+// theirs to the gradient (the last butterfly stage is left to the atomic unit).  The 10 gradient
+// components live in slots 0..4 and 8..12 (kSlot); slots 5..7 and 13..15 are zero in every lane,
+// so the first stage skips their three all-zero pairs: 12 shuffles in total.
 __device__ __forceinline__ void warp_transpose_reduce16(float (&v)[16], int lane) {
     {
         const bool up = lane & 16;
@@ -339,7 +340,6 @@ __device__ __forceinline__ void warp_transpose_reduce16(float (&v)[16], int lane
         const float keep = up ? v[1] : v[0];
         v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
     }
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 // slot of each gradient component (mean_x, mean_y, A, B, C, opacity, depth, r, g, b)
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
     const uint32_t wbit = 1u << (tid >> 5);
     const int slot = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
     const int comp = slot < 5 ? slot : slot - 3;           // component index in the grad2d record
-    const bool issuer = ((lane & 1) == 0) && (slot < 5 || (slot >= 8 && slot < 13));
+    const bool issuer = slot < 5 || (slot >= 8 && slot < 13);   // 20 lanes, two per component
     const long long tpv = (long long)a.Tx * a.Ty;
     const long long HW = (long long)a.W * a.H;
     int lx, ly;
