@@ -221,22 +221,23 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
 #pragma unroll
                 for (int p = 0; p < kPPT; ++p) al[p] = fminf(a.amax, fp::mul(r1.y, spec_expf(-sg[p])));
                 const float4 r2 = rec[3 * k + 2];
+                // both pixels without branches: the same FP32 decisions (skip, stop before
+                // blending), taken as selects
 #pragma unroll
                 for (int p = 0; p < kPPT; ++p) {
-                    if (!ev[p] || al[p] < a.amin) continue;
+                    const bool bl = ev[p] && !(al[p] < a.amin);
                     const float Tn = fp::mul(T[p], fp::sub(1.0f, al[p]));
-                    if (Tn < a.tmin) {
-                        done[p] = true;
-                        visited[p] = b + k + 1;
-                        continue;
-                    }
-                    const float wgt = al[p] * T[p];
+                    const bool stop = bl && Tn < a.tmin;
+                    const bool acc = bl && !stop;
+                    done[p] = done[p] || stop;
+                    visited[p] = stop ? b + k + 1 : visited[p];
+                    const float wgt = acc ? al[p] * T[p] : 0.f;
                     C0[p] += r2.x * wgt;
                     C1[p] += r2.y * wgt;
                     C2[p] += r2.z * wgt;
                     D[p] += r1.z * wgt;
-                    T[p] = Tn;
-                    last[p] = b + k + 1;
+                    T[p] = acc ? Tn : T[p];
+                    last[p] = acc ? b + k + 1 : last[p];
                 }
                 if (done[0] && done[1]) break;
               }
@@ -479,15 +480,19 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
                         araw[p] = fp::mul(r1.y, e[p]);
                     }
                     const float4 r2 = rec[3 * k + 2];
+                    // both pixels evaluated without branches; a pixel that does not blend the
+                    // entry contributes zero (selects, not products, so an infinite e or a
+                    // meaningless alpha of a skipped pixel never reaches a sum)
 #pragma unroll
                     for (int p = 0; p < kPPT; ++p) {
                         const float al = fminf(a.amax, araw[p]);
-                        if (!ev[p] || al < a.amin) continue;
-                        contrib = true;
+                        const bool blend = ev[p] && !(al < a.amin);
+                        const bool uncapped = blend && araw[p] <= a.amax;
+                        contrib |= blend;
                         const float dy = dyv[p];
                         const float ioma = __fdividef(1.0f, 1.0f - al);
                         const float Tj = T[p] * ioma;
-                        const float w = al * Tj;
+                        const float w = blend ? al * Tj : 0.f;
                         gv[kSR] += gC0[p] * w;
                         gv[kSG] += gC1[p] * w;
                         gv[kSBl] += gC2[p] * w;
@@ -495,16 +500,15 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
                         const float Pj = gC0[p] * r2.x + gC1[p] * r2.y + gC2[p] * r2.z + gD[p] * r1.z;
                         const float dLda = Tj * Pj - Q[p] * ioma;
                         Q[p] += Pj * w;
-                        T[p] = Tj;
-                        if (araw[p] <= a.amax) {
-                            gv[kSO] += dLda * e[p];
-                            const float dLds = -dLda * al;
-                            gv[kSA] += 0.5f * dLds * dx * dx;
-                            gv[kSB] += dLds * dx * dy;
-                            gv[kSC] += 0.5f * dLds * dy * dy;
-                            gv[kSMx] -= dLds * (r0.z * dx + r0.w * dy);
-                            gv[kSMy] -= dLds * (r0.w * dx + r1.x * dy);
-                        }
+                        T[p] = blend ? Tj : T[p];
+                        gv[kSO] += uncapped ? dLda * e[p] : 0.f;
+                        const float dLds = uncapped ? -dLda * al : 0.f;
+                        const float tdx = dLds * dx, tdy = dLds * dy;
+                        gv[kSA] += 0.5f * tdx * dx;
+                        gv[kSB] += tdx * dy;
+                        gv[kSC] += 0.5f * tdy * dy;
+                        gv[kSMx] -= r0.z * tdx + r0.w * tdy;
+                        gv[kSMy] -= r0.w * tdx + r1.x * tdy;
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
