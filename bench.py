@@ -162,7 +162,7 @@ class Pipeline:
                                                                               "opacities", "colors")])
         self.R.L.check(self.R.L.load().gs_grads_zero(self.g.n, C.byref(gg), self.R._stream()), "gs_grads_zero")
 
-    def stages(self):
+    def stages(self, zero=True):
         pb = self.pb
         return [
             lambda: pb.project(self.g),
@@ -170,7 +170,8 @@ class Pipeline:
             # forward compositing with the L1 loss and its gradient in the same kernel's epilogue
             lambda: pb.render_fwd_l1(self.img, self.rgb_t, self.depth_t, 1.0, 0.1, self.d_rgb, self.d_depth,
                                      self.loss),
-            lambda: (self.zero_grads(), pb.render_bwd(self.g, self.img, self.d_rgb, self.d_depth, None, self.grads)),
+            lambda: (zero and self.zero_grads(),
+                     pb.render_bwd(self.g, self.img, self.d_rgb, self.d_depth, None, self.grads)),
             lambda: pb.pose_grad(self.pose),
         ]
 
@@ -199,9 +200,20 @@ class Pipeline:
             with torch.cuda.graph(gr):
                 fn()
             self.graphs.append(gr)
+        # the whole step: the gradient zeroing runs on a forked branch of the graph, concurrently
+        # with the projection, the sort and the forward (it only has to finish before the backward)
         self.whole = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
         with torch.cuda.graph(self.whole):
-            for fn in self.stages():
+            main = torch.cuda.current_stream()
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                self.zero_grads()
+            st = self.stages(zero=False)
+            for fn in st[:3]:
+                fn()
+            main.wait_stream(side)
+            for fn in st[3:]:
                 fn()
         torch.cuda.synchronize()
 
@@ -756,7 +768,7 @@ def main():
     fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s at max SM clock
     # DRAM bytes (read + write) of one launch from an ncu capture of this workload's current
     # kernel code (profiles/*_room500k.md); a stage without such a capture reports None
-    traffic = {}
+    traffic = {"render_fwd_l1": 26_614_528, "render_bwd": 35_203_584}
     if dom in ("render_fwd_l1", "render_bwd"):
         flops = stats["fwd_pairs"] * FLOP_FWD if dom == "render_fwd_l1" else stats["bwd_pairs"] * FLOP_BWD
         ach = flops / (stage_ms[dom] * 1e-3) / 1e12
