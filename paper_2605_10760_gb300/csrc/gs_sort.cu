@@ -261,6 +261,12 @@ constexpr int kSweepWarps = kSortThreads / 32;
 template <int IPT>
 constexpr size_t sweep_dyn_smem() { return (size_t)kSortThreads * IPT * (sizeof(uint64_t) + sizeof(uint32_t)); }
 
+// Predecessors whose digit words one look-back round loads together.  A partition's keys, values
+// and ranks already sit in shared memory when it looks back, so the window costs registers only
+// while it is consumed; a window this wide lets a partition of a small sort (tens of partitions,
+// all running at once) add up every predecessor's published count in one or two rounds.
+constexpr int kLookback = 32;
+
 template <int IPT>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
     constexpr int kSortIPT = IPT;
@@ -275,9 +281,16 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
     __shared__ uint32_t s_part;
     __shared__ int s_bad;
     __shared__ uint32_t s_goff[256];      // exclusive global start of each digit in this pass
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the first partition is claimed while the pass histogram is read and scanned
+    if (threadIdx.x == 0) {
+        s_part = atomicAdd(a.ctr, 1u);
+        s_bad = 0;
+    }
+#pragma unroll
+    for (int w = 0; w < kSweepWarps; ++w) s_wcnt[w][threadIdx.x] = 0;
     {
         // exclusive scan of the pass's 256 digit counts, once per CTA
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const uint32_t c = a.hist[threadIdx.x];
         uint32_t incl = c;
 #pragma unroll
@@ -285,78 +298,87 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        if (lane == 31) s_tstart[warp] = incl;   // scratch: per-warp totals
+        if (lane == 31) s_wsum[warp] = incl;
         __syncthreads();
         uint32_t off = 0;
-        for (int w = 0; w < warp; ++w) off += s_tstart[w];
+        for (int w = 0; w < warp; ++w) off += s_wsum[w];
         s_goff[threadIdx.x] = off + incl - c;
         __syncthreads();
     }
     const unsigned long long Kll = min(a.st->num_keys, (unsigned long long)a.cap);
     const uint32_t K = (uint32_t)Kll;
     const uint32_t nparts = (K + kSortTile - 1) / kSortTile;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = lanemask_lt();
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_part = atomicAdd(a.ctr, 1u);
-            s_bad = 0;
-        }
-#pragma unroll
-        for (int w = 0; w < kSweepWarps; ++w) s_wcnt[w][threadIdx.x] = 0;
-        __syncthreads();
         const uint32_t part = s_part;
         if (part >= nparts) break;
         const uint32_t base = part * kSortTile;
         const uint32_t tile_n = min((uint32_t)kSortTile, K - base);
-        uint64_t k[kSortIPT];
-        uint32_t val[kSortIPT];
-        uint32_t rk[kSortIPT];
+        const int d = threadIdx.x;            // thread d owns digit d from the digit totals on
+        uint32_t total = 0, tstart = 0;
+        {
+            uint64_t k[kSortIPT];
+            uint32_t val[kSortIPT];
+            uint32_t rk[kSortIPT];
 #pragma unroll
-        for (int r = 0; r < kSortIPT; ++r) {
-            const uint32_t li = warp * (kSortIPT * 32) + r * 32 + lane;
-            const bool valid = li < tile_n;
-            k[r] = valid ? a.kin[base + li] : 0ull;
-            val[r] = valid ? a.vin[base + li] : 0u;
-        }
+            for (int r = 0; r < kSortIPT; ++r) {
+                const uint32_t li = warp * (kSortIPT * 32) + r * 32 + lane;
+                const bool valid = li < tile_n;
+                k[r] = valid ? a.kin[base + li] : 0ull;
+                val[r] = valid ? a.vin[base + li] : 0u;
+            }
+            // stable rank inside the warp: match_any groups equal digits, per-warp digit counters
 #pragma unroll
-        for (int r = 0; r < kSortIPT; ++r) {
-            const uint32_t li = warp * (kSortIPT * 32) + r * 32 + lane;
-            const uint32_t d = li < tile_n ? (uint32_t)((k[r] >> a.shift) & 255u) : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t c = d < 256u ? s_wcnt[warp][d] : 0u;
-            __syncwarp();
-            if (d < 256u && lane == __ffs(peers) - 1) s_wcnt[warp][d] = c + __popc(peers);
-            __syncwarp();
-            rk[r] = c + __popc(peers & lt_mask);
-        }
-        __syncthreads();
-        // thread d owns digit d
-        const int d = threadIdx.x;
-        uint32_t total = 0;
+            for (int r = 0; r < kSortIPT; ++r) {
+                const uint32_t li = warp * (kSortIPT * 32) + r * 32 + lane;
+                const uint32_t dg = li < tile_n ? (uint32_t)((k[r] >> a.shift) & 255u) : 256u;
+                const unsigned peers = __match_any_sync(0xffffffffu, dg);
+                const uint32_t c = dg < 256u ? s_wcnt[warp][dg] : 0u;
+                __syncwarp();
+                if (dg < 256u && lane == __ffs(peers) - 1) s_wcnt[warp][dg] = c + __popc(peers);
+                __syncwarp();
+                rk[r] = c + __popc(peers & lt_mask);
+            }
+            __syncthreads();
 #pragma unroll
-        for (int w = 0; w < kSweepWarps; ++w) {
-            const uint32_t c = s_wcnt[w][d];
-            s_wcnt[w][d] = total;
-            total += c;
-        }
-        uint32_t *my_state = a.state + (size_t)part * 256 + d;
-        if (part == 0) st_relaxed_u32(my_state, kFlagInc | total);
-        else st_relaxed_u32(my_state, kFlagAgg | total);
-        // exclusive scan of the digit totals inside the tile
-        uint32_t incl = total;
+            for (int w = 0; w < kSweepWarps; ++w) {
+                const uint32_t c = s_wcnt[w][d];
+                s_wcnt[w][d] = total;
+                total += c;
+            }
+            // publish this partition's digit count before anything else, for the successors
+            st_relaxed_u32(a.state + (size_t)part * 256 + d, (part == 0 ? kFlagInc : kFlagAgg) | total);
+            // exclusive scan of the digit totals inside the partition
+            uint32_t incl = total;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            uint32_t woff = 0;
+            for (int w = 0; w < warp; ++w) woff += s_wsum[w];
+            tstart = woff + incl - total;
+            s_tstart[d] = tstart;
+            __syncthreads();
+            // local scatter: the partition in digit order in shared memory (needs no global offset)
+#pragma unroll
+            for (int r = 0; r < kSortIPT; ++r) {
+                const uint32_t li = warp * (kSortIPT * 32) + r * 32 + lane;
+                if (li < tile_n) {
+                    const uint32_t dd = (uint32_t)((k[r] >> a.shift) & 255u);
+                    const uint32_t lp = s_tstart[dd] + s_wcnt[warp][dd] + rk[r];
+                    s_keys[lp] = k[r];
+                    s_vals[lp] = val[r];
+                }
+            }
         }
-        if (lane == 31) s_wsum[warp] = incl;
-        // look back over the predecessors' counts of digit d
+        // look back over the predecessors' counts of digit d: a window of kLookback words loaded
+        // together, consumed nearest first until an inclusive word (done) or a not-yet-published
+        // one (wait, then reload from there); every wait is bounded
         uint32_t excl = 0;
         if (part > 0) {
-            // window of kLookback predecessors loaded together, consumed nearest first until an
-            // inclusive word (done) or a not-yet-published one (wait, then reload from there)
-            constexpr int kLookback = 8;
             int j = (int)part - 1;
             unsigned long long spins = 0;
             bool timed_out = false;
@@ -387,29 +409,13 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
                     __nanosleep(64);
                 }
             }
-            st_relaxed_u32(my_state, kFlagInc | ((excl + total) & kVal));
+            st_relaxed_u32(a.state + (size_t)part * 256 + d, kFlagInc | ((excl + total) & kVal));
             if (timed_out) {
                 s_bad = 1;
                 record_error(a.st, GS_ERR_TIMEOUT, 4);
             }
         }
-        __syncthreads();
-        uint32_t woff = 0;
-        for (int w = 0; w < warp; ++w) woff += s_wsum[w];
-        const uint32_t tstart = woff + incl - total;
-        s_tstart[d] = tstart;
         s_gbase[d] = s_goff[d] + excl - tstart;
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kSortIPT; ++r) {
-            const uint32_t li = warp * (kSortIPT * 32) + r * 32 + lane;
-            if (li < tile_n) {
-                const uint32_t dd = (uint32_t)((k[r] >> a.shift) & 255u);
-                const uint32_t lp = s_tstart[dd] + s_wcnt[warp][dd] + rk[r];
-                s_keys[lp] = k[r];
-                s_vals[lp] = val[r];
-            }
-        }
         __syncthreads();
         if (!s_bad) {
             for (uint32_t i = threadIdx.x; i < tile_n; i += kSortThreads) {
@@ -422,6 +428,14 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
                 }
             }
         }
+        __syncthreads();
+        // next partition; the per-warp digit counters start from zero again
+        if (threadIdx.x == 0) {
+            s_part = atomicAdd(a.ctr, 1u);
+            s_bad = 0;
+        }
+#pragma unroll
+        for (int w = 0; w < kSweepWarps; ++w) s_wcnt[w][threadIdx.x] = 0;
         __syncthreads();
     }
 }
