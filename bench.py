@@ -768,7 +768,7 @@ def main():
     fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s at max SM clock
     # DRAM bytes (read + write) of one launch from an ncu capture of this workload's current
     # kernel code (profiles/*_room500k.md); a stage without such a capture reports None
-    traffic = {"render_fwd_l1": 26_614_528, "render_bwd": 35_203_584}
+    traffic = {"render_fwd_l1": 26_660_096, "render_bwd": 35_184_128}
     if dom in ("render_fwd_l1", "render_bwd"):
         flops = stats["fwd_pairs"] * FLOP_FWD if dom == "render_fwd_l1" else stats["bwd_pairs"] * FLOP_BWD
         ach = flops / (stage_ms[dom] * 1e-3) / 1e12

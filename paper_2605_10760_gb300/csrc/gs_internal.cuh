@@ -216,6 +216,50 @@ __device__ __forceinline__ float spec_sigma(float A, float B, float C, float dx,
 }
 
 // ------------------------------------------------------------------------------------------
+// the same chain on two arguments at once (two pixels of a thread): packed FP32x2 operations
+// round each component exactly like the scalar operation, so every component equals the scalar
+// chain's result bit for bit
+// ------------------------------------------------------------------------------------------
+namespace fp2 {
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+}  // namespace fp2
+
+// spec_expf of both components (a - b is computed as a + (-b) and (-k) c as k (-c), both exact)
+__device__ __forceinline__ float2 spec_expf2(float2 x) {
+    const float kLog2e = 0x1.715476p+0f;
+    const float kLn2Hi = 0x1.62e4p-1f;
+    const float kLn2Lo = 0x1.7f7d1cp-20f;
+    const float kShift = 12582912.0f;
+    const float2 t = fp2::add(fp2::mul(x, fp2::splat(kLog2e)), fp2::splat(kShift));
+    const float2 kf = fp2::add(t, fp2::splat(-kShift));
+    float2 r = fp2::fma(kf, fp2::splat(-kLn2Hi), x);
+    r = fp2::fma(kf, fp2::splat(-kLn2Lo), r);
+    float2 p = fp2::fma(fp2::splat(0x1.a01a02p-13f), r, fp2::splat(0x1.6c16c2p-10f));
+    p = fp2::fma(p, r, fp2::splat(0x1.111112p-7f));
+    p = fp2::fma(p, r, fp2::splat(0x1.555556p-5f));
+    p = fp2::fma(p, r, fp2::splat(0x1.555556p-3f));
+    p = fp2::fma(p, r, fp2::splat(0.5f));
+    p = fp2::fma(p, r, fp2::splat(1.0f));
+    p = fp2::fma(p, r, fp2::splat(1.0f));
+    const int kx = __float_as_int(t.x) - 0x4B400000, ky = __float_as_int(t.y) - 0x4B400000;
+    float2 e = fp2::mul(p, make_float2(__int_as_float((kx + 127) << 23), __int_as_float((ky + 127) << 23)));
+    const float inf = __int_as_float(0x7f800000);
+    e.x = !(x.x > -87.0f) ? 0.0f : (x.x > 88.0f ? inf : e.x);
+    e.y = !(x.y > -87.0f) ? 0.0f : (x.y > 88.0f ? inf : e.y);
+    return e;
+}
+
+// spec_sigma at two pixels of one column (dy per pixel)
+__device__ __forceinline__ float2 spec_sigma2(float A, float B, float C, float dx, float2 dy) {
+    const float2 q = fp2::fma(fp2::splat(fp::mul(A, dx)), fp2::splat(dx), fp2::mul(fp2::mul(fp2::splat(C), dy), dy));
+    return fp2::fma(fp2::splat(fp::mul(B, dx)), dy, fp2::mul(fp2::splat(0.5f), q));
+}
+
+// ------------------------------------------------------------------------------------------
 // relaxed device-scope loads / stores for decoupled look-back
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {

@@ -28,7 +28,10 @@
 // warp's last blended position are not visited at all.
 //
 // In both kernels each warp drops the entries whose region bit is clear 32 at a time (a ballot
-// over the mask bytes) and visits only the rest.  The forward can also evaluate the L1 terms of
+// over the mask bytes) and visits only the rest.  A thread's two pixels are the two components of
+// packed FP32x2 arithmetic (one instruction for both pixels, each component rounded exactly as
+// the scalar operation, so the decision chain is unchanged bit for bit); the decisions
+// themselves are scalar compares and selects.  The forward can also evaluate the L1 terms of
 // the mapping loss and their gradient in its per-pixel epilogue (gs_render_fwd_l1).
 #include "gs_kernels.cuh"
 
@@ -154,17 +157,18 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
         const int x = tx * TW + lx, y0 = ty * TH + ly;
         const uint32_t start = a.ranges[2 * g], end = a.ranges[2 * g + 1];
         const int n = (int)(end - start);
+        // per-pixel state of the thread's two pixels, packed (component p = pixel p)
+        static_assert(kPPT == 2, "two pixels per thread, one per packed component");
         bool done[kPPT];
-        float T[kPPT], C0[kPPT], C1[kPPT], C2[kPPT], D[kPPT], py[kPPT];
         int last[kPPT], visited[kPPT];
+        float2 T = fp2::splat(1.0f), C0 = fp2::splat(0.f), C1 = fp2::splat(0.f), C2 = fp2::splat(0.f),
+               D = fp2::splat(0.f);
+        const float2 py = make_float2((float)y0 + 0.5f, (float)(y0 + 1) + 0.5f);
 #pragma unroll
         for (int p = 0; p < kPPT; ++p) {
             done[p] = !(x < a.W && y0 + p < a.H);
-            T[p] = 1.0f;
-            C0[p] = C1[p] = C2[p] = D[p] = 0.f;
             last[p] = 0;
             visited[p] = done[p] ? 0 : n;      // entries visited, up to and including the stopping one
-            py[p] = (float)(y0 + p) + 0.5f;
         }
         const float px = (float)x + 0.5f;
         const int nb = (n + NB - 1) / NB;
@@ -209,36 +213,32 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
                 const float4 r1 = rec[3 * k + 1];
                 const float cut = rec[3 * k + 2].w;
                 const float dx = fp::sub(px, r0.x);
-                float sg[kPPT];
-                bool ev[kPPT];
-#pragma unroll
-                for (int p = 0; p < kPPT; ++p) {
-                    sg[p] = spec_sigma(r0.z, r0.w, r1.x, dx, fp::sub(py[p], r0.y));
-                    ev[p] = !done[p] && !(sg[p] < 0.0f) && !(sg[p] > cut);
-                }
-                if (!(ev[0] || ev[1])) continue;
-                float al[kPPT];
-#pragma unroll
-                for (int p = 0; p < kPPT; ++p) al[p] = fminf(a.amax, fp::mul(r1.y, spec_expf(-sg[p])));
+                const float2 sg = spec_sigma2(r0.z, r0.w, r1.x, dx, fp2::add(py, fp2::splat(-r0.y)));
+                const bool ev0 = !done[0] && !(sg.x < 0.0f) && !(sg.x > cut);
+                const bool ev1 = !done[1] && !(sg.y < 0.0f) && !(sg.y > cut);
+                if (!(ev0 || ev1)) continue;
+                const float2 ar = fp2::mul(fp2::splat(r1.y), spec_expf2(fp2::neg(sg)));
+                const float2 al = make_float2(fminf(a.amax, ar.x), fminf(a.amax, ar.y));
                 const float4 r2 = rec[3 * k + 2];
                 // both pixels without branches: the same FP32 decisions (skip, stop before
                 // blending), taken as selects
-#pragma unroll
-                for (int p = 0; p < kPPT; ++p) {
-                    const bool bl = ev[p] && !(al[p] < a.amin);
-                    const float Tn = fp::mul(T[p], fp::sub(1.0f, al[p]));
-                    const bool stop = bl && Tn < a.tmin;
-                    const bool acc = bl && !stop;
-                    done[p] = done[p] || stop;
-                    visited[p] = stop ? b + k + 1 : visited[p];
-                    const float wgt = acc ? al[p] * T[p] : 0.f;
-                    C0[p] += r2.x * wgt;
-                    C1[p] += r2.y * wgt;
-                    C2[p] += r2.z * wgt;
-                    D[p] += r1.z * wgt;
-                    T[p] = acc ? Tn : T[p];
-                    last[p] = acc ? b + k + 1 : last[p];
-                }
+                const float2 Tn = fp2::mul(T, fp2::add(fp2::splat(1.0f), fp2::neg(al)));
+                const float2 w = fp2::mul(al, T);
+                const bool bl0 = ev0 && !(al.x < a.amin), bl1 = ev1 && !(al.y < a.amin);
+                const bool stop0 = bl0 && Tn.x < a.tmin, stop1 = bl1 && Tn.y < a.tmin;
+                const bool acc0 = bl0 && !stop0, acc1 = bl1 && !stop1;
+                done[0] = done[0] || stop0;
+                done[1] = done[1] || stop1;
+                visited[0] = stop0 ? b + k + 1 : visited[0];
+                visited[1] = stop1 ? b + k + 1 : visited[1];
+                const float2 wgt = make_float2(acc0 ? w.x : 0.f, acc1 ? w.y : 0.f);
+                C0 = fp2::fma(fp2::splat(r2.x), wgt, C0);
+                C1 = fp2::fma(fp2::splat(r2.y), wgt, C1);
+                C2 = fp2::fma(fp2::splat(r2.z), wgt, C2);
+                D = fp2::fma(fp2::splat(r1.z), wgt, D);
+                T = make_float2(acc0 ? Tn.x : T.x, acc1 ? Tn.y : T.y);
+                last[0] = acc0 ? b + k + 1 : last[0];
+                last[1] = acc1 ? b + k + 1 : last[1];
                 if (done[0] && done[1]) break;
               }
             }
@@ -262,14 +262,16 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
             pairs += (unsigned long long)visited[p];
             if (x < a.W && y0 + p < a.H) {
                 const long long pix = (long long)(y0 + p) * a.W + x;
-                const float c[3] = {C0[p] + T[p] * a.bg0, C1[p] + T[p] * a.bg1, C2[p] + T[p] * a.bg2};
+                const float Tp = p ? T.y : T.x, Dp = p ? D.y : D.x;
+                const float c[3] = {(p ? C0.y : C0.x) + Tp * a.bg0, (p ? C1.y : C1.x) + Tp * a.bg1,
+                                    (p ? C2.y : C2.x) + Tp * a.bg2};
                 if (a.rgb) {
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) a.rgb[(3 * (long long)v + ch) * HW + pix] = c[ch];
                 }
-                if (a.depth) a.depth[(long long)v * HW + pix] = D[p];
-                if (a.alpha) a.alpha[(long long)v * HW + pix] = 1.0f - T[p];
-                a.finalT[(long long)v * HW + pix] = T[p];
+                if (a.depth) a.depth[(long long)v * HW + pix] = Dp;
+                if (a.alpha) a.alpha[(long long)v * HW + pix] = 1.0f - Tp;
+                a.finalT[(long long)v * HW + pix] = Tp;
                 a.last[(long long)v * HW + pix] = last[p];
                 if (a.rgb_t) {   // L1 terms and their gradient, as gs_loss_l1 computes them
 #pragma unroll
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
                     }
                     if (a.depth_t) {
                         const long long idx = (long long)v * HW + pix;
-                        const float d = D[p] - a.depth_t[idx];
+                        const float d = Dp - a.depth_t[idx];
                         l1_d += fabsf(d);
                         a.d_depth[idx] = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * a.sc_d;
                     }
@@ -383,36 +385,40 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
         const uint32_t start = a.ranges[2 * g];
         const int n = (int)(a.ranges[2 * g + 1] - start);
         const float px = (float)x + 0.5f;
+        // per-pixel state of the thread's two pixels, packed (component p = pixel p)
+        static_assert(kPPT == 2, "two pixels per thread, one per packed component");
         int lst[kPPT];
-        float T[kPPT], gC0[kPPT], gC1[kPPT], gC2[kPPT], gD[kPPT], py[kPPT];
-        // Q = sum over blended entries behind the current one of (gC . c + gD z) alpha T, plus the
-        // background and alpha-output terms: dL/dalpha_j = T_j (gC . c_j + gD z_j) - Q / (1 - alpha_j)
-        float Q[kPPT];
+        float tT[kPPT], tQ[kPPT], tC0[kPPT], tC1[kPPT], tC2[kPPT], tD[kPPT];
         int tmax = 0;
 #pragma unroll
         for (int p = 0; p < kPPT; ++p) {
             lst[p] = 0;
-            T[p] = 1.0f;
-            gC0[p] = gC1[p] = gC2[p] = gD[p] = 0.f;
+            tT[p] = 1.0f;
+            tC0[p] = tC1[p] = tC2[p] = tD[p] = 0.f;
             float gA = 0.f;
-            py[p] = (float)(y0 + p) + 0.5f;
             if (x < a.W && y0 + p < a.H) {
                 const long long pix = (long long)(y0 + p) * a.W + x;
                 lst[p] = min(max(a.last[(long long)v * HW + pix], 0), n);   // never past the list
-                T[p] = a.finalT[(long long)v * HW + pix];
+                tT[p] = a.finalT[(long long)v * HW + pix];
                 if (a.d_rgb) {
-                    gC0[p] = a.d_rgb[(3 * (long long)v + 0) * HW + pix];
-                    gC1[p] = a.d_rgb[(3 * (long long)v + 1) * HW + pix];
-                    gC2[p] = a.d_rgb[(3 * (long long)v + 2) * HW + pix];
+                    tC0[p] = a.d_rgb[(3 * (long long)v + 0) * HW + pix];
+                    tC1[p] = a.d_rgb[(3 * (long long)v + 1) * HW + pix];
+                    tC2[p] = a.d_rgb[(3 * (long long)v + 2) * HW + pix];
                 }
-                if (a.d_depth) gD[p] = a.d_depth[(long long)v * HW + pix];
+                if (a.d_depth) tD[p] = a.d_depth[(long long)v * HW + pix];
                 if (a.d_alpha) gA = a.d_alpha[(long long)v * HW + pix];
             }
             // rgb = sum c alpha T + T_final bg, alpha_out = 1 - T_final
-            Q[p] = T[p] * (gC0[p] * a.bg0 + gC1[p] * a.bg1 + gC2[p] * a.bg2 - gA);
+            tQ[p] = tT[p] * (tC0[p] * a.bg0 + tC1[p] * a.bg1 + tC2[p] * a.bg2 - gA);
             pairs += (unsigned long long)lst[p];
             tmax = max(tmax, lst[p]);
         }
+        // Q = sum over blended entries behind the current one of (gC . c + gD z) alpha T, plus the
+        // background and alpha-output terms: dL/dalpha_j = T_j (gC . c_j + gD z_j) - Q / (1 - alpha_j)
+        float2 T = make_float2(tT[0], tT[1]), Q = make_float2(tQ[0], tQ[1]);
+        const float2 gC0 = make_float2(tC0[0], tC0[1]), gC1 = make_float2(tC1[0], tC1[1]),
+                     gC2 = make_float2(tC2[0], tC2[1]), gD = make_float2(tD[0], tD[1]);
+        const float2 py = make_float2((float)y0 + 0.5f, (float)(y0 + 1) + 0.5f);
         const int wmax = __reduce_max_sync(0xffffffffu, tmax);
         if (lane == 0) atomicMax(&sm.maxlast, wmax);
         __syncthreads();
@@ -460,56 +466,59 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
                 const float4 r1 = rec[3 * k + 1];
                 const float cut = rec[3 * k + 2].w;
                 const float dx = fp::sub(px, r0.x);
-                float sg[kPPT], dyv[kPPT];
-                bool ev[kPPT];
-#pragma unroll
-                for (int p = 0; p < kPPT; ++p) {
-                    dyv[p] = fp::sub(py[p], r0.y);
-                    sg[p] = spec_sigma(r0.z, r0.w, r1.x, dx, dyv[p]);
-                    ev[p] = pos < lst[p] && !(sg[p] < 0.0f) && !(sg[p] > cut);
-                }
+                const float2 dy = fp2::add(py, fp2::splat(-r0.y));
+                const float2 sg = spec_sigma2(r0.z, r0.w, r1.x, dx, dy);
+                const bool ev0 = pos < lst[0] && !(sg.x < 0.0f) && !(sg.x > cut);
+                const bool ev1 = pos < lst[1] && !(sg.y < 0.0f) && !(sg.y > cut);
                 float gv[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) gv[c] = 0.f;
                 bool contrib = false;
-                if (ev[0] || ev[1]) {
-                    float e[kPPT], araw[kPPT];
-#pragma unroll
-                    for (int p = 0; p < kPPT; ++p) {
-                        e[p] = spec_expf(-sg[p]);
-                        araw[p] = fp::mul(r1.y, e[p]);
-                    }
+                if (ev0 || ev1) {
+                    const float2 e = spec_expf2(fp2::neg(sg));
+                    const float2 araw = fp2::mul(fp2::splat(r1.y), e);
+                    const float2 al = make_float2(fminf(a.amax, araw.x), fminf(a.amax, araw.y));
                     const float4 r2 = rec[3 * k + 2];
                     // both pixels evaluated without branches; a pixel that does not blend the
                     // entry contributes zero (selects, not products, so an infinite e or a
                     // meaningless alpha of a skipped pixel never reaches a sum)
-#pragma unroll
-                    for (int p = 0; p < kPPT; ++p) {
-                        const float al = fminf(a.amax, araw[p]);
-                        const bool blend = ev[p] && !(al < a.amin);
-                        const bool uncapped = blend && araw[p] <= a.amax;
-                        contrib |= blend;
-                        const float dy = dyv[p];
-                        const float ioma = __fdividef(1.0f, 1.0f - al);
-                        const float Tj = T[p] * ioma;
-                        const float w = blend ? al * Tj : 0.f;
-                        gv[kSR] += gC0[p] * w;
-                        gv[kSG] += gC1[p] * w;
-                        gv[kSBl] += gC2[p] * w;
-                        gv[kSZ] += gD[p] * w;
-                        const float Pj = gC0[p] * r2.x + gC1[p] * r2.y + gC2[p] * r2.z + gD[p] * r1.z;
-                        const float dLda = Tj * Pj - Q[p] * ioma;
-                        Q[p] += Pj * w;
-                        T[p] = blend ? Tj : T[p];
-                        gv[kSO] += uncapped ? dLda * e[p] : 0.f;
-                        const float dLds = uncapped ? -dLda * al : 0.f;
-                        const float tdx = dLds * dx, tdy = dLds * dy;
-                        gv[kSA] += 0.5f * tdx * dx;
-                        gv[kSB] += tdx * dy;
-                        gv[kSC] += 0.5f * tdy * dy;
-                        gv[kSMx] -= r0.z * tdx + r0.w * tdy;
-                        gv[kSMy] -= r0.w * tdx + r1.x * tdy;
-                    }
+                    const bool bl0 = ev0 && !(al.x < a.amin), bl1 = ev1 && !(al.y < a.amin);
+                    const bool un0 = bl0 && araw.x <= a.amax, un1 = bl1 && araw.y <= a.amax;
+                    contrib = bl0 || bl1;
+                    const float2 oma = fp2::add(fp2::splat(1.0f), fp2::neg(al));
+                    const float2 ioma = make_float2(__fdividef(1.0f, oma.x), __fdividef(1.0f, oma.y));
+                    const float2 Tj = fp2::mul(T, ioma);
+                    const float2 wr = fp2::mul(al, Tj);
+                    const float2 w = make_float2(bl0 ? wr.x : 0.f, bl1 ? wr.y : 0.f);
+                    const float2 Pj = fp2::fma(gD, fp2::splat(r1.z),
+                                               fp2::fma(gC2, fp2::splat(r2.z),
+                                                        fp2::fma(gC1, fp2::splat(r2.y), fp2::mul(gC0, fp2::splat(r2.x)))));
+                    const float2 dLda = fp2::fma(Tj, Pj, fp2::neg(fp2::mul(Q, ioma)));
+                    Q = fp2::fma(Pj, w, Q);
+                    T = make_float2(bl0 ? Tj.x : T.x, bl1 ? Tj.y : T.y);
+                    const float2 cR = fp2::mul(gC0, w), cG = fp2::mul(gC1, w), cB = fp2::mul(gC2, w),
+                                 cZ = fp2::mul(gD, w);
+                    gv[kSR] = cR.x + cR.y;
+                    gv[kSG] = cG.x + cG.y;
+                    gv[kSBl] = cB.x + cB.y;
+                    gv[kSZ] = cZ.x + cZ.y;
+                    const float2 oe = fp2::mul(dLda, e);
+                    gv[kSO] = (un0 ? oe.x : 0.f) + (un1 ? oe.y : 0.f);
+                    // dL/dsigma per pixel; the conic and mean gradients are sums over the two
+                    // pixels of dL/dsigma times 1/2 dx^2, dx dy, 1/2 dy^2 and -(A dx + B dy),
+                    // -(B dx + C dy): dx is the pair's, so only s0 = sum dL/dsigma,
+                    // s1 = sum dL/dsigma dy and s2 = sum dL/dsigma dy^2 need both pixels
+                    const float2 ds = fp2::mul(dLda, al);
+                    const float2 dLds = make_float2(un0 ? -ds.x : 0.f, un1 ? -ds.y : 0.f);
+                    const float2 t1 = fp2::mul(dLds, dy);
+                    const float2 t2 = fp2::mul(t1, dy);
+                    const float s0 = dLds.x + dLds.y, s1 = t1.x + t1.y, s2 = t2.x + t2.y;
+                    const float s0dx = s0 * dx;
+                    gv[kSA] = 0.5f * s0dx * dx;
+                    gv[kSB] = s1 * dx;
+                    gv[kSC] = 0.5f * s2;
+                    gv[kSMx] = -(r0.z * s0dx + r0.w * s1);
+                    gv[kSMy] = -(r0.w * s0dx + r1.x * s1);
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
                     warp_transpose_reduce16(gv, lane);
