@@ -760,7 +760,7 @@ def main():
     npx = pipe.V * pipe.pb.W * pipe.pb.H
     alg_bytes = {
         "project": P * 60 + 0,
-        "bin_sort": (P * 8 + K * 12 + K * 8 + passes * K * 24 + K * 8 + pipe.pb.V * 3225 * 8) if onesweep else
+        "bin_sort": (P * 8 + K * 12 + passes * K * 24 + K * 8 + pipe.pb.V * 3225 * 8) if onesweep else
                     (pipe.pb.V * 3225 * 8 + vis * 32 + K * 12 + K * 116),
         "render_fwd_l1": npx * 48,
         "pose_grad": 0,
@@ -768,7 +768,7 @@ def main():
     fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s at max SM clock
     # DRAM bytes (read + write) of one launch from an ncu capture of this workload's current
     # kernel code (profiles/*_room500k.md); a stage without such a capture reports None
-    traffic = {"render_fwd_l1": 26_660_096, "render_bwd": 35_184_128}
+    traffic = {"render_fwd_l1": 26_724_352, "render_bwd": 35_204_864}
     if dom in ("render_fwd_l1", "render_bwd"):
         flops = stats["fwd_pairs"] * FLOP_FWD if dom == "render_fwd_l1" else stats["bwd_pairs"] * FLOP_BWD
         ach = flops / (stage_ms[dom] * 1e-3) / 1e12

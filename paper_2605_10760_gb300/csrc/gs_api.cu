@@ -98,9 +98,10 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     L->o_views = o; o = align256(o + sizeof(ViewEntry) * L->V);
     L->o_proj = o; o = align256(o + sizeof(float) * 12 * (size_t)std::max<long long>(P, 1));
     L->o_touched = o; o = align256(o + sizeof(uint32_t) * (size_t)std::max<long long>(P, 1) + 64);
-    L->o_scan_state = o; o = align256(o + sizeof(unsigned long long) * L->scan_parts);
     for (int k = 0; k < 2; ++k) { L->o_keys[k] = o; o = align256(o + sizeof(uint64_t) * (size_t)L->cap); }
     for (int k = 0; k < 2; ++k) { L->o_vals[k] = o; o = align256(o + sizeof(uint32_t) * (size_t)L->cap); }
+    // scan_state .. ranges are adjacent: the onesweep binning clears them with one memset
+    L->o_scan_state = o; o = align256(o + sizeof(unsigned long long) * L->scan_parts);
     L->o_hist = o; o = align256(o + sizeof(uint32_t) * kMaxPasses * 256);
     L->o_sort_state = o; o = align256(o + sizeof(uint32_t) * 256 * (size_t)L->sort_parts * L->passes);
     L->o_ranges = o; o = align256(o + sizeof(uint32_t) * 2 * (size_t)L->G);
@@ -318,6 +319,8 @@ static BinArgs make_bin_args(const Layout &L, void *ws) {
     a.sort_mode = L.sort_mode;
     a.tile_cnt = ws_ptr<uint32_t>(ws, L.o_tcnt);
     a.tile_list = ws_ptr<uint32_t>(ws, L.o_tlist);
+    a.clear_begin = ws_ptr<unsigned char>(ws, L.o_scan_state);
+    a.clear_bytes = L.o_ranges + sizeof(uint32_t) * 2 * (size_t)L.G - L.o_scan_state;
     return a;
 }
 

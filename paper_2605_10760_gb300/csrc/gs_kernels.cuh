@@ -54,14 +54,15 @@ struct BinArgs {
     float tw, th;
     long long P, cap, sort_parts, max_chunks, G;
     int fault_scan_part;               // -1 normally; >= 0: that scan partition never publishes
-    int zero_for_sort;                 // the scan kernel also clears hist, sort_state and ranges
+    void *clear_begin;                 // scan_state, hist, sort_state and ranges: one span cleared before
+    size_t clear_bytes;                //   the onesweep binning
     unsigned long long spin_limit;
     int sort_mode;                     // GS_SORT_TILE_BUCKET or GS_SORT_ONESWEEP
     uint32_t *tile_cnt;                // [G + 1] per-tile key counts -> slice starts (bucket mode)
     uint32_t *tile_list;               // [G] tiles whose slices are sorted by k_tile_sort_long
 };
 
-// onesweep: scan -> emit -> histogram -> onesweep passes -> ranges; tile bucket: scan of the
+// onesweep: scan with key emission and digit histograms -> onesweep passes -> ranges; tile bucket: scan of the
 // tile counts -> emission into tile slices -> per-tile sort.  Either way the sorted keys end in
 // keys[passes % 2], the values in vals[passes % 2], the records in list order in srec
 int run_bin_sort(const BinArgs &a, cudaStream_t s);

@@ -1,19 +1,20 @@
 // gs_sort.cu -- tile binning: key emission and a hand-written onesweep LSD radix sort.
 //
 // Pipeline (all stream-ordered, no host synchronisation, K read from device memory):
-//   1. k_scan      single-pass inclusive scan of tiles_touched with decoupled look-back;
-//                  the last partition writes K and flags K > capacity;
-//   2. k_emit      one key (global tile << 32 | float bits of depth) per touched tile, tiles in
-//                  row-major order, value = flattened (view, Gaussian) index; also clears that
-//                  pair's backward accumulator;
-//   3. k_hist      digit histograms of every 8-bit pass in one read of the keys (the scan kernel
-//                  cleared the histograms, look-back words and ranges beforehand);
-//   4. (each onesweep CTA turns its pass's histogram into digit start offsets itself);
-//   5. k_onesweep  one launch per pass: each CTA claims the next partition of 4096 keys, ranks them
+//   0. one memset clears the look-back words, the digit histograms and the tile ranges;
+//   1. k_scan_emit single-pass inclusive scan of tiles_touched with decoupled look-back; as soon
+//                  as a partition of pairs has its prefix, the CTA emits the partition's keys
+//                  (global tile << 32 | float bits of depth, one per touched tile, tiles in
+//                  row-major order, value = flattened (view, Gaussian) index), a thread per key,
+//                  and counts the digits of every 8-bit pass (a shared histogram per CTA, added
+//                  to the global one at the end); the last partition writes K and flags
+//                  K > capacity;
+//   2. (each onesweep CTA turns its pass's histogram into digit start offsets itself);
+//   3. k_onesweep  one launch per pass: each CTA claims the next partition of 4096 keys, ranks them
 //                  stably (warp match_any + per-warp digit counters), publishes its digit counts,
-//                  looks back over its predecessors' counts (bounded spins) and scatters through
-//                  shared memory so that each digit run is written contiguously;
-//   6. k_ranges    [start, end) of every global tile in the sorted keys, and every entry's record
+//                  places the partition in digit order in shared memory, looks back over its
+//                  predecessors' counts (bounded spins) and writes each digit run contiguously;
+//   4. k_ranges    [start, end) of every global tile in the sorted keys, and every entry's record
 //                  copied into list order (so a tile's list is one contiguous block for TMA).
 // Depth is positive (z > near > 0), so its float bit pattern orders like its value, and the sort is
 // stable, so equal keys keep the emission order (ascending flattened index).
@@ -42,22 +43,128 @@ constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kVal = (1u << 30) -
 // ------------------------------------------------------------------------------------------
 // 1. inclusive scan with decoupled look-back
 // ------------------------------------------------------------------------------------------
+template <int THREADS>
+struct ScanShared {
+    unsigned long long wsum[THREADS / 32];
+    unsigned long long prefix;
+};
+
+// Global exclusive prefix of this thread's first count in partition `part`, given tsum, the sum of
+// the thread's counts (threads in order).  Block scan of the per-thread sums; warp 0 publishes the
+// partition total, looks back over the predecessors (a warp reads 32 at a time, the nearest
+// inclusive word ends it; bounded spins) and publishes the inclusive prefix; the last partition
+// writes K and checks the capacity.  sh.prefix holds the partition's prefix on return.
+template <int THREADS>
+__device__ unsigned long long scan_partition(const BinArgs &a, ScanShared<THREADS> &sh, long long part,
+                                             long long nparts, unsigned long long tsum) {
+    static_assert(THREADS / 32 <= 32, "warp 0 scans the warp sums");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh.wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = lane < THREADS / 32 ? sh.wsum[lane] : 0ull;
+        unsigned long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < THREADS / 32) sh.wsum[lane] = wi - w;   // exclusive warp offsets
+        const unsigned long long total = __shfl_sync(0xffffffffu, wi, THREADS / 32 - 1);
+        const bool silent = (part == a.fault_scan_part);
+        unsigned long long prefix = 0;
+        if (part == 0) {
+            if (lane == 0 && !silent) st_relaxed_u64(a.scan_state, kFlagInc64 | total);
+        } else {
+            if (lane == 0 && !silent) st_relaxed_u64(a.scan_state + part, kFlagAgg64 | total);
+            // warp look-back: lane i reads predecessor j - i; the nearest inclusive word ends it
+            long long j = part - 1;
+            unsigned long long spins = 0;
+            bool timed_out = false;
+            for (;;) {
+                const long long jj = j - lane;
+                const unsigned long long w2 = jj >= 0 ? ld_relaxed_u64(a.scan_state + jj) : kFlagInc64;
+                const unsigned long long fl = w2 & ~kVal64;
+                const unsigned ready = __ballot_sync(0xffffffffu, fl != 0);
+                const unsigned inc = __ballot_sync(0xffffffffu, fl == kFlagInc64);
+                const int first = inc ? __ffs(inc) - 1 : 32;               // nearest inclusive lane
+                const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
+                if ((ready & need) == need) {
+                    unsigned long long v = (lane <= first) ? (w2 & kVal64) : 0ull;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    prefix += v;
+                    if (inc) break;
+                    j -= 32;
+                    continue;
+                }
+                if (++spins > a.spin_limit) { timed_out = true; break; }
+                __nanosleep(100);
+            }
+            if (lane == 0) {
+                if (timed_out) record_error(a.st, GS_ERR_TIMEOUT, 1);
+                if (!silent) st_relaxed_u64(a.scan_state + part, kFlagInc64 | ((prefix + total) & kVal64));
+            }
+        }
+        if (lane == 0) {
+            sh.prefix = prefix;
+            if (part == nparts - 1) {
+                const unsigned long long K = prefix + total;
+                a.st->num_keys = K;
+                if (K > (unsigned long long)a.cap) {
+                    a.st->required_keys = K;
+                    record_error(a.st, GS_ERR_CAPACITY, 2);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return sh.prefix + sh.wsum[warp] + (incl - tsum);
+}
+
+__device__ __forceinline__ uint32_t sat32(unsigned long long x) { return x > 0xffffffffull ? 0xffffffffu : (uint32_t)x; }
+
+// The IPT counts of this thread (consecutive pairs from base).
+template <int IPT>
+__device__ __forceinline__ void scan_load(const BinArgs &a, long long base, uint32_t (&x)[IPT]) {
+    if (base + IPT <= a.P) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.touched + base);
+#pragma unroll
+        for (int q = 0; q < IPT / 4; ++q) {
+            uint4 u = src[q];
+            x[4 * q] = u.x; x[4 * q + 1] = u.y; x[4 * q + 2] = u.z; x[4 * q + 3] = u.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) x[k] = (base + k < a.P) ? a.touched[base + k] : 0u;
+    }
+}
+
+// Inclusive sums y of this thread's counts back into tiles_touched.
+template <int IPT>
+__device__ __forceinline__ void scan_store(const BinArgs &a, long long base, const uint32_t (&y)[IPT]) {
+    if (base + IPT <= a.P) {
+        uint4 *dst = reinterpret_cast<uint4 *>(a.touched + base);
+#pragma unroll
+        for (int q = 0; q < IPT / 4; ++q) dst[q] = make_uint4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < IPT; ++k)
+            if (base + k < a.P) a.touched[base + k] = y[k];
+    }
+}
+
+// Scan alone: counts -> inclusive sums in place (tile-bucket binning and the bounded-wait test).
 __global__ void __launch_bounds__(kScanThreads) k_scan(BinArgs a) {
     __shared__ uint32_t s_part;
-    __shared__ unsigned long long s_wsum[kScanThreads / 32];
-    __shared__ unsigned long long s_prefix;
+    __shared__ ScanShared<kScanThreads> sh;
     const long long nparts = (a.P + kScanTile - 1) / kScanTile;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (a.zero_for_sort) {
-        // clear what the later binning kernels accumulate into (they run after this kernel)
-        const long long stride = (long long)gridDim.x * blockDim.x;
-        const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        for (long long i = t0; i < (long long)kMaxPasses * 256; i += stride) a.hist[i] = 0u;
-        const long long ns = 256LL * a.sort_parts * a.passes / 4;
-        uint4 *ss = reinterpret_cast<uint4 *>(a.sort_state);
-        for (long long i = t0; i < ns; i += stride) ss[i] = make_uint4(0u, 0u, 0u, 0u);
-        for (long long i = t0; i < 2 * a.G; i += stride) a.ranges[i] = 0u;
-    }
     for (;;) {
         if (threadIdx.x == 0) s_part = atomicAdd(&a.st->ctr[kCtrScan], 1u);
         __syncthreads();
@@ -65,183 +172,151 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(BinArgs a) {
         if (part >= nparts) break;
         const long long base = part * kScanTile + (long long)threadIdx.x * kScanIPT;
         uint32_t x[kScanIPT];
-        if (base + kScanIPT <= a.P) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(a.touched + base);
-#pragma unroll
-            for (int q = 0; q < kScanIPT / 4; ++q) {
-                uint4 u = src[q];
-                x[4 * q] = u.x; x[4 * q + 1] = u.y; x[4 * q + 2] = u.z; x[4 * q + 3] = u.w;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < kScanIPT; ++k) x[k] = (base + k < a.P) ? a.touched[base + k] : 0u;
-        }
+        scan_load<kScanIPT>(a, base, x);
         unsigned long long tsum = 0;
 #pragma unroll
         for (int k = 0; k < kScanIPT; ++k) tsum += x[k];
-        // block exclusive scan of the per-thread sums
-        unsigned long long incl = tsum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) s_wsum[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            unsigned long long w = lane < kScanThreads / 32 ? s_wsum[lane] : 0ull;
-            unsigned long long wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long y = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += y;
-            }
-            if (lane < kScanThreads / 32) s_wsum[lane] = wi - w;   // exclusive warp offsets
-            const unsigned long long total = __shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
-            const bool silent = (part == a.fault_scan_part);
-            unsigned long long prefix = 0;
-            if (part == 0) {
-                if (lane == 0 && !silent) st_relaxed_u64(a.scan_state, kFlagInc64 | total);
-            } else {
-                if (lane == 0 && !silent) st_relaxed_u64(a.scan_state + part, kFlagAgg64 | total);
-                // warp look-back: lane i reads predecessor j - i; the nearest inclusive word ends it
-                long long j = part - 1;
-                unsigned long long spins = 0;
-                bool timed_out = false;
-                for (;;) {
-                    const long long jj = j - lane;
-                    const unsigned long long w2 = jj >= 0 ? ld_relaxed_u64(a.scan_state + jj) : kFlagInc64;
-                    const unsigned long long fl = w2 & ~kVal64;
-                    const unsigned ready = __ballot_sync(0xffffffffu, fl != 0);
-                    const unsigned inc = __ballot_sync(0xffffffffu, fl == kFlagInc64);
-                    const int first = inc ? __ffs(inc) - 1 : 32;               // nearest inclusive lane
-                    const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
-                    if ((ready & need) == need) {
-                        unsigned long long v = (lane <= first) ? (w2 & kVal64) : 0ull;
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                        prefix += v;
-                        if (inc) break;
-                        j -= 32;
-                        continue;
-                    }
-                    if (++spins > a.spin_limit) { timed_out = true; break; }
-                    __nanosleep(100);
-                }
-                if (lane == 0) {
-                    if (timed_out) record_error(a.st, GS_ERR_TIMEOUT, 1);
-                    if (!silent) st_relaxed_u64(a.scan_state + part, kFlagInc64 | ((prefix + total) & kVal64));
-                }
-            }
-            if (lane == 0) {
-                s_prefix = prefix;
-                if (part == nparts - 1) {
-                    const unsigned long long K = prefix + total;
-                    a.st->num_keys = K;
-                    if (K > (unsigned long long)a.cap) {
-                        a.st->required_keys = K;
-                        record_error(a.st, GS_ERR_CAPACITY, 2);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        unsigned long long run = s_prefix + s_wsum[warp] + (incl - tsum);
+        unsigned long long run = scan_partition<kScanThreads>(a, sh, part, nparts, tsum);
         uint32_t y[kScanIPT];
 #pragma unroll
         for (int k = 0; k < kScanIPT; ++k) {
             run += x[k];
-            y[k] = run > 0xffffffffull ? 0xffffffffu : (uint32_t)run;
+            y[k] = sat32(run);
         }
-        if (base + kScanIPT <= a.P) {
-            uint4 *dst = reinterpret_cast<uint4 *>(a.touched + base);
-#pragma unroll
-            for (int q = 0; q < kScanIPT / 4; ++q) dst[q] = make_uint4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < kScanIPT; ++k)
-                if (base + k < a.P) a.touched[base + k] = y[k];
-        }
+        scan_store<kScanIPT>(a, base, y);
         __syncthreads();
     }
 }
 
-// ------------------------------------------------------------------------------------------
-// 2. key emission
-// ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kChunk) k_emit(BinArgs a) {
-    const int v = blockIdx.y;
-    __shared__ ViewEntry s_ve;
-    if (threadIdx.x == 0) s_ve = a.views[v];
-    __syncthreads();
-    const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
-    if (i >= s_ve.count) return;
-    const long long f = s_ve.pair_off + i;
-    const uint32_t end = a.touched[f];
-    const uint32_t start = f > 0 ? a.touched[f - 1] : 0u;
-    if (end == start) return;
-    const float4 r0 = a.proj[3 * f], r1 = a.proj[3 * f + 1];
-    int x0, x1, y0, y1;
-    spec_rect(r0.x, r0.y, r1.w, a.tw, a.th, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
-    const unsigned long long zbits = __float_as_uint(r1.z);
-    const unsigned long long gbase = (unsigned long long)v * a.Tx * a.Ty;
-    unsigned long long k = start;
-    uint64_t *keys = a.keys[0];
-    uint32_t *vals = a.vals[0];
-    for (int ty = y0; ty < y1; ++ty)
-        for (int tx = x0; tx < x1; ++tx) {
-            if (k < (unsigned long long)a.cap) {
-                keys[k] = ((gbase + (unsigned long long)(ty * a.Tx + tx)) << 32) | zbits;
-                vals[k] = (uint32_t)f;
-            }
-            ++k;
-        }
-    if (k != end) record_error(a.st, GS_ERR_DEVICE_FAULT, 3);
-    float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    a.g2d[3 * f] = z4;
-    a.g2d[3 * f + 1] = z4;
-    a.g2d[3 * f + 2] = z4;
+// View of flattened pair f: the last view whose pair offset is <= f (views with no Gaussians share
+// their successor's offset, so the last such view is the non-empty one holding f).
+__device__ __forceinline__ int view_of_pair(const ViewEntry *views, int V, long long f) {
+    int lo = 0, hi = V - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].pair_off <= f) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
-// ------------------------------------------------------------------------------------------
-// 3./4. digit histograms
-// ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_hist(BinArgs a) {
-    __shared__ uint32_t sh[kMaxPasses][256];
-    for (int i = threadIdx.x; i < kMaxPasses * 256; i += 256) (&sh[0][0])[i] = 0;
-    __syncthreads();
-    const unsigned long long K = min(a.st->num_keys, (unsigned long long)a.cap);
-    const uint64_t *keys = a.keys[0];
+// Shared memory of k_scan_emit: per pair of the partition its inclusive key end, the global tile
+// of its rectangle's top-left corner, the rectangle's width and the depth bits.
+struct EmitSmem {
+    uint32_t inc[kScanTile];
+    uint32_t g0[kScanTile];
+    uint32_t wr[kScanTile];
+    uint32_t z[kScanTile];
+};
+constexpr size_t kEmitDynSmem = sizeof(EmitSmem);
+
+// Scan of tiles_touched with the key emission and the digit histograms of every pass.  Per
+// partition of kScanTile pairs: (1) the scan; (2) a thread per pair (kEmitThreads apart, so the
+// record reads coalesce) puts the pair's rectangle and depth bits in shared memory and clears its
+// backward accumulator; (3) a thread per key: consecutive threads write consecutive keys, each
+// finding its pair by binary search over the inclusive ends, and the digits of every pass are
+// counted per warp (match_any) into the CTA's histogram.  Every loop bound is the same for the
+// whole CTA.
+constexpr int kEmitThreads = 1024;                 // a partition of kScanTile pairs per CTA,
+constexpr int kEmitIPT = kScanTile / kEmitThreads;  // kEmitIPT consecutive counts per thread in the scan
+__global__ void __launch_bounds__(kEmitThreads) k_scan_emit(BinArgs a) {
+    static_assert(kEmitIPT % 4 == 0, "counts load as uint4");
+    extern __shared__ __align__(16) unsigned char em_smem[];
+    EmitSmem &es = *reinterpret_cast<EmitSmem *>(em_smem);
+    __shared__ uint32_t s_part;
+    __shared__ ScanShared<kEmitThreads> sh;
+    __shared__ uint32_t s_hist[kMaxPasses][256];
+    for (int i = threadIdx.x; i < kMaxPasses * 256; i += kEmitThreads) (&s_hist[0][0])[i] = 0u;
+    const long long nparts = (a.P + kScanTile - 1) / kScanTile;
+    const unsigned long long cap = (unsigned long long)a.cap;
     const int lane = threadIdx.x & 31;
-    // kHistBatch keys per thread are loaded before any is counted, so their loads overlap
-    constexpr int kHistBatch = 4;
-    const unsigned long long step = (unsigned long long)gridDim.x * 256;
-    for (unsigned long long i0 = (unsigned long long)blockIdx.x * 256; i0 < K; i0 += step * kHistBatch) {
-        uint64_t key[kHistBatch];
-        bool valid[kHistBatch];
+    for (;;) {
+        if (threadIdx.x == 0) s_part = atomicAdd(&a.st->ctr[kCtrScan], 1u);
+        __syncthreads();
+        const long long part = s_part;
+        if (part >= nparts) break;
+        const long long pbase = part * kScanTile;
+        const long long base = pbase + (long long)threadIdx.x * kEmitIPT;
+        // (1) scan
+        {
+            uint32_t x[kEmitIPT];
+            scan_load<kEmitIPT>(a, base, x);
+            unsigned long long tsum = 0;
 #pragma unroll
-        for (int b = 0; b < kHistBatch; ++b) {
-            const unsigned long long i = i0 + b * step + threadIdx.x;
-            valid[b] = i < K;
-            key[b] = valid[b] ? keys[i] : 0ull;
-        }
+            for (int k = 0; k < kEmitIPT; ++k) tsum += x[k];
+            unsigned long long run = scan_partition<kEmitThreads>(a, sh, part, nparts, tsum);
+            uint32_t y[kEmitIPT];
 #pragma unroll
-        for (int b = 0; b < kHistBatch; ++b)
-            for (int p = 0; p < a.passes; ++p) {
-                const uint32_t d = valid[b] ? (uint32_t)((key[b] >> (8 * p)) & 255u) : 256u;
-                const unsigned peers = __match_any_sync(0xffffffffu, d);
-                if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&sh[p][d], (uint32_t)__popc(peers));
+            for (int k = 0; k < kEmitIPT; ++k) {
+                run += x[k];
+                y[k] = sat32(run);
+                es.inc[threadIdx.x * kEmitIPT + k] = y[k];
             }
+            scan_store<kEmitIPT>(a, base, y);
+        }
+        const uint32_t pstart = sat32(sh.prefix);
+        const int np = (int)min((long long)kScanTile, a.P - pbase);   // pairs in this partition
+        __syncthreads();
+        const uint32_t pend = es.inc[np - 1];
+        // (2) per pair: rectangle and depth bits
+#pragma unroll
+        for (int j = 0; j < kEmitIPT; ++j) {
+            const int li = j * kEmitThreads + threadIdx.x;
+            if (li >= np) break;
+            const uint32_t b1 = es.inc[li], b0 = li ? es.inc[li - 1] : pstart;
+            if (b1 == b0) continue;
+            const long long f = pbase + li;
+            const float4 r0 = a.proj[3 * f], r1 = a.proj[3 * f + 1];
+            int x0, x1, y0, y1;
+            spec_rect(r0.x, r0.y, r1.w, a.tw, a.th, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
+            const int v = view_of_pair(a.views, a.V, f);
+            if ((uint32_t)((x1 - x0) * (y1 - y0)) != b1 - b0 || x1 <= x0) record_error(a.st, GS_ERR_DEVICE_FAULT, 3);
+            es.g0[li] = (uint32_t)((unsigned long long)v * a.Tx * a.Ty + (unsigned long long)(y0 * a.Tx + x0));
+            es.wr[li] = (uint32_t)max(x1 - x0, 1);
+            es.z[li] = __float_as_uint(r1.z);
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            a.g2d[3 * f] = z4;
+            a.g2d[3 * f + 1] = z4;
+            a.g2d[3 * f + 2] = z4;
+        }
+        __syncthreads();
+        // (3) per key
+        for (uint32_t k0 = pstart; k0 < pend; k0 += kEmitThreads) {
+            const uint32_t kk = k0 + threadIdx.x;
+            const bool valid = kk < pend && (unsigned long long)kk < cap;
+            unsigned long long key = 0;
+            if (valid) {
+                // the pair: smallest li with inc[li] > kk (pairs without keys repeat their end)
+                int lo = 0, hi = np - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (es.inc[mid] > kk) hi = mid;
+                    else lo = mid + 1;
+                }
+                const uint32_t m = kk - (lo ? es.inc[lo - 1] : pstart);
+                const uint32_t w = es.wr[lo];
+                const uint32_t row = m / w;
+                const unsigned long long g = (unsigned long long)es.g0[lo] + (unsigned long long)row * a.Tx + (m - row * w);
+                key = (g << 32) | es.z[lo];
+                a.keys[0][kk] = key;
+                a.vals[0][kk] = (uint32_t)(pbase + lo);
+            }
+            for (int p = 0; p < a.passes; ++p) {
+                const uint32_t dg = valid ? (uint32_t)((key >> (8 * p)) & 255u) : 256u;
+                const unsigned peers = __match_any_sync(0xffffffffu, dg);
+                if (dg < 256u && lane == __ffs(peers) - 1) atomicAdd(&s_hist[p][dg], (uint32_t)__popc(peers));
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < a.passes * 256; i += 256) {
-        uint32_t c = (&sh[0][0])[i];
+    for (int i = threadIdx.x; i < a.passes * 256; i += kEmitThreads) {
+        const uint32_t c = (&s_hist[0][0])[i];
         if (c) atomicAdd(a.hist + i, c);
     }
 }
 
 // ------------------------------------------------------------------------------------------
-// 5. onesweep pass
+// 3. onesweep pass
 // ------------------------------------------------------------------------------------------
 struct SweepArgs {
     const uint64_t *kin;
@@ -441,7 +516,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------
-// 6. tile ranges
+// 4. tile ranges
 // ------------------------------------------------------------------------------------------
 __global__ void k_ranges(const uint64_t *keys, const uint32_t *vals, const float4 *proj, float4 *srec, DevStatus *st,
                          long long cap, long long G, long long P, uint32_t *ranges) {
@@ -717,7 +792,6 @@ static int run_bucket(const BinArgs &a, cudaStream_t s) {
     BinArgs sa = a;
     sa.touched = a.tile_cnt;
     sa.P = a.G;
-    sa.zero_for_sort = 0;
     int rc = run_scan(sa, s, true);   // run_bin_sort cleared the scan counter
     if (rc) return rc;
     if (a.P > 0) {
@@ -798,23 +872,21 @@ int run_bin_sort(const BinArgs &a, cudaStream_t s) {
     if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t) * (kCtrTileLong + 1), s) != cudaSuccess)
         return GS_ERR_CUDA;
     if (a.sort_mode == GS_SORT_TILE_BUCKET) return run_bucket(a, s);
-    BinArgs sa = a;
-    sa.zero_for_sort = 1;                 // the scan also clears hist, look-back state and ranges
-    if (a.P == 0) {
-        if (cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * kMaxPasses * 256, s) != cudaSuccess) return GS_ERR_CUDA;
-        if (cudaMemsetAsync(a.ranges, 0, sizeof(uint32_t) * 2 * (size_t)a.G, s) != cudaSuccess) return GS_ERR_CUDA;
-    }
-    int rc = run_scan(sa, s, true);   // run_bin_sort cleared the scan counter
-    if (rc) return rc;
-    if (a.P > 0) {
-        dim3 grid((unsigned)a.max_chunks, (unsigned)a.V);
-        k_emit<<<grid, kChunk, 0, s>>>(a);
-        count_launches(1);
-    }
+    // look-back words of the scan and of every pass, digit histograms and tile ranges
+    if (cudaMemsetAsync(a.clear_begin, 0, a.clear_bytes, s) != cudaSuccess) return GS_ERR_CUDA;
     const int sms = device_sm_count();
-    const int hist_grid = (int)std::min<long long>(sms * 4, std::max<long long>(sms, (a.cap + 2047) / 2048));
-    k_hist<<<hist_grid, 256, 0, s>>>(a);
-    count_launches(1);
+    const long long parts = (a.P + kScanTile - 1) / kScanTile;
+    if (parts > 0) {
+        static bool attr = cudaFuncSetAttribute((const void *)k_scan_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)kEmitDynSmem) == cudaSuccess;
+        if (!attr) return GS_ERR_CUDA;
+        static int occ = occupancy((const void *)k_scan_emit, kEmitThreads, kEmitDynSmem);
+        const long long grid = std::min<long long>(parts, (long long)sms * occ);
+        k_scan_emit<<<(unsigned)grid, kEmitThreads, kEmitDynSmem, s>>>(a);
+        count_launches(1);
+    } else if (cudaMemsetAsync(&a.st->num_keys, 0, sizeof(unsigned long long), s) != cudaSuccess) {
+        return GS_ERR_CUDA;   // no pairs: K = 0
+    }
     const int rc2 = sweep_passes<kSortIPT>(a, s);
     if (rc2) return rc2;
     k_ranges<<<sms * 8, 256, 0, s>>>(a.keys[a.passes & 1], a.vals[a.passes & 1], a.proj, a.srec, a.st, a.cap, a.G,
