@@ -70,7 +70,8 @@ typedef struct gs_camera {
 /* Binning algorithms of gs_bin_sort.  Both produce the same lists bit for bit: every tile's
  * entries ordered by (depth bits, flattened pair index).
  *   GS_SORT_ONESWEEP (default): scan of tiles_touched, keys (tile << 32 | depth bits) in emission
- *     order and a stable LSD onesweep radix sort over all keys (8-bit digits, decoupled look-back).
+ *     order and the digit histograms of every pass (one kernel), then a stable LSD onesweep radix
+ *     sort over all keys (8-bit digits, decoupled look-back).
  *   GS_SORT_TILE_BUCKET: gs_project counts the keys of every tile, a scan of the G counts gives
  *     each tile its slice, emission drops each key into its tile's slice by atomic slot taking
  *     (order inside the slice arbitrary), and each tile's slice is sorted by (depth bits, pair
