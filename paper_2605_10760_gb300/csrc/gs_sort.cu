@@ -280,10 +280,12 @@ __global__ void __launch_bounds__(kEmitThreads) k_scan_emit(BinArgs a) {
             a.g2d[3 * f + 2] = z4;
         }
         __syncthreads();
-        // (3) per key
-        for (uint32_t k0 = pstart; k0 < pend; k0 += kEmitThreads) {
+        // (3) per key, up to the capacity (< 2^30, so the counter cannot wrap even when the sums
+        // saturated); keys at or beyond it are neither written nor counted
+        const uint32_t kend = (uint32_t)min((unsigned long long)pend, cap);
+        for (uint32_t k0 = pstart; k0 < kend; k0 += kEmitThreads) {
             const uint32_t kk = k0 + threadIdx.x;
-            const bool valid = kk < pend && (unsigned long long)kk < cap;
+            const bool valid = kk < kend;
             unsigned long long key = 0;
             if (valid) {
                 // the pair: smallest li with inc[li] > kk (pairs without keys repeat their end)
