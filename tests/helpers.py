@@ -17,7 +17,6 @@ def rel_l2(a, b):
 
 
 def gpu_problem(wl: S.Workload, views=None, params=None, key_capacity=None, device="cuda"):
-    import torch
     from paper_2605_10760_gb300 import raster as R
     views = list(range(len(wl.cameras))) if views is None else list(views)
     sov = wl.scene_of_view[views]
