@@ -9,6 +9,9 @@ TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU baseline).
   averaged over views, channels and pixels.  The paper gives only the weight lambda = 0.2.
 * Adam with bias correction, as the per-agent optimiser (Sec. III-A, "optimized ... by gradient
   descent"; Sec. III-C, refinement "at half the per-agent learning rate").
+* The normal term of the mapping loss (Eq. 4: lambda_n L_normal, lambda_n = 1e-2): a cosine
+  loss |1 - N_hat . N_bar| between the normal induced by the rendered depth and a given normal
+  prior (the prior is an input; its monocular network is not part of this path).
 """
 from __future__ import annotations
 
@@ -165,3 +168,71 @@ def iso_loss(log_scales, weight=10.0):
     # d|s_a - sbar| / d s_b = sg_a (delta_ab - 1/3); chain through s_b = exp(l_b)
     g_s = sg - sg.sum(axis=1, keepdims=True) / 3.0
     return weight * np.abs(d).sum(), weight * g_s * s
+
+
+def pixel_rays(W, H, fx, fy, cx, cy):
+    """Ray of every pixel in the camera frame, r = ((x + 0.5 - cx) / fx, (y + 0.5 - cy) / fy, 1)
+    (pixel centres at +0.5, camera x right, y down, z forward): [3, H, W]."""
+    X, Y = np.meshgrid((np.arange(W) + 0.5 - cx) / fx, (np.arange(H) + 0.5 - cy) / fy)
+    return np.stack([X, Y, np.ones_like(X)])
+
+
+def depth_normals(depth, fx, fy, cx, cy):
+    """Normal induced by one view's depth map (the N_hat of Eq. 4's normal term).  The pixel's
+    point is P = D r; t_x = P(x+1, y) - P(x-1, y), t_y = P(x, y+1) - P(x, y-1) (central
+    differences); u = t_y x t_x and N_hat = u / |u|, which faces the camera for a surface seen from
+    the front (-z for a fronto-parallel plane).  A pixel is valid when it is not on the image
+    border, its depth and its four neighbours' depths are positive and finite, and |u| > 0.
+    Returns (N_hat [3,H,W] (zero where invalid), valid [H,W], t_x, t_y, |u|)."""
+    D = np.asarray(depth, np.float64)
+    H, W = D.shape
+    P = D[None] * pixel_rays(W, H, fx, fy, cx, cy)
+    ok = (D > 0) & np.isfinite(D)
+    valid = np.zeros((H, W), bool)
+    valid[1:-1, 1:-1] = ok[1:-1, 1:-1] & ok[1:-1, 2:] & ok[1:-1, :-2] & ok[2:, 1:-1] & ok[:-2, 1:-1]
+    tx, ty = np.zeros((3, H, W)), np.zeros((3, H, W))
+    tx[:, 1:-1, 1:-1] = P[:, 1:-1, 2:] - P[:, 1:-1, :-2]
+    ty[:, 1:-1, 1:-1] = P[:, 2:, 1:-1] - P[:, :-2, 1:-1]
+    tx[:, ~valid] = 0.0
+    ty[:, ~valid] = 0.0
+    u = np.cross(ty, tx, axis=0)
+    nu = np.sqrt((u * u).sum(0))
+    valid &= nu > 0
+    safe = np.where(valid, nu, 1.0)
+    n = np.where(valid[None], u / safe[None], 0.0)
+    return n, valid, tx, ty, safe
+
+
+def normal_loss(depth, prior, intr, weight=1e-2):
+    """Normal term of the mapping loss (Eq. 4, lambda_n L_normal with lambda_n = 1e-2):
+    L_normal = |1 - N_hat . N_bar| per valid pixel (depth_normals), averaged over all V*H*W pixels
+    (invalid ones add 0), with N_bar the given normal prior [V,3,H,W] in the camera frame and
+    intr [V,4] = (fx, fy, cx, cy).  sign(0) = 0.  Returns (weight * L_normal, d/d depth [V,H,W]).
+
+    Adjoint: g_n = dL/dN_hat = -scale sign(c) N_bar (c = 1 - N_hat . N_bar, scale = weight / VHW);
+    g_u = (g_n - N_hat (N_hat . g_n)) / |u|; for u = t_y x t_x, dL/dt_y = t_x x g_u and
+    dL/dt_x = g_u x t_y; P(q) enters t_x at q -+ 1 and t_y at q -+ W, so
+    dL/dP(q) = G_x(q-x) - G_x(q+x) + G_y(q-y) - G_y(q+y) and dL/dD(q) = r(q) . dL/dP(q)."""
+    depth = np.asarray(depth, np.float64)
+    prior = np.asarray(prior, np.float64)
+    V, H, W = depth.shape
+    scale = weight / (V * H * W)
+    total = 0.0
+    grad = np.zeros_like(depth)
+    for v in range(V):
+        fx, fy, cx, cy = (float(t) for t in intr[v])
+        n, valid, tx, ty, nu = depth_normals(depth[v], fx, fy, cx, cy)
+        c = 1.0 - (n * prior[v]).sum(0)
+        total += scale * np.abs(c)[valid].sum()
+        sg = np.where(valid, np.sign(c), 0.0)
+        g_n = -scale * sg[None] * prior[v]
+        g_u = (g_n - n * (n * g_n).sum(0)[None]) / nu[None]
+        gx = np.cross(g_u, ty, axis=0) * valid[None]
+        gy = np.cross(tx, g_u, axis=0) * valid[None]
+        dP = np.zeros((3, H, W))
+        dP[:, :, 1:] += gx[:, :, :-1]
+        dP[:, :, :-1] -= gx[:, :, 1:]
+        dP[:, 1:, :] += gy[:, :-1, :]
+        dP[:, :-1, :] -= gy[:, 1:, :]
+        grad[v] = (pixel_rays(W, H, fx, fy, cx, cy) * dP).sum(0)
+    return total, grad
