@@ -482,6 +482,51 @@ FLOP_PHO = 410
 BYTES_PHO = 28
 
 
+def normal_bench(R, S, torch, reps=20):
+    """Normal term of Eq. 4 over 8 views at 1200x680: a smooth synthetic depth surface per view and a
+    random camera-facing unit prior; inputs, scratch and gradient (~290 MB) exceed L2, so nothing is
+    flushed between calls."""
+    V, H, W = 8, 680, 1200
+    rng = np.random.default_rng(31)
+    y, x = np.mgrid[0:H, 0:W].astype(np.float32)
+    depth = np.stack([2.5 + 1.2 * x / W - 0.8 * y / H + 0.4 * np.sin(9.0 * x / W + v) * np.cos(7.0 * y / H)
+                      for v in range(V)]).astype(np.float32)
+    prior = rng.normal(size=(V, 3, H, W)).astype(np.float32)
+    prior[:, 2] = -np.abs(prior[:, 2]) - 0.5
+    prior /= np.linalg.norm(prior, axis=1, keepdims=True)
+    cams = np.zeros((V, 16), np.float32)
+    cams[:, 0] = cams[:, 4] = cams[:, 8] = 1.0
+    cams[:, 12:16] = (600.0, 600.0, 600.0, 340.0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d, p, c = t(depth), t(prior), t(cams)
+    d_depth = torch.zeros_like(d)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    scratch = R.normal_scratch(V, H, W)
+    for _ in range(3):
+        R.loss_normal(d, p, c, 1e-2, d_depth, loss, scratch)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = R.L.load().gs_launch_count()
+    ev0.record(st)
+    for _ in range(reps):
+        R.loss_normal(d, p, c, 1e-2, d_depth, loss, scratch)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    px = V * H * W
+    # depth 4 B + prior 12 B read, adjoints 24 B written and read back, d_depth 4 B read + 4 B written
+    ach = 72.0 * px / (ms * 1e-3) / 1e9
+    peaks = _peaks()
+    return {"workload": "8 views 1200x680, smooth synthetic depth, random camera-facing prior, lambda_n 1e-2",
+            "ms_per_call": ms, "pixels_per_s": px / (ms * 1e-3),
+            "launches_per_call": (R.L.load().gs_launch_count() - n0) // reps,
+            "loss_per_call": loss.item() / (reps + 3),
+            "roofline": {"kernel": "k_normal_terms + k_normal_gather", "bound": "hbm", "achieved": ach,
+                         "unit": "GB/s", "peak": peaks["hbm_gbs"], "frac": ach / peaks["hbm_gbs"],
+                         "bytes_per_pixel": 72}}
+
+
 def pho_bench(R, S, torch, reps=20):
     """Eq. 12 photometric blocks of 16 pose-graph edges: 8 rooms of agents8x4 (50k..400k
     Gaussians), in each an anchor keyframe and a second one moved 8 cm / 2 deg, rendered at
@@ -694,7 +739,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the graph-loop and 4M/64-view measurements")
-    ap.add_argument("--only", choices=["photometric", "fusion", "mapping", "refine", "fused", "batched"],
+    ap.add_argument("--only", choices=["photometric", "normal", "fusion", "mapping", "refine", "fused", "batched"],
                     help="run one secondary measurement alone and print its JSON (not the headline line)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -705,7 +750,8 @@ def main():
         from paper_2605_10760_gb300 import scenes as S
         R.L.load()
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        fn = {"photometric": pho_bench, "fusion": fusion_bench, "mapping": mapping_graph, "refine": refine_graph,
+        fn = {"photometric": pho_bench, "normal": normal_bench, "fusion": fusion_bench, "mapping": mapping_graph,
+              "refine": refine_graph,
               "fused": fused_map, "batched": lambda R, S, torch: batched_speedup(R, S, torch, flush)}[args.only]
         print(json.dumps({"section": args.only, "result": fn(R, S, torch)}))
         return 0
@@ -785,6 +831,12 @@ def main():
     fusion = None if args.no_extra else fusion_bench(R, S, torch)
     pho = None if args.no_extra else pho_bench(R, S, torch)
     fused = None if args.no_extra else fused_map(R, S, torch)
+    normal = None
+    if not args.no_extra:      # the last device work of the run; an error is reported in the line
+        try:
+            normal = normal_bench(R, S, torch)
+        except Exception as e:  # noqa: BLE001
+            normal = {"error": repr(e)[:300]}
     cpu = None if args.no_cpu else cpu_baseline()
     line = {
         "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
@@ -809,6 +861,7 @@ def main():
         "refine_graph": refine,
         "fusion": fusion,
         "photometric": pho,
+        "normal_loss": normal,
         "fused_map": fused,
         "cpu_baseline": cpu,
         "clocks": clocks,

@@ -246,6 +246,23 @@ int gs_loss_l1(int32_t views, int32_t width, int32_t height, const float *rgb, c
                const float *depth, const float *depth_t, float w_rgb, float w_depth,
                float *d_rgb, float *d_depth, double *loss, void *stream);
 
+/* Normal term of the mapping loss (Eq. 4: lambda_n L_normal, lambda_n = 1e-2 in the paper), the
+ * cosine loss between the depth-induced normal N_hat and a given normal prior N_bar:
+ * L = weight * (1 / (V H W)) * sum over valid pixels of |1 - N_hat . N_bar|.  P = D r with
+ * r = ((x + 0.5 - cx) / fx, (y + 0.5 - cy) / fy, 1); t_x = P(x+1, y) - P(x-1, y),
+ * t_y = P(x, y+1) - P(x, y-1); N_hat = (t_y x t_x) / |t_y x t_x| (facing the camera for a surface
+ * seen from the front).  Valid: not on the image border, depth positive and finite at the pixel
+ * and its four neighbours, |t_y x t_x| > 0.  sign(0) = 0.
+ *   depth [V,H,W] (the rendered depth), prior [V,3,H,W] unit normals in each view's camera frame,
+ *   cams [V] device cameras (only the intrinsics are read).  ADDS L to *loss (device double) and
+ *   dL/d depth to d_depth [V,H,W] (so it follows gs_loss_l1 / gs_render_fwd_l1, which write
+ *   them).  scratch: device buffer of gs_normal_scratch_size() bytes (24 B per pixel),
+ *   256-byte aligned.  Two kernels, no synchronisation. */
+size_t gs_normal_scratch_size(int32_t views, int32_t width, int32_t height);
+int gs_loss_normal(int32_t views, int32_t width, int32_t height, const float *depth, const float *prior,
+                   const gs_camera *cams, float weight, float *d_depth, double *loss, void *scratch,
+                   void *stream);
+
 /* L = w_l1 mean|rgb - rgb_t| + w_ssim (1 - SSIM(rgb, rgb_t)) (Eq. 23's photometric and
  * structural terms): 11x11 Gaussian window, sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2,
  * mean over views, channels, pixels.  Writes d_rgb and writes L to *loss (overwritten).

@@ -442,6 +442,31 @@ int gs_loss_l1(int32_t views, int32_t width, int32_t height, const float *rgb, c
                           (cudaStream_t)stream);
 }
 
+size_t gs_normal_scratch_size(int32_t views, int32_t width, int32_t height) {
+    if (views < 1 || width < 1 || height < 1) return 0;
+    return normal_scratch_bytes(views, width, height);
+}
+
+int gs_loss_normal(int32_t views, int32_t width, int32_t height, const float *depth, const float *prior,
+                   const gs_camera *cams, float weight, float *d_depth, double *loss, void *scratch, void *stream) {
+    GS_RANGE("gs_loss_normal");
+    if (views < 1 || views > GS_MAX_VIEWS || width < 1 || height < 1 || width > 16384 || height > 16384 || !depth ||
+        !prior || !cams || !d_depth || !loss || !ws_ok(scratch) || !(weight == weight))
+        return GS_ERR_INVALID_ARG;
+    NormalArgs a;
+    a.depth = depth;
+    a.prior = prior;
+    a.cams = cams;
+    a.scratch = static_cast<float *>(scratch);
+    a.d_depth = d_depth;
+    a.loss = loss;
+    a.V = views;
+    a.W = width;
+    a.H = height;
+    a.scale = (float)((double)weight / ((double)views * width * height));
+    return launch_loss_normal(a, (cudaStream_t)stream);
+}
+
 size_t gs_ssim_scratch_size(int32_t views, int32_t width, int32_t height) {
     if (views < 1 || width < 1 || height < 1) return 0;
     return ssim_scratch_bytes(views, width, height);

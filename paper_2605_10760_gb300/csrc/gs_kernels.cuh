@@ -133,6 +133,20 @@ int launch_grads_zero(long long n, const gs_grads &g, cudaStream_t s);
 int launch_adam(long long n, const gs_adam_state &st, const gs_grads &g, const float lr[5], int zero_grads,
                 cudaStream_t s, float iso_weight = 0.f, double *iso_loss = nullptr);
 
+// normal term of the mapping loss, Eq. 4 (gs_normal.cu)
+struct NormalArgs {
+    const float *depth;                // [V,H,W]
+    const float *prior;                // [V,3,H,W] unit normals, camera frame
+    const gs_camera *cams;             // [V] (intrinsics read)
+    float *scratch;                    // [V,6,H,W] dL/dt_x, dL/dt_y per pixel
+    float *d_depth;                    // [V,H,W], +=
+    double *loss;                      // +=
+    int V, W, H;
+    float scale;                       // weight / (V H W)
+};
+size_t normal_scratch_bytes(int V, int W, int H);
+int launch_loss_normal(const NormalArgs &a, cudaStream_t s);
+
 // Eq. 12 photometric residual blocks (gs_photometric.cu)
 constexpr int kPhoMaxBlocksPerEdge = 1024;
 struct PhoArgs {

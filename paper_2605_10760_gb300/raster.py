@@ -252,6 +252,27 @@ def loss_l1(rgb, rgb_t, depth=None, depth_t=None, w_rgb=1.0, w_depth=0.0, d_rgb=
     return loss, d_rgb, d_depth
 
 
+def normal_scratch(V, H, W, device="cuda") -> torch.Tensor:
+    n = L.load().gs_normal_scratch_size(V, W, H)
+    return torch.empty(int(n), dtype=torch.uint8, device=device)
+
+
+def loss_normal(depth, prior, cams, weight=1e-2, d_depth=None, loss=None, scratch=None):
+    """Normal term of the mapping loss (Eq. 4, lambda_n = 1e-2): weight * mean over all pixels of
+    |1 - N_hat . N_bar| for the depth-induced normal N_hat and the prior N_bar [V,3,H,W].  ADDS the
+    loss to `loss` and dL/d depth to `d_depth` (zero tensors are created when None); returns both."""
+    V, H, W = depth.shape
+    if d_depth is None:
+        d_depth = torch.zeros_like(depth)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float64, device=depth.device)
+    if scratch is None:
+        scratch = normal_scratch(V, H, W, depth.device)
+    L.check(L.load().gs_loss_normal(V, W, H, _ptr(depth), _ptr(prior), _ptr(cams), float(weight), _ptr(d_depth),
+                                    _ptr(loss), _ptr(scratch), _stream()), "gs_loss_normal")
+    return loss, d_depth
+
+
 def ssim_scratch(V, H, W, device="cuda") -> torch.Tensor:
     n = L.load().gs_ssim_scratch_size(V, W, H)
     return torch.empty(int(n), dtype=torch.uint8, device=device)

@@ -114,3 +114,22 @@ def test_follow_up_calls_reject_bad_arguments_without_launching(lib):
     assert lib.gs_voxset_clear(one, 100, None) == L.GS_ERR_INVALID_ARG
     assert lib.gs_voxset_add_boxes(one, 128, 1, None, None, 3.0, 0.05, None) == L.GS_ERR_INVALID_ARG
     assert lib.gs_voxset_keep(1, one, one, 128, None, 0, 0.0, one, None) == L.GS_ERR_INVALID_ARG   # voxel 0
+
+
+def test_normal_loss_rejects_bad_arguments_without_launching(lib):
+    assert lib.gs_normal_scratch_size(2, 16, 8) == 24 * 2 * 16 * 8
+    assert lib.gs_normal_scratch_size(0, 16, 8) == 0
+    one = C.c_void_p(1 << 20)
+    args = [one, one, one, C.c_float(0.01), one, one, one, None]   # depth, prior, cams, w, d_depth, loss, scratch
+    assert lib.gs_loss_normal(0, 16, 8, *args) == L.GS_ERR_INVALID_ARG            # no views
+    assert lib.gs_loss_normal(1, 0, 8, *args) == L.GS_ERR_INVALID_ARG             # empty image
+    for k in (0, 1, 2, 4, 5):                                                      # a missing pointer
+        bad = list(args)
+        bad[k] = None
+        assert lib.gs_loss_normal(1, 16, 8, *bad) == L.GS_ERR_INVALID_ARG
+    bad = list(args)
+    bad[6] = C.c_void_p((1 << 20) + 8)                                             # scratch not 256-B aligned
+    assert lib.gs_loss_normal(1, 16, 8, *bad) == L.GS_ERR_INVALID_ARG
+    bad = list(args)
+    bad[3] = C.c_float(float("nan"))                                               # weight
+    assert lib.gs_loss_normal(1, 16, 8, *bad) == L.GS_ERR_INVALID_ARG
