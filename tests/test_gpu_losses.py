@@ -20,8 +20,10 @@ def R():
     return raster
 
 
+# weights: the benchmark step's (1.0, 0.1) and Eq. 4's alpha = 0.95, beta = 0.25
+@pytest.mark.parametrize("w_rgb,w_depth", [(1.0, 0.1), (0.95, 0.25)])
 @pytest.mark.parametrize("V,H,W", [(1, 37, 53), (2, 68, 120), (1, 680, 1200)])
-def test_l1_rgb_depth(R, V, H, W):
+def test_l1_rgb_depth(R, V, H, W, w_rgb, w_depth):
     rng = np.random.default_rng(V * H)
     x = rng.uniform(0, 1, (V, 3, H, W)).astype(np.float32)
     y = rng.uniform(0, 1, (V, 3, H, W)).astype(np.float32)
@@ -29,8 +31,8 @@ def test_l1_rgb_depth(R, V, H, W):
     dt = rng.uniform(0, 5, (V, H, W)).astype(np.float32)
     x[0, 0, 0, :5] = y[0, 0, 0, :5]              # sign(0) = 0
     t = lambda a: torch.from_numpy(a).cuda()
-    loss, d_rgb, d_d = R.loss_l1(t(x), t(y), t(d), t(dt), 1.0, 0.1)
-    L, gr, gd = OL.mapping_l1_loss(x, y, d, dt, 1.0, 0.1)
+    loss, d_rgb, d_d = R.loss_l1(t(x), t(y), t(d), t(dt), w_rgb, w_depth)
+    L, gr, gd = OL.mapping_l1_loss(x, y, d, dt, w_rgb, w_depth)
     assert abs(loss.item() - L) <= 1e-6 * abs(L)
     np.testing.assert_allclose(d_rgb.cpu().numpy(), gr, rtol=1e-6, atol=0)
     np.testing.assert_allclose(d_d.cpu().numpy(), gd, rtol=1e-6, atol=0)
