@@ -356,3 +356,158 @@ def test_exp_se3_left_matches_matrix_exponential():
         np.testing.assert_allclose(out[:9].reshape(3, 3), Tn[:3, :3], atol=1e-12)
         np.testing.assert_allclose(out[9:12], Tn[:3, 3], atol=1e-12)
         np.testing.assert_array_equal(out[12:], cam[12:])
+
+
+# ------------------------------------------------------------------------------------------
+# rotation conventions: the Gaussian's quaternion and the camera's world-to-camera rotation
+# ------------------------------------------------------------------------------------------
+
+def _quat_wxyz_to_scipy(q):
+    from scipy.spatial.transform import Rotation
+    q = np.asarray(q, np.float64)
+    return Rotation.from_quat([q[1], q[2], q[3], q[0]])          # scipy stores (x, y, z, w)
+
+
+@pytest.mark.parametrize("qcase", ["optical_axis_+35deg", "optical_axis_-50deg", "general"])
+def test_textbook_rotated_gaussian_without_dilation(qcase):
+    """Eq. 19's covariance form Sigma = R(q) S^2 R(q)^T for a rotated, anisotropic Gaussian.
+
+    A Gaussian on the optical axis of an identity camera projects with J = (f/z) [I | 0], so with
+    no dilation its alpha field is o * 2 pi |Sigma_2|^1/2 * N(x; c, Sigma_2) with Sigma_2 the upper
+    2x2 block of (f/z)^2 R S^2 R^T.  R comes from scipy's quaternion map (Hamilton convention, the
+    active rotation), not from the oracle.  The rotations about the optical axis put the long
+    axis at +35 and -50 degrees from the image x axis towards +y, so the sign of the off-diagonal
+    term (and of the conic's B) is fixed by the test; the general case also mixes in the z scale.
+    """
+    from scipy.stats import multivariate_normal
+    W, H, f, z, cx, cy = 64, 56, 120.0, 2.5, 32.0, 28.0
+    s_log = np.log([0.09, 0.025, 0.05])
+    if qcase == "general":
+        q = np.array([0.8, 0.3, -0.4, 0.5])
+    else:
+        th = np.deg2rad(35.0 if qcase.endswith("+35deg") else -50.0)
+        q = np.array([np.cos(th / 2), 0.0, 0.0, np.sin(th / 2)])
+    q32 = q.astype(np.float32)
+    o = 0.8
+    orc = single_view([[0, 0, z]], [s_log], [q32], [o], [[1, 1, 1]], cam_row(fx=f, fy=f, cx=cx, cy=cy), W, H,
+                      params=Params(dilation=0.0))
+    out = orc.forward()
+    Rm = _quat_wxyz_to_scipy(q32.astype(np.float64)).as_matrix()
+    s = np.exp(s_log.astype(np.float32).astype(np.float64))
+    Sigma = Rm @ np.diag(s ** 2) @ Rm.T
+    Sigma2 = (f / z) ** 2 * Sigma[:2, :2]
+    corr = Sigma2[0, 1] / np.sqrt(Sigma2[0, 0] * Sigma2[1, 1])
+    if qcase.endswith("+35deg"):
+        assert corr > 0.3            # long axis towards +x +y: positive correlation
+    elif qcase.endswith("-50deg"):
+        assert corr < -0.3
+    X, Y = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    pdf = multivariate_normal(mean=[cx, cy], cov=Sigma2).pdf(np.stack([X, Y], -1))
+    a = float(np.float32(o)) * 2 * np.pi * np.sqrt(np.linalg.det(Sigma2)) * pdf
+    on = out["last"][0] > 0
+    assert on.sum() > 100
+    np.testing.assert_allclose(out["alpha"][0][on], a[on], rtol=1e-9)
+    # blended exactly where the textbook alpha reaches 1/255, within the 3-sigma bounding square
+    r = 3.0 * np.sqrt(np.linalg.eigvalsh(Sigma2).max())
+    inside = (np.abs(X - cx) <= r) & (np.abs(Y - cy) <= r)
+    amin = 1.0 / 255.0
+    assert np.all(on[inside & (a > amin * (1 + 1e-6))])
+    assert not np.any(on & (a < amin * (1 - 1e-6)))
+    conic = orc.projection()["conic_d"][0]
+    np.testing.assert_allclose(conic, [np.linalg.inv(Sigma2)[0, 0], np.linalg.inv(Sigma2)[0, 1],
+                                       np.linalg.inv(Sigma2)[1, 1]], rtol=1e-10)
+
+
+def _scene_in_camera(rng, n, W, H, f):
+    """n Gaussians whose camera-frame positions fall inside a W x H pinhole view at depths 1.5..3."""
+    z = rng.uniform(1.5, 3.0, n)
+    x = rng.uniform(-0.4, 0.4, n) * W / f * z
+    y = rng.uniform(-0.4, 0.4, n) * H / f * z
+    pc = np.stack([x, y, z], 1)
+    ls = rng.normal(-2.6, 0.35, (n, 3)).astype(np.float32).astype(np.float64)
+    q = rng.normal(0, 1, (n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    o = (1 / (1 + np.exp(-rng.normal(0.5, 1.0, n)))).astype(np.float32).astype(np.float64)
+    c = rng.uniform(0, 1, (n, 3)).astype(np.float32).astype(np.float64)
+    return pc, ls, q, o, c
+
+
+def _orc_f32_f64(means, ls, q, o, c, cam, W, H):
+    """Oracle whose FP32 inputs are the roundings of the given FP64 values and whose FP64 value
+    chain runs on the FP64 values themselves (an exactly orthonormal R in particular)."""
+    vals = dict(means=means, log_scales=ls, quats=q, opacities=o, colors=c, cams=cam[None])
+    return Oracle(means, ls, q, o, c, cam[None], [0], [len(means)], W, H, values=vals)
+
+
+def test_camera_rotation_equals_rotating_the_scene():
+    """World-to-camera poses (Sec. III-B) and Eq. 19's rotation composition q' = q_R (x) q.
+
+    Rendering Gaussians (mu, q) from a camera (R, t) must equal rendering (R mu + t, q_R (x) q) from
+    the identity camera with the same intrinsics: same keys, same last index everywhere, images
+    within 1e-12; the opacity, colour and log-scale gradients agree and the mean gradient maps by
+    R^T.  q_R (x) q is scipy's rotation composition, independent of the oracle's quaternion map."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(21)
+    W, H, f = 64, 48, 60.0
+    n = 18
+    pc, ls, q, o, c = _scene_in_camera(rng, n, W, H, f)
+    Rot = Rotation.from_rotvec([0.45, -0.7, 0.3])
+    R = Rot.as_matrix()
+    t = np.array([0.3, -0.2, 0.5])
+    mu_w = (R.T @ (pc - t).T).T                    # world points that the camera sees at pc
+    mu_w = mu_w.astype(np.float32).astype(np.float64)
+    q_w = (Rot.inv() * _quat_wxyz_to_scipy_batch(q)).as_quat()[:, [3, 0, 1, 2]]
+    cam_rot = cam_row(R=R, t=t, fx=f, fy=f, cx=W / 2, cy=H / 2)
+    a = _orc_f32_f64(mu_w, ls, q_w, o, c, cam_rot, W, H)
+    # the same Gaussians expressed in the camera frame, seen by the identity camera
+    mu_c = (R @ mu_w.T).T + t
+    q_c = (Rot * _quat_wxyz_to_scipy_batch(q_w)).as_quat()[:, [3, 0, 1, 2]]
+    b = _orc_f32_f64(mu_c, ls, q_c, o, c, cam_row(fx=f, fy=f, cx=W / 2, cy=H / 2), W, H)
+    oa, ob = a.forward(), b.forward()
+    assert a.K == b.K and a.K > 20
+    np.testing.assert_array_equal(oa["last"], ob["last"])
+    assert (oa["last"] > 0).sum() > 0.3 * W * H
+    for k in ("rgb", "depth", "alpha", "final_T"):
+        np.testing.assert_allclose(oa[k], ob[k], rtol=0, atol=1e-12, err_msg=k)
+    g = (rng.normal(0, 1, (1, 3, H, W)), rng.normal(0, 0.3, (1, H, W)), rng.normal(0, 1, (1, H, W)))
+    ga, gb = a.backward(*g), b.backward(*g)
+    for k in ("opacities", "colors", "log_scales"):
+        np.testing.assert_allclose(ga[k], gb[k], rtol=1e-9, atol=1e-12 * np.abs(gb[k]).max(), err_msg=k)
+    np.testing.assert_allclose(ga["means"], gb["means"] @ R, rtol=1e-9, atol=1e-12 * np.abs(gb["means"]).max())
+
+
+def _quat_wxyz_to_scipy_batch(q):
+    from scipy.spatial.transform import Rotation
+    q = np.asarray(q, np.float64)
+    return Rotation.from_quat(q[:, [1, 2, 3, 0]])
+
+
+def test_camera_roll_by_90_degrees_rotates_the_image():
+    """A camera rolled by +90 degrees about its optical axis (R' = Rz R, t' = Rz t, Rz taking x to y)
+    sees camera coordinates (x', y') = (-y, x); for a square image with the principal point at its
+    centre, pixel (row i, column j) of the rolled view shows pixel (row W-1-j, column i) of the
+    original.  RGB, depth, alpha and final transmittance must match within 1e-12 (last indices are
+    not compared: they are positions in the per-tile lists)."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(33)
+    W = H = 64
+    f = 55.0
+    n = 20
+    pc, ls, q, o, c = _scene_in_camera(rng, n, W, H, f)
+    Rot = Rotation.from_rotvec([-0.2, 0.5, 0.35])
+    R = Rot.as_matrix()
+    t = np.array([-0.1, 0.25, 0.4])
+    mu_w = (R.T @ (pc - t).T).T.astype(np.float32).astype(np.float64)
+    q_w = (Rot.inv() * _quat_wxyz_to_scipy_batch(q)).as_quat()[:, [3, 0, 1, 2]]
+    Rz = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    base = _orc_f32_f64(mu_w, ls, q_w, o, c, cam_row(R=R, t=t, fx=f, fy=f, cx=W / 2, cy=H / 2), W, H)
+    roll = _orc_f32_f64(mu_w, ls, q_w, o, c, cam_row(R=Rz @ R, t=Rz @ t, fx=f, fy=f, cx=W / 2, cy=H / 2), W, H)
+    ob, orl = base.forward(), roll.forward()
+    assert (ob["last"] > 0).sum() > 0.3 * W * H
+    ii, jj = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    for k in ("depth", "alpha", "final_T"):
+        np.testing.assert_allclose(orl[k][0], ob[k][0][W - 1 - jj, ii], rtol=0, atol=1e-12, err_msg=k)
+    for ch in range(3):
+        np.testing.assert_allclose(orl["rgb"][0, ch], ob["rgb"][0, ch][W - 1 - jj, ii], rtol=0, atol=1e-12)
+    # the image really changed: a roll is not a symmetry of this scene
+    assert np.abs(orl["rgb"][0] - ob["rgb"][0]).max() > 0.05
