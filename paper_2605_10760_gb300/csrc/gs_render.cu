@@ -49,51 +49,75 @@ __device__ __forceinline__ void thread_pixel(int tid, int &lx, int &ly) {
     ly = (w / (TW / kWX)) * kWY + (lane / kWX) * kPPT;
 }
 
-// Minimum over the box [xa, xb] x [ya, yb] of sigma(d) = 1/2 (A dx^2 + C dy^2) + B dx dy,
-// d = p - mean (a convex quadratic: 0 when the mean is inside, else attained on an edge, where the
-// 1-D minimiser is clamped to the edge).  Ordinary FP32 arithmetic; callers compare it against the
-// cut-off with a margin.  Returns 0 (never skip) for non-finite or non-positive-definite input.
-__device__ __forceinline__ float sigma_min_box(float A, float B, float C, float mx, float my, float xa, float xb,
-                                               float ya, float yb) {
+// sigma(d) = 1/2 (A dx^2 + C dy^2) + B dx dy in the decision chain's operation order (spec_sigma),
+// used for the box minimum below so that its rounding error has the same bound
+__device__ __forceinline__ float sigma_rn(float A, float B, float C, float dx, float dy) {
+    const float q = fp::fma(fp::mul(A, dx), dx, fp::mul(fp::mul(C, dy), dy));
+    return fp::fma(fp::mul(B, dx), dy, fp::mul(0.5f, q));
+}
+
+// True when the decision chain's sigma exceeds `cut` at every pixel centre of the box
+// [xa, xb] x [ya, yb] (pixel centres; the mean (mx, my) and the conic (A, B, C) as recorded), so
+// that every pixel of the box skips the entry.
+//
+// The box minimum of the convex quadratic sigma is 0 when the mean is inside the box, else it is
+// attained on an edge at the 1-D minimiser clamped to that edge; s is that minimum evaluated in
+// FP32.  Error bound, with u = 2^-24 and M = 1/2 (A Dx^2 + C Dy^2) + |B| Dx Dy (Dx, Dy the largest
+// |offset| of the box from the mean along each axis, so M bounds the sum of the magnitudes of the
+// three terms of sigma anywhere in the box):
+//  * the decision chain at a pixel rounds dx and dy once (at most 2u M on sigma), forms the
+//    non-negative A dx^2 + C dy^2 with three roundings (3u M) and adds B dx dy with one fused
+//    rounding (u M): it is within 6u M of the exact sigma of that pixel;
+//  * s rounds each candidate's edge offset once and evaluates sigma with the same sequence
+//    (6u M); its minimiser, computed with an approximate reciprocal, is off by a relative
+//    O(u), which raises sigma only by O(u^2) M (sigma is quadratic about the minimiser);
+// so s - 12u M (up to O(u^2) M) is below the chain's sigma at every pixel of the box.  The box
+// is skipped when s > cut + 0.01 + 1e-3 |cut| + 32u M: the 32u term covers the 12u bound with
+// room for the rounding of M itself, and for thin footprints (conic entries of 1e4 and more,
+// where B dx dy cancels most of the other two terms) it is what keeps the skip exact.  Non-finite
+// or non-positive-definite input never skips.
+__device__ __forceinline__ bool box_skips(float A, float B, float C, float mx, float my, float xa, float xb,
+                                          float ya, float yb, float cut) {
     if (!(A > 0.f && C > 0.f && A < 1e30f && C < 1e30f && fabsf(B) < 1e30f && fabsf(mx) < 1e30f &&
-          fabsf(my) < 1e30f))
-        return 0.f;
+          fabsf(my) < 1e30f && fabsf(cut) < 1e30f))
+        return false;
     const float dxa = xa - mx, dxb = xb - mx, dya = ya - my, dyb = yb - my;
-    if (dxa <= 0.f && dxb >= 0.f && dya <= 0.f && dyb >= 0.f) return 0.f;
+    if (dxa <= 0.f && dxb >= 0.f && dya <= 0.f && dyb >= 0.f) return false;
     const float iA = __fdividef(1.f, A), iC = __fdividef(1.f, C);
     float best = 3.0e38f;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const float dx = e ? dxb : dxa;
         const float dy = fminf(fmaxf(-B * dx * iC, dya), dyb);
-        best = fminf(best, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
+        best = fminf(best, sigma_rn(A, B, C, dx, dy));
     }
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const float dy = e ? dyb : dya;
         const float dx = fminf(fmaxf(-B * dy * iA, dxa), dxb);
-        best = fminf(best, 0.5f * (A * dx * dx + C * dy * dy) + B * dx * dy);
+        best = fminf(best, sigma_rn(A, B, C, dx, dy));
     }
-    return best;
+    const float Dx = fmaxf(fabsf(dxa), fabsf(dxb)), Dy = fmaxf(fabsf(dya), fabsf(dyb));
+    const float M = 0.5f * (A * Dx * Dx + C * Dy * Dy) + fabsf(B) * Dx * Dy;
+    const float thr = cut + 0.01f + 1e-3f * fabsf(cut) + 0x1p-19f * M;
+    return best > thr;   // false for a NaN or infinite threshold
 }
 
-// Bit w set <=> warp w's block of pixels (kWX x kWY, see thread_pixel) may blend the entry.  A cleared bit means sigma > cut at every pixel of that block: every pixel there skips the
-// entry in the decision chain, so the warp may skip it without evaluating anything.  The margin
-// (0.01 + 1e-3 |cut|) is far above the FP32 error of either sigma evaluation.
+// Bit w set <=> warp w's block of pixels (kWX x kWY, see thread_pixel) may blend the entry.  A
+// cleared bit means the decision chain's sigma exceeds the cut at every pixel of that block
+// (box_skips): every pixel there skips the entry, so the warp may skip it without evaluating it.
 template <int TW, int TH>
 __device__ __forceinline__ uint32_t warp_region_mask(const float4 &r0, const float4 &r1, float cut, int tile_x0,
                                                      int tile_y0) {
     constexpr int NW = TW * TH / (kPPT * 32);
     static_assert(TW % kWX == 0 && TH % kWY == 0, "tile must hold whole warp blocks");
-    const float thr = cut + 0.01f + 1e-3f * fabsf(cut);
     uint32_t m = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         const float xa = (float)(tile_x0 + (w % (TW / kWX)) * kWX) + 0.5f;
         const float ya = (float)(tile_y0 + (w / (TW / kWX)) * kWY) + 0.5f;
-        const float s = sigma_min_box(r0.z, r0.w, r1.x, r0.x, r0.y, xa, xa + (float)(kWX - 1), ya,
-                                      ya + (float)(kWY - 1));
-        if (!(s > thr)) m |= 1u << w;
+        if (!box_skips(r0.z, r0.w, r1.x, r0.x, r0.y, xa, xa + (float)(kWX - 1), ya, ya + (float)(kWY - 1), cut))
+            m |= 1u << w;
     }
     return m;
 }
