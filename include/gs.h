@@ -67,11 +67,16 @@ typedef struct gs_camera {
     float fx, fy, cx, cy;
 } gs_camera;
 
-/* Binning algorithms of gs_bin_sort.  Both produce the same lists bit for bit: every tile's
+/* Binning algorithms of gs_bin_sort.  All produce the same lists bit for bit: every tile's
  * entries ordered by (depth bits, flattened pair index).
  *   GS_SORT_ONESWEEP (default): scan of tiles_touched, keys (tile << 32 | depth bits) in emission
- *     order and the digit histograms of every pass (one kernel), then a stable LSD onesweep radix
- *     sort over all keys (8-bit digits, decoupled look-back).
+ *     order and the digit histograms of every pass, then a stable LSD radix sort over all keys
+ *     (8-bit digits) and the tile ranges.  When the key capacity allows one sort partition of
+ *     8192 keys per SM (about 1.2 M keys on a GB300), all of it is ONE cooperative launch whose
+ *     CTAs meet at bounded grid barriers between the passes; otherwise it is GS_SORT_ONESWEEP_PASSES.
+ *   GS_SORT_ONESWEEP_PASSES: the same sort as one launch per phase: the scan / emission /
+ *     histogram kernel, one onesweep launch per pass (4096-key partitions, decoupled look-back),
+ *     then the ranges.
  *   GS_SORT_TILE_BUCKET: gs_project counts the keys of every tile, a scan of the G counts gives
  *     each tile its slice, emission drops each key into its tile's slice by atomic slot taking
  *     (order inside the slice arbitrary), and each tile's slice is sorted by (depth bits, pair
@@ -79,7 +84,7 @@ typedef struct gs_camera {
  *     slices longer than 4096 entries as sorted runs merged in global memory).  No global sort,
  *     but one atomic per key twice; measured slower than the onesweep path on GB300 except for
  *     small single-view problems. */
-enum { GS_SORT_TILE_BUCKET = 0, GS_SORT_ONESWEEP = 1 };
+enum { GS_SORT_TILE_BUCKET = 0, GS_SORT_ONESWEEP = 1, GS_SORT_ONESWEEP_PASSES = 2 };
 
 /* Rasterizer constants.  gs_default_params() gives tile 16x16, near 0.2, dilation 0.3,
  * radius_sigmas 3, alpha_max 0.99, alpha_min 1/255 (float division), t_min 1e-4, bg 0,
@@ -93,7 +98,7 @@ typedef struct gs_params {
     float alpha_min;
     float t_min;
     float bg[3];
-    int32_t sort_mode;                 /* GS_SORT_ONESWEEP or GS_SORT_TILE_BUCKET */
+    int32_t sort_mode;                 /* GS_SORT_ONESWEEP, GS_SORT_ONESWEEP_PASSES or GS_SORT_TILE_BUCKET */
     int32_t batch_records;             /* list entries staged per TMA batch by the compositing kernels:
                                           0 = min(256, tile pixels); else 64, 128 or 256, at most the
                                           tile's pixel count (a tuning knob: results do not change) */
@@ -256,12 +261,10 @@ int gs_loss_l1(int32_t views, int32_t width, int32_t height, const float *rgb, c
  *   depth [V,H,W] (the rendered depth), prior [V,3,H,W] unit normals in each view's camera frame,
  *   cams [V] device cameras (only the intrinsics are read).  ADDS L to *loss (device double) and
  *   dL/d depth to d_depth [V,H,W] (so it follows gs_loss_l1 / gs_render_fwd_l1, which write
- *   them).  scratch: device buffer of gs_normal_scratch_size() bytes (24 B per pixel),
- *   256-byte aligned.  Two kernels, no synchronisation. */
-size_t gs_normal_scratch_size(int32_t views, int32_t width, int32_t height);
+ *   them).  One kernel (a tile of pixels per CTA, the neighbours' terms recomputed in shared
+ *   memory), no scratch memory, no synchronisation. */
 int gs_loss_normal(int32_t views, int32_t width, int32_t height, const float *depth, const float *prior,
-                   const gs_camera *cams, float weight, float *d_depth, double *loss, void *scratch,
-                   void *stream);
+                   const gs_camera *cams, float weight, float *d_depth, double *loss, void *stream);
 
 /* L = w_l1 mean|rgb - rgb_t| + w_ssim (1 - SSIM(rgb, rgb_t)) (Eq. 23's photometric and
  * structural terms): 11x11 Gaussian window, sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2,
@@ -283,8 +286,10 @@ int gs_loss_l1_ssim(int32_t views, int32_t width, int32_t height, const float *r
  * routine.  The caller still provides rgb, rgb_t, d_rgb and loss as for gs_loss_l1_ssim.
  *  - Limit: width * height <= GS_SSIM_NOALLOC_MAX_PLANE pixels per image plane (any number of
  *    views); larger images are rejected with GS_ERR_TOO_LARGE before anything is launched.
- *  - Set-up: the first call on a device (with that device current) looks up the device address of
- *    the static area; make that first call before any stream capture on that device.
+ *  - Set-up: a call made outside stream capture (with its device current) looks up the device
+ *    address of the static area, every time, so the address stays right after a device reset
+ *    reloads the library's module; a call made during stream capture reuses the address of the
+ *    last call outside capture on that device, so make one call on a device before capturing.
  *  - Sharing: every call on a device uses the same area and leaves its last contents there; the
  *    call clears what must start at zero itself.  Calls whose executions overlap on the GPU (on
  *    different streams, or from different host threads) race on the area and give wrong results:
@@ -468,6 +473,14 @@ int gs_debug_expf(const float *x, float *y_spec, float *y_cuda, int64_t n, void 
  * GS_OK otherwise.  *total receives the scan total (n on a normal run). */
 size_t gs_debug_scan_scratch_size(int64_t n);
 int gs_debug_scan_timeout(void *scratch, int64_t n, int32_t silent_partition, void *stream, int64_t *total);
+
+/* Bounded-wait check of the single-kernel binning (GS_SORT_ONESWEEP when it applies): runs
+ * gs_bin_sort's cooperative kernel on the projected problem in `ws` with CTA `absent_cta` leaving
+ * before its first grid barrier (-1: normal run) and a short spin limit (about a millisecond),
+ * then synchronises and returns the recorded status: GS_ERR_TIMEOUT when the other CTAs gave up
+ * waiting, GS_OK otherwise.  GS_ERR_INVALID_ARG when the single-kernel form does not apply to the
+ * problem (its key capacity is too large) or absent_cta is not a CTA of the launch. */
+int gs_debug_bin_sort_absent_cta(const gs_problem *pb, void *ws, int32_t absent_cta, void *stream);
 
 #ifdef __cplusplus
 }

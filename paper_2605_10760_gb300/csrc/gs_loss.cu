@@ -335,13 +335,18 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 static std::mutex g_noalloc_mu;
 static void *g_noalloc_addr[64];
 
-// Device address of g_noalloc_scratch on the current device, looked up once per device.  (On the
-// host the symbol names a host-side stand-in, never the device memory itself.)
-static int noalloc_scratch(void **out) {
+// Device address of g_noalloc_scratch on the current device.  (On the host the symbol names a
+// host-side stand-in, never the device memory itself.)  Outside stream capture every call looks
+// the address up again, which is cheap and stays right after a device reset has reloaded the
+// module; while `s` is being captured the address cached by the last call outside capture is
+// used, and without one the lookup is attempted once more.
+static int noalloc_scratch(cudaStream_t s, void **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GS_ERR_CUDA;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return GS_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone || !g_noalloc_addr[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return GS_ERR_CUDA;
         g_noalloc_addr[dev] = p;
@@ -356,7 +361,7 @@ int launch_loss_l1_ssim_noalloc(int V, int W, int H, const float *rgb, const flo
     if (plane > kNoallocMaxPlane) return GS_ERR_TOO_LARGE;
     static const SsimTaps taps = make_taps();
     void *base = nullptr;
-    int rc = noalloc_scratch(&base);
+    int rc = noalloc_scratch(s, &base);
     if (rc) return rc;
     double *sums = reinterpret_cast<double *>(base);
     float *dmu = reinterpret_cast<float *>(static_cast<char *>(base) + 256);
