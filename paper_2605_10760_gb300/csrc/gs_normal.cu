@@ -2,15 +2,20 @@
 // |1 - N_hat . N_bar| between the normal induced by the rendered depth and a given normal prior,
 // and its gradient with respect to the depth.
 //
-// k_normal_terms: a thread per pixel.  P = D r with r = ((x + 0.5 - cx) / fx, (y + 0.5 - cy) / fy,
-// 1) the pixel's ray; central-difference tangents t_x = P(x+1, y) - P(x-1, y),
-// t_y = P(x, y+1) - P(x, y-1); u = t_y x t_x, N_hat = u / |u| (facing the camera for a surface
-// seen from the front).  A pixel is valid when it is not on the image border, its depth and its
-// four neighbours' depths are positive and finite, and |u| > 0.  The pixel's loss term goes to a
-// per-thread FP64 sum (one atomic per block); the adjoints G_x = dL/dt_x and G_y = dL/dt_y go to a
-// scratch plane (zero for invalid pixels).  k_normal_gather: a thread per pixel q adds
-// r(q) . (G_x(q-x) - G_x(q+x) + G_y(q-y) - G_y(q+y)) to d_depth, every neighbour read inside the
-// image.  Values in FP32.
+// One persistent kernel; a CTA takes (view, 32 x 8 tile) items in turn.  Per item the tile's depths
+// with a 2-pixel halo and the prior over the tile plus a 1-pixel halo go to shared memory (loaded
+// one item ahead into registers, so the next tile's loads overlap this tile's arithmetic); every
+// pixel of the tile plus a 1-pixel halo computes, from P = D r with
+// r = ((x + 0.5 - cx) / fx, (y + 0.5 - cy) / fy, 1) its pixel ray (nm_ray), the central-difference
+// tangents t_x = P(x+1, y) - P(x-1, y), t_y = P(x, y+1) - P(x, y-1), u = t_y x t_x and
+// N_hat = u / |u| (facing the camera for a surface seen from the front), and the adjoints
+// G_x = dL/dt_x, G_y = dL/dt_y into shared memory (zero where the pixel is invalid: on the image
+// border, a depth of the pixel or of its four neighbours not positive and finite, or |u| = 0).
+// The loss of the tile's own pixels goes to a per-thread FP64 sum (one atomic per CTA).  Then every
+// pixel q of the tile adds r(q) . (G_x(q-x) - G_x(q+x) + G_y(q-y) - G_y(q+y)) to d_depth.  The halo
+// pixels' adjoints are recomputed by each neighbouring tile instead of going through global
+// memory, so a pixel costs its depth, its prior and a read-modify-write of d_depth.  Values in
+// FP32.
 #include <algorithm>
 
 #include "gs_kernels.cuh"
@@ -39,98 +44,159 @@ __device__ __forceinline__ void nm_block_add(double v, double *out) {
     }
 }
 
-__global__ void __launch_bounds__(kNormalThreads) k_normal_terms(NormalArgs a) {
-    const long long HW = (long long)a.H * a.W, n = (long long)a.V * HW;
+constexpr int kNTW = 32, kNTH = 8;                        // output tile
+constexpr int kNDW = kNTW + 4, kNDH = kNTH + 4;            // depths: 2-pixel halo
+constexpr int kNGW = kNTW + 2, kNGH = kNTH + 2;            // adjoints: 1-pixel halo
+static_assert(kNTW * kNTH == kNormalThreads, "one output pixel per thread");
+
+// the pixel ray of column x / row y (one expression for the normal and for its adjoint)
+__device__ __forceinline__ float nm_ray(int x, float c, float inv_f) { return ((float)x + 0.5f - c) * inv_f; }
+
+constexpr int kNDElems = kNDH * kNDW;                    // depths staged per tile
+constexpr int kNPElems = 3 * kNGH * kNGW;                // prior components staged per tile
+constexpr int kNDPer = (kNDElems + kNormalThreads - 1) / kNormalThreads;
+constexpr int kNPPer = (kNPElems + kNormalThreads - 1) / kNormalThreads;
+
+// Global inputs of one (view, tile) item, held in registers from the previous item on: the
+// thread's share of the depth halo and of the prior over the adjoint region, and d_depth of its
+// own output pixel.  Everything is loaded one item ahead, so a CTA's loads for the next tile are in
+// flight while it computes the current one.
+struct NormalStage {
+    float d[kNDPer];
+    float p[kNPPer];
+    float dd;
+};
+
+__device__ __forceinline__ void nm_item(const NormalArgs &a, long long item, int tiles_x, int tiles_y, int &v,
+                                        int &x0, int &y0) {
+    v = (int)(item / ((long long)tiles_x * tiles_y));
+    const int t = (int)(item - (long long)v * tiles_x * tiles_y);
+    x0 = (t % tiles_x) * kNTW;
+    y0 = (t / tiles_x) * kNTH;
+}
+
+__device__ __forceinline__ void nm_fetch(const NormalArgs &a, int v, int x0, int y0, NormalStage &st) {
+    const long long HW = (long long)a.H * a.W;
+    const float *D = a.depth + (long long)v * HW;
+#pragma unroll
+    for (int k = 0; k < kNDPer; ++k) {
+        const int i = threadIdx.x + k * kNormalThreads;
+        const int ly = i / kNDW, lx = i - ly * kNDW;
+        const int x = x0 - 2 + lx, y = y0 - 2 + ly;
+        st.d[k] = (i < kNDElems && x >= 0 && x < a.W && y >= 0 && y < a.H) ? D[(long long)y * a.W + x] : -1.0f;
+    }
+    const float *Pr = a.prior + (long long)v * 3 * HW;
+#pragma unroll
+    for (int k = 0; k < kNPPer; ++k) {
+        const int i = threadIdx.x + k * kNormalThreads;
+        const int ch = i / (kNGH * kNGW), r = i - ch * (kNGH * kNGW);
+        const int gy_ = r / kNGW, gx_ = r - gy_ * kNGW;
+        const int x = x0 - 1 + gx_, y = y0 - 1 + gy_;
+        st.p[k] = (i < kNPElems && x >= 0 && x < a.W && y >= 0 && y < a.H)
+                      ? Pr[(long long)ch * HW + (long long)y * a.W + x] : 0.0f;
+    }
+    const int x = x0 + threadIdx.x % kNTW, y = y0 + threadIdx.x / kNTW;
+    st.dd = (x < a.W && y < a.H) ? a.d_depth[(long long)v * HW + (long long)y * a.W + x] : 0.0f;
+}
+
+__global__ void __launch_bounds__(kNormalThreads) k_normal(NormalArgs a) {
+    __shared__ float s_d[kNDH][kNDW];
+    __shared__ float s_p[3][kNGH][kNGW];
+    __shared__ float s_g[6][kNGH][kNGW];
+    const long long HW = (long long)a.H * a.W;
+    const int tiles_x = (a.W + kNTW - 1) / kNTW, tiles_y = (a.H + kNTH - 1) / kNTH;
+    const long long tiles = (long long)a.V * tiles_x * tiles_y;
     double acc = 0.0;
-    for (long long i = (long long)blockIdx.x * kNormalThreads + threadIdx.x; i < n;
-         i += (long long)gridDim.x * kNormalThreads) {
-        const int v = (int)(i / HW);
-        const long long pix = i - (long long)v * HW;
-        const int y = (int)(pix / a.W), x = (int)(pix - (long long)y * a.W);
-        float3 gx = make_float3(0.f, 0.f, 0.f), gy = make_float3(0.f, 0.f, 0.f);
-        if (x >= 1 && x <= a.W - 2 && y >= 1 && y <= a.H - 2) {
-            const float *D = a.depth + (long long)v * HW;
-            const float dc = D[pix], dl = D[pix - 1], dr = D[pix + 1], du = D[pix - a.W], dd = D[pix + a.W];
-            if (nm_depth_ok(dc) && nm_depth_ok(dl) && nm_depth_ok(dr) && nm_depth_ok(du) && nm_depth_ok(dd)) {
-                const gs_camera &cam = a.cams[v];
-                const float ifx = 1.0f / cam.fx, ify = 1.0f / cam.fy;
-                const float rxc = ((float)x + 0.5f - cam.cx) * ifx;
-                const float rxl = ((float)(x - 1) + 0.5f - cam.cx) * ifx, rxr = ((float)(x + 1) + 0.5f - cam.cx) * ifx;
-                const float ryc = ((float)y + 0.5f - cam.cy) * ify;
-                const float ryu = ((float)(y - 1) + 0.5f - cam.cy) * ify, ryd = ((float)(y + 1) + 0.5f - cam.cy) * ify;
-                // neighbours in a row share the ray's y component, in a column its x component
-                const float3 tx = make_float3(dr * rxr - dl * rxl, (dr - dl) * ryc, dr - dl);
-                const float3 ty = make_float3((dd - du) * rxc, dd * ryd - du * ryu, dd - du);
-                const float3 u = nm_cross(ty, tx);
-                const float nu = sqrtf(nm_dot(u, u));
-                if (nu > 0.0f) {
-                    const float inu = 1.0f / nu;
-                    const float3 nh = make_float3(u.x * inu, u.y * inu, u.z * inu);
-                    const float *pr = a.prior + (long long)v * 3 * HW + pix;
-                    const float3 nb = make_float3(pr[0], pr[HW], pr[2 * HW]);
-                    const float c = 1.0f - nm_dot(nh, nb);
-                    acc += (double)fabsf(c);
-                    const float k = c > 0.f ? -a.scale : (c < 0.f ? a.scale : 0.f);   // -scale sign(c)
-                    const float3 gn = make_float3(k * nb.x, k * nb.y, k * nb.z);
-                    const float pn = nm_dot(nh, gn);
-                    const float3 gu = make_float3((gn.x - nh.x * pn) * inu, (gn.y - nh.y * pn) * inu,
-                                                  (gn.z - nh.z * pn) * inu);
-                    gx = nm_cross(gu, ty);
-                    gy = nm_cross(tx, gu);
+    NormalStage st;
+    long long item = blockIdx.x;
+    int v = 0, x0 = 0, y0 = 0;
+    if (item < tiles) {
+        nm_item(a, item, tiles_x, tiles_y, v, x0, y0);
+        nm_fetch(a, v, x0, y0, st);
+    }
+    // persistent over the (view, tile) items, so the loss needs one atomic per CTA, not per tile
+    for (; item < tiles; item += gridDim.x) {
+        __syncthreads();   // the previous item's reads of s_d, s_p and s_g are done
+#pragma unroll
+        for (int k = 0; k < kNDPer; ++k) {
+            const int i = threadIdx.x + k * kNormalThreads;
+            if (i < kNDElems) (&s_d[0][0])[i] = st.d[k];
+        }
+#pragma unroll
+        for (int k = 0; k < kNPPer; ++k) {
+            const int i = threadIdx.x + k * kNormalThreads;
+            if (i < kNPElems) (&s_p[0][0][0])[i] = st.p[k];
+        }
+        const float dd_own = st.dd;
+        const int cv = v, cx0 = x0, cy0 = y0;
+        const long long next = item + gridDim.x;
+        if (next < tiles) {   // the next item's inputs, in flight while this one is computed
+            nm_item(a, next, tiles_x, tiles_y, v, x0, y0);
+            nm_fetch(a, v, x0, y0, st);
+        }
+        const gs_camera &cam = a.cams[cv];
+        const float ifx = 1.0f / cam.fx, ify = 1.0f / cam.fy;
+        __syncthreads();
+        for (int i = threadIdx.x; i < kNGH * kNGW; i += kNormalThreads) {
+            const int gy_ = i / kNGW, gx_ = i - gy_ * kNGW;
+            const int x = cx0 - 1 + gx_, y = cy0 - 1 + gy_;
+            float3 gx = make_float3(0.f, 0.f, 0.f), gy = make_float3(0.f, 0.f, 0.f);
+            if (x >= 1 && x <= a.W - 2 && y >= 1 && y <= a.H - 2) {
+                const int cx = gx_ + 1, cy = gy_ + 1;            // position in s_d
+                const float dc = s_d[cy][cx], dl = s_d[cy][cx - 1], dr = s_d[cy][cx + 1], du = s_d[cy - 1][cx],
+                            dd = s_d[cy + 1][cx];
+                if (nm_depth_ok(dc) && nm_depth_ok(dl) && nm_depth_ok(dr) && nm_depth_ok(du) && nm_depth_ok(dd)) {
+                    const float rxc = nm_ray(x, cam.cx, ifx), rxl = nm_ray(x - 1, cam.cx, ifx),
+                                rxr = nm_ray(x + 1, cam.cx, ifx);
+                    const float ryc = nm_ray(y, cam.cy, ify), ryu = nm_ray(y - 1, cam.cy, ify),
+                                ryd = nm_ray(y + 1, cam.cy, ify);
+                    // neighbours in a row share the ray's y component, in a column its x component
+                    const float3 tx = make_float3(dr * rxr - dl * rxl, (dr - dl) * ryc, dr - dl);
+                    const float3 ty = make_float3((dd - du) * rxc, dd * ryd - du * ryu, dd - du);
+                    const float3 u = nm_cross(ty, tx);
+                    const float nu = sqrtf(nm_dot(u, u));
+                    if (nu > 0.0f) {
+                        const float inu = 1.0f / nu;
+                        const float3 nh = make_float3(u.x * inu, u.y * inu, u.z * inu);
+                        const float3 nb = make_float3(s_p[0][gy_][gx_], s_p[1][gy_][gx_], s_p[2][gy_][gx_]);
+                        const float c = 1.0f - nm_dot(nh, nb);
+                        if (gx_ >= 1 && gx_ <= kNTW && gy_ >= 1 && gy_ <= kNTH) acc += (double)fabsf(c);   // own pixel
+                        const float k = c > 0.f ? -a.scale : (c < 0.f ? a.scale : 0.f);   // -scale sign(c)
+                        const float3 gn = make_float3(k * nb.x, k * nb.y, k * nb.z);
+                        const float pn = nm_dot(nh, gn);
+                        const float3 gu = make_float3((gn.x - nh.x * pn) * inu, (gn.y - nh.y * pn) * inu,
+                                                      (gn.z - nh.z * pn) * inu);
+                        gx = nm_cross(gu, ty);
+                        gy = nm_cross(tx, gu);
+                    }
                 }
             }
+            s_g[0][gy_][gx_] = gx.x; s_g[1][gy_][gx_] = gx.y; s_g[2][gy_][gx_] = gx.z;
+            s_g[3][gy_][gx_] = gy.x; s_g[4][gy_][gx_] = gy.y; s_g[5][gy_][gx_] = gy.z;
         }
-        float *G = a.scratch + (long long)v * 6 * HW + pix;
-        G[0] = gx.x;
-        G[HW] = gx.y;
-        G[2 * HW] = gx.z;
-        G[3 * HW] = gy.x;
-        G[4 * HW] = gy.y;
-        G[5 * HW] = gy.z;
+        __syncthreads();
+        const int tx_ = threadIdx.x % kNTW, ty_ = threadIdx.x / kNTW;
+        const int x = cx0 + tx_, y = cy0 + ty_;
+        if (x < a.W && y < a.H) {
+            const int gx_ = tx_ + 1, gy_ = ty_ + 1;
+            // + G_x of the left neighbour (t_x there = P(q) - P(q - 2)), - G_x of the right one,
+            // + G_y of the pixel above, - G_y of the pixel below (zero outside the image)
+            float3 dP;
+            dP.x = s_g[0][gy_][gx_ - 1] - s_g[0][gy_][gx_ + 1] + s_g[3][gy_ - 1][gx_] - s_g[3][gy_ + 1][gx_];
+            dP.y = s_g[1][gy_][gx_ - 1] - s_g[1][gy_][gx_ + 1] + s_g[4][gy_ - 1][gx_] - s_g[4][gy_ + 1][gx_];
+            dP.z = s_g[2][gy_][gx_ - 1] - s_g[2][gy_][gx_ + 1] + s_g[5][gy_ - 1][gx_] - s_g[5][gy_ + 1][gx_];
+            const float3 r = make_float3(nm_ray(x, cam.cx, ifx), nm_ray(y, cam.cy, ify), 1.0f);
+            a.d_depth[(long long)cv * HW + (long long)y * a.W + x] = dd_own + nm_dot(r, dP);
+        }
     }
     nm_block_add(acc * (double)a.scale, a.loss);
 }
 
-__global__ void __launch_bounds__(kNormalThreads) k_normal_gather(NormalArgs a) {
-    const long long HW = (long long)a.H * a.W, n = (long long)a.V * HW;
-    for (long long i = (long long)blockIdx.x * kNormalThreads + threadIdx.x; i < n;
-         i += (long long)gridDim.x * kNormalThreads) {
-        const int v = (int)(i / HW);
-        const long long pix = i - (long long)v * HW;
-        const int y = (int)(pix / a.W), x = (int)(pix - (long long)y * a.W);
-        const float *G = a.scratch + (long long)v * 6 * HW;
-        float3 dP = make_float3(0.f, 0.f, 0.f);
-        if (x >= 1) {                   // + G_x of the left neighbour (t_x there = P(q) - P(q - 2))
-            const long long q = pix - 1;
-            dP.x += G[q]; dP.y += G[HW + q]; dP.z += G[2 * HW + q];
-        }
-        if (x + 1 < a.W) {              // - G_x of the right neighbour
-            const long long q = pix + 1;
-            dP.x -= G[q]; dP.y -= G[HW + q]; dP.z -= G[2 * HW + q];
-        }
-        if (y >= 1) {                   // + G_y of the pixel above
-            const long long q = pix - a.W;
-            dP.x += G[3 * HW + q]; dP.y += G[4 * HW + q]; dP.z += G[5 * HW + q];
-        }
-        if (y + 1 < a.H) {              // - G_y of the pixel below
-            const long long q = pix + a.W;
-            dP.x -= G[3 * HW + q]; dP.y -= G[4 * HW + q]; dP.z -= G[5 * HW + q];
-        }
-        const gs_camera &cam = a.cams[v];
-        const float3 r = make_float3(((float)x + 0.5f - cam.cx) / cam.fx, ((float)y + 0.5f - cam.cy) / cam.fy, 1.0f);
-        a.d_depth[i] += nm_dot(r, dP);
-    }
-}
-
-size_t normal_scratch_bytes(int V, int W, int H) { return (size_t)6 * sizeof(float) * (size_t)V * W * H; }
-
 int launch_loss_normal(const NormalArgs &a, cudaStream_t s) {
-    const long long n = (long long)a.V * a.W * a.H;
-    const long long grid = std::max<long long>(1, std::min<long long>((n + kNormalThreads - 1) / kNormalThreads,
-                                                                      (long long)device_sm_count() * 8));
-    k_normal_terms<<<(unsigned)grid, kNormalThreads, 0, s>>>(a);
-    k_normal_gather<<<(unsigned)grid, kNormalThreads, 0, s>>>(a);
-    count_launches(2);
+    const long long tiles = (long long)a.V * ((a.W + kNTW - 1) / kNTW) * ((a.H + kNTH - 1) / kNTH);
+    const long long grid = std::max<long long>(1, std::min<long long>(tiles, (long long)device_sm_count() * 8));
+    k_normal<<<(unsigned)grid, kNormalThreads, 0, s>>>(a);
+    count_launches(1);
     return check_launch();
 }
 
