@@ -67,16 +67,11 @@ typedef struct gs_camera {
     float fx, fy, cx, cy;
 } gs_camera;
 
-/* Binning algorithms of gs_bin_sort.  All produce the same lists bit for bit: every tile's
+/* Binning algorithms of gs_bin_sort.  Both produce the same lists bit for bit: every tile's
  * entries ordered by (depth bits, flattened pair index).
  *   GS_SORT_ONESWEEP (default): scan of tiles_touched, keys (tile << 32 | depth bits) in emission
- *     order and the digit histograms of every pass, then a stable LSD radix sort over all keys
- *     (8-bit digits) and the tile ranges.  When the key capacity allows one sort partition of
- *     8192 keys per SM (about 1.2 M keys on a GB300), all of it is ONE cooperative launch whose
- *     CTAs meet at bounded grid barriers between the passes; otherwise it is GS_SORT_ONESWEEP_PASSES.
- *   GS_SORT_ONESWEEP_PASSES: the same sort as one launch per phase: the scan / emission /
- *     histogram kernel, one onesweep launch per pass (4096-key partitions, decoupled look-back),
- *     then the ranges.
+ *     order and the digit histograms of every pass (one kernel), then a stable LSD onesweep radix
+ *     sort over all keys (8-bit digits, decoupled look-back).
  *   GS_SORT_TILE_BUCKET: gs_project counts the keys of every tile, a scan of the G counts gives
  *     each tile its slice, emission drops each key into its tile's slice by atomic slot taking
  *     (order inside the slice arbitrary), and each tile's slice is sorted by (depth bits, pair
@@ -84,7 +79,7 @@ typedef struct gs_camera {
  *     slices longer than 4096 entries as sorted runs merged in global memory).  No global sort,
  *     but one atomic per key twice; measured slower than the onesweep path on GB300 except for
  *     small single-view problems. */
-enum { GS_SORT_TILE_BUCKET = 0, GS_SORT_ONESWEEP = 1, GS_SORT_ONESWEEP_PASSES = 2 };
+enum { GS_SORT_TILE_BUCKET = 0, GS_SORT_ONESWEEP = 1 };
 
 /* Rasterizer constants.  gs_default_params() gives tile 16x16, near 0.2, dilation 0.3,
  * radius_sigmas 3, alpha_max 0.99, alpha_min 1/255 (float division), t_min 1e-4, bg 0,
@@ -98,7 +93,7 @@ typedef struct gs_params {
     float alpha_min;
     float t_min;
     float bg[3];
-    int32_t sort_mode;                 /* GS_SORT_ONESWEEP, GS_SORT_ONESWEEP_PASSES or GS_SORT_TILE_BUCKET */
+    int32_t sort_mode;                 /* GS_SORT_ONESWEEP or GS_SORT_TILE_BUCKET */
     int32_t batch_records;             /* list entries staged per TMA batch by the compositing kernels:
                                           0 = min(256, tile pixels); else 64, 128 or 256, at most the
                                           tile's pixel count (a tuning knob: results do not change) */
@@ -234,9 +229,23 @@ int gs_render_fwd_l1(const gs_problem *pb, void *ws, const gs_image *out, const 
 
 /* Adjoint of the compositing, back to front from final_T and last_idx (no per-pixel lists),
  * followed by the projection adjoint: accumulates dL/d(means, log_scales, quats, opacities,
- * colors) into `grads` (+=) and leaves per-view pose partial sums in the workspace. */
+ * colors) into `grads` (+=) and leaves per-view pose partial sums in the workspace.  It is
+ * gs_render_bwd_composite followed by gs_project_bwd. */
 int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const gs_image *fwd,
                   const gs_image_grad *dimg, const gs_grads *grads, void *stream);
+
+/* The compositing adjoint alone: the 10 per-(view, Gaussian) 2-D gradients (mean2D, conic,
+ * opacity, depth, colour) summed over every pixel into the workspace (they were zeroed for the
+ * visible pairs by gs_bin_sort).  dimg: dL/d rgb [V,3,H,W], dL/d depth [V,H,W], dL/d alpha
+ * [V,H,W], each may be NULL (zero). */
+int gs_render_bwd_composite(const gs_problem *pb, void *ws, const gs_image *fwd, const gs_image_grad *dimg,
+                            void *stream);
+
+/* The projection adjoint alone (after gs_render_bwd_composite): chains the 2-D gradients through
+ * the projection to the Gaussian parameters, accumulated (+=) into `grads` and summed over the
+ * views of each Gaussian, and leaves per-view pose partial sums in the workspace for
+ * gs_pose_grad. */
+int gs_project_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const gs_grads *grads, void *stream);
 
 /* dL/d xi for each view, xi = (rho, phi) the left perturbation T <- Exp(xi) T of the world-to-camera
  * pose at xi = 0 (the per-keyframe pose delta of Sec. III-C): pose_grad [V,6] (rho_x, rho_y, rho_z,
@@ -474,13 +483,6 @@ int gs_debug_expf(const float *x, float *y_spec, float *y_cuda, int64_t n, void 
 size_t gs_debug_scan_scratch_size(int64_t n);
 int gs_debug_scan_timeout(void *scratch, int64_t n, int32_t silent_partition, void *stream, int64_t *total);
 
-/* Bounded-wait check of the single-kernel binning (GS_SORT_ONESWEEP when it applies): runs
- * gs_bin_sort's cooperative kernel on the projected problem in `ws` with CTA `absent_cta` leaving
- * before its first grid barrier (-1: normal run) and a short spin limit (about a millisecond),
- * then synchronises and returns the recorded status: GS_ERR_TIMEOUT when the other CTAs gave up
- * waiting, GS_OK otherwise.  GS_ERR_INVALID_ARG when the single-kernel form does not apply to the
- * problem (its key capacity is too large) or absent_cta is not a CTA of the launch. */
-int gs_debug_bin_sort_absent_cta(const gs_problem *pb, void *ws, int32_t absent_cta, void *stream);
 
 #ifdef __cplusplus
 }

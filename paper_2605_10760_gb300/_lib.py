@@ -130,9 +130,11 @@ _SIGS = {
     "gs_render_fwd_l1": (C.c_int, [C.POINTER(gs_problem), _P, C.POINTER(gs_image), C.POINTER(gs_l1_target), _P]),
     "gs_render_bwd": (C.c_int, [C.POINTER(gs_problem), C.POINTER(gs_gaussians), _P, C.POINTER(gs_image),
                                 C.POINTER(gs_image_grad), C.POINTER(gs_grads), _P]),
+    "gs_render_bwd_composite": (C.c_int, [C.POINTER(gs_problem), _P, C.POINTER(gs_image), C.POINTER(gs_image_grad),
+                                          _P]),
+    "gs_project_bwd": (C.c_int, [C.POINTER(gs_problem), C.POINTER(gs_gaussians), _P, C.POINTER(gs_grads), _P]),
     "gs_pose_grad": (C.c_int, [C.POINTER(gs_problem), _P, _P, _P]),
-    "gs_normal_scratch_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
-    "gs_loss_normal": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, C.c_float, _P, _P, _P, _P]),
+    "gs_loss_normal": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, C.c_float, _P, _P, _P]),
     "gs_loss_l1": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, C.c_float, C.c_float, _P, _P, _P,
                              _P]),
     "gs_ssim_scratch_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),

@@ -284,7 +284,7 @@ int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stre
     a.proj = ws_ptr<float4>(ws, L.o_proj);
     a.touched = ws_ptr<uint32_t>(ws, L.o_touched);
     a.W = L.W; a.H = L.H;
-    a.tw = (float)L.tw; a.th = (float)L.th; a.Tx = (float)L.Tx; a.Ty = (float)L.Ty;
+    a.itw = 1.0f / (float)L.tw; a.ith = 1.0f / (float)L.th; a.Tx = (float)L.Tx; a.Ty = (float)L.Ty;
     a.near_plane = pb->params.near_plane; a.dil = pb->params.dilation; a.sigmas = pb->params.radius_sigmas;
     a.alpha_min = pb->params.alpha_min;
     a.tile_cnt = L.sort_mode == GS_SORT_TILE_BUCKET ? ws_ptr<uint32_t>(ws, L.o_tcnt) : nullptr;
@@ -312,7 +312,7 @@ static BinArgs make_bin_args(const Layout &L, void *ws) {
     a.srec = ws_ptr<float4>(ws, L.o_srec);
     a.st = ws_ptr<DevStatus>(ws, L.o_status);
     a.V = L.V; a.Tx = L.Tx; a.Ty = L.Ty; a.passes = L.passes;
-    a.tw = (float)L.tw; a.th = (float)L.th;
+    a.itw = 1.0f / (float)L.tw; a.ith = 1.0f / (float)L.th;
     a.P = L.P; a.cap = L.cap; a.sort_parts = L.sort_parts; a.max_chunks = L.max_chunks; a.G = L.G;
     a.fault_scan_part = -1;
     a.spin_limit = kSpinLimit;
@@ -379,17 +379,13 @@ int gs_render_fwd_l1(const gs_problem *pb, void *ws, const gs_image *out, const 
     return render_fwd_impl(pb, ws, out, l1, stream);
 }
 
-int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const gs_image *fwd,
-                  const gs_image_grad *dimg, const gs_grads *grads, void *stream) {
-    GS_RANGE("gs_render_bwd");
+int gs_render_bwd_composite(const gs_problem *pb, void *ws, const gs_image *fwd, const gs_image_grad *dimg,
+                            void *stream) {
+    GS_RANGE("gs_render_bwd_composite");
     Layout L;
     int rc = compute_layout(pb, &L);
     if (rc) return rc;
-    if (!ws_ok(ws) || !g || !fwd || !fwd->final_T || !fwd->last_idx || !dimg || !grads || !pb->cameras)
-        return GS_ERR_INVALID_ARG;
-    if (L.N > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacities || !grads->colors))
-        return GS_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
+    if (!ws_ok(ws) || !fwd || !fwd->final_T || !fwd->last_idx || !dimg) return GS_ERR_INVALID_ARG;
     BwdArgs a;
     a.srec = ws_ptr<const float4>(ws, L.o_srec);
     a.ranges = ws_ptr<const uint32_t>(ws, L.o_ranges);
@@ -401,8 +397,17 @@ int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const g
     const gs_params &p = pb->params;
     a.amax = p.alpha_max; a.amin = p.alpha_min;
     a.bg0 = p.bg[0]; a.bg1 = p.bg[1]; a.bg2 = p.bg[2];
-    rc = launch_render_bwd(L.tw, L.th, L.nb, a, s);
+    return launch_render_bwd(L.tw, L.th, L.nb, a, (cudaStream_t)stream);
+}
+
+int gs_project_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const gs_grads *grads, void *stream) {
+    GS_RANGE("gs_project_bwd");
+    Layout L;
+    int rc = compute_layout(pb, &L);
     if (rc) return rc;
+    if (!ws_ok(ws) || !g || !grads || !pb->cameras) return GS_ERR_INVALID_ARG;
+    if (L.N > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacities || !grads->colors))
+        return GS_ERR_INVALID_ARG;
     if (L.P == 0) return GS_OK;
     ProjBwdArgs b;
     b.views = ws_ptr<ViewEntry>(ws, L.o_views);
@@ -415,9 +420,18 @@ int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const g
     b.g_op = grads->opacities; b.g_col = grads->colors;
     b.pose_part = ws_ptr<float>(ws, L.o_pose_part);
     b.W = L.W; b.H = L.H;
-    b.dil = p.dilation;
-    launch_project_bwd(L, b, s);
+    b.dil = pb->params.dilation;
+    launch_project_bwd(L, b, (cudaStream_t)stream);
     return check_launch();
+}
+
+int gs_render_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const gs_image *fwd,
+                  const gs_image_grad *dimg, const gs_grads *grads, void *stream) {
+    GS_RANGE("gs_render_bwd");
+    if (!g || !grads || !pb || !pb->cameras) return GS_ERR_INVALID_ARG;
+    const int rc = gs_render_bwd_composite(pb, ws, fwd, dimg, stream);
+    if (rc) return rc;
+    return gs_project_bwd(pb, g, ws, grads, stream);
 }
 
 int gs_pose_grad(const gs_problem *pb, void *ws, float *pose_grad, void *stream) {
@@ -442,22 +456,16 @@ int gs_loss_l1(int32_t views, int32_t width, int32_t height, const float *rgb, c
                           (cudaStream_t)stream);
 }
 
-size_t gs_normal_scratch_size(int32_t views, int32_t width, int32_t height) {
-    if (views < 1 || width < 1 || height < 1) return 0;
-    return normal_scratch_bytes(views, width, height);
-}
-
 int gs_loss_normal(int32_t views, int32_t width, int32_t height, const float *depth, const float *prior,
-                   const gs_camera *cams, float weight, float *d_depth, double *loss, void *scratch, void *stream) {
+                   const gs_camera *cams, float weight, float *d_depth, double *loss, void *stream) {
     GS_RANGE("gs_loss_normal");
     if (views < 1 || views > GS_MAX_VIEWS || width < 1 || height < 1 || width > 16384 || height > 16384 || !depth ||
-        !prior || !cams || !d_depth || !loss || !ws_ok(scratch) || !(weight == weight))
+        !prior || !cams || !d_depth || !loss || !(weight == weight))
         return GS_ERR_INVALID_ARG;
     NormalArgs a;
     a.depth = depth;
     a.prior = prior;
     a.cams = cams;
-    a.scratch = static_cast<float *>(scratch);
     a.d_depth = d_depth;
     a.loss = loss;
     a.V = views;

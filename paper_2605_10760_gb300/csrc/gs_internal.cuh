@@ -116,25 +116,28 @@ struct SpecProj {
 };
 
 // Tile rectangle of the bounding square [m - r, m + r] (x1, y1 exclusive), clamped to the grid.
-__device__ __forceinline__ void spec_rect(float mx, float my, float rf, float tw, float th, float Tx, float Ty,
+// itw, ith are 1/tile_w and 1/tile_h: tile sizes are powers of two (16, 8, 32), so multiplying by
+// the exact reciprocal rounds exactly like the division by the tile size.
+__device__ __forceinline__ void spec_rect(float mx, float my, float rf, float itw, float ith, float Tx, float Ty,
                                           int &x0, int &x1, int &y0, int &y1) {
-    float fx0 = fminf(fmaxf(floorf(fp::div(fp::sub(mx, rf), tw)), 0.0f), Tx);
-    float fx1 = fminf(fmaxf(fp::add(floorf(fp::div(fp::add(mx, rf), tw)), 1.0f), 0.0f), Tx);
-    float fy0 = fminf(fmaxf(floorf(fp::div(fp::sub(my, rf), th)), 0.0f), Ty);
-    float fy1 = fminf(fmaxf(fp::add(floorf(fp::div(fp::add(my, rf), th)), 1.0f), 0.0f), Ty);
+    float fx0 = fminf(fmaxf(floorf(fp::mul(fp::sub(mx, rf), itw)), 0.0f), Tx);
+    float fx1 = fminf(fmaxf(fp::add(floorf(fp::mul(fp::add(mx, rf), itw)), 1.0f), 0.0f), Tx);
+    float fy0 = fminf(fmaxf(floorf(fp::mul(fp::sub(my, rf), ith)), 0.0f), Ty);
+    float fy1 = fminf(fmaxf(fp::add(floorf(fp::mul(fp::add(my, rf), ith)), 1.0f), 0.0f), Ty);
     x0 = (int)fx0; x1 = (int)fx1; y0 = (int)fy0; y1 = (int)fy1;
 }
 
 // EWA projection of one Gaussian into one view (the FP32 decision chain).
 //   p_c = R mu + t; unit quaternion -> rotation Rq; M = Rq diag(exp(l));
 //   J = [[fx/z, 0, -fx tx/z], [0, fy/z, -fy ty/z]] with tx, ty = x/z, y/z clamped to
-//   +-0.65 W/fx, +-0.65 H/fy; U = (J R) M; Sigma_2 = U U^T + dilation I; conic = Sigma_2^-1;
+//   +-limx, +-limy (limx = fl(fl(0.65 W) / fx), limy likewise: per-view constants the caller
+//   computes once); U = (J R) M; Sigma_2 = U U^T + dilation I; conic = Sigma_2^-1;
 //   mean2D = (fx x/z + cx, fy y/z + cy); radius = ceil(sigmas sqrt(lambda_max)).
 __device__ __forceinline__ SpecProj spec_project(const float *R, const float *t, float fx, float fy, float cx,
-                                                 float cy, int W, int H, float tw, float th, float Tx, float Ty,
-                                                 float near_plane, float dil, float sigmas, float m0, float m1,
-                                                 float m2, float l0, float l1, float l2, float qw, float qx,
-                                                 float qy, float qz) {
+                                                 float cy, float limx, float limy, float itw, float ith, float Tx,
+                                                 float Ty, float near_plane, float dil, float sigmas, float m0,
+                                                 float m1, float m2, float l0, float l1, float l2, float qw,
+                                                 float qx, float qy, float qz) {
     using namespace fp;
     SpecProj o;
     o.visible = false;
@@ -171,8 +174,6 @@ __device__ __forceinline__ SpecProj spec_project(const float *R, const float *t,
         M[3 * j + 2] = mul(Rq[3 * j + 2], s2);
     }
     float iz = div(1.0f, zc);
-    float limx = div(mul(0.65f, (float)W), fx);
-    float limy = div(mul(0.65f, (float)H), fy);
     float ux = mul(xc, iz), uy = mul(yc, iz);
     float tx = fminf(limx, fmaxf(-limx, ux));
     float ty = fminf(limy, fmaxf(-limy, uy));
@@ -204,7 +205,7 @@ __device__ __forceinline__ SpecProj spec_project(const float *R, const float *t,
     float disc = fma(mid, mid, -det);
     float lam = add(mid, sqrt(fmaxf(0.0f, disc)));
     o.rf = ceilf(mul(sigmas, sqrt(lam)));
-    spec_rect(o.mx, o.my, o.rf, tw, th, Tx, Ty, o.x0, o.x1, o.y0, o.y1);
+    spec_rect(o.mx, o.my, o.rf, itw, ith, Tx, Ty, o.x0, o.x1, o.y0, o.y1);
     o.visible = (o.x1 > o.x0) && (o.y1 > o.y0);
     return o;
 }

@@ -13,7 +13,7 @@ struct ProjArgs {
     float4 *proj;               // [P,3] float4
     uint32_t *touched;          // [P]
     int W, H;
-    float tw, th, Tx, Ty;
+    float itw, ith, Tx, Ty;     // 1 / tile size (exact: tile sizes are powers of two), tiles per row / column
     float near_plane, dil, sigmas, alpha_min;
     uint32_t *tile_cnt;         // [G] key count per global tile (tile-bucket binning), else null
     int Txi, Ty_i;
@@ -51,7 +51,7 @@ struct BinArgs {
     float4 *srec;                      // [cap,3] records in list order
     DevStatus *st;
     int V, Tx, Ty, passes;
-    float tw, th;
+    float itw, ith;                    // 1 / tile size (exact: tile sizes are powers of two)
     long long P, cap, sort_parts, max_chunks, G;
     int fault_scan_part;               // -1 normally; >= 0: that scan partition never publishes
     void *clear_begin;                 // scan_state, hist, sort_state and ranges: one span cleared before
@@ -138,13 +138,11 @@ struct NormalArgs {
     const float *depth;                // [V,H,W]
     const float *prior;                // [V,3,H,W] unit normals, camera frame
     const gs_camera *cams;             // [V] (intrinsics read)
-    float *scratch;                    // [V,6,H,W] dL/dt_x, dL/dt_y per pixel
     float *d_depth;                    // [V,H,W], +=
     double *loss;                      // +=
     int V, W, H;
     float scale;                       // weight / (V H W)
 };
-size_t normal_scratch_bytes(int V, int W, int H);
 int launch_loss_normal(const NormalArgs &a, cudaStream_t s);
 
 // Eq. 12 photometric residual blocks (gs_photometric.cu)

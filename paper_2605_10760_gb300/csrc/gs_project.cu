@@ -3,7 +3,9 @@
 // Forward: the FP32 decision chain of gs_internal.cuh; one thread per pair, grid (chunk, view).
 // Backward: the chain rule through the same projection in FP32 value arithmetic, accumulating
 // dL/d(mean, log-scale, quaternion, opacity, colour) with atomics (several views of one scene add
-// into the same Gaussian) and the per-view SE(3) pose gradient as one partial sum per block.
+// into the same Gaussian; a reduction is issued without waiting for a result, which also makes it
+// cheaper than a load and a store where no two views share a Gaussian) and the per-view SE(3) pose
+// gradient as one partial sum per block.
 #include "gs_kernels.cuh"
 
 namespace gs {
@@ -13,9 +15,14 @@ namespace gs {
 __global__ void __launch_bounds__(kChunk) k_project(ProjArgs a) {
     const int v = blockIdx.y;
     __shared__ ViewEntry s_ve;
-    __shared__ float s_cam[16];
+    __shared__ float s_cam[18];   // R, t, fx, fy, cx, cy, then the view's Jacobian clamp limits
     if (threadIdx.x == 0) s_ve = a.views[v];
     if (threadIdx.x < 16) s_cam[threadIdx.x] = reinterpret_cast<const float *>(a.cams + v)[threadIdx.x];
+    if (threadIdx.x == 32) {      // once per view and block, the same operations as the per-pair chain
+        const gs_camera &c = a.cams[v];
+        s_cam[16] = fp::div(fp::mul(0.65f, (float)a.W), c.fx);
+        s_cam[17] = fp::div(fp::mul(0.65f, (float)a.H), c.fy);
+    }
     __syncthreads();
     const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
     const bool in = i < s_ve.count;
@@ -28,9 +35,9 @@ __global__ void __launch_bounds__(kChunk) k_project(ProjArgs a) {
         const float *mu = a.means + 3 * gi;
         const float *ls = a.log_scales + 3 * gi;
         const float4 q = __ldg(reinterpret_cast<const float4 *>(a.quats) + gi);
-        o = spec_project(s_cam, s_cam + 9, s_cam[12], s_cam[13], s_cam[14], s_cam[15], a.W, a.H, a.tw, a.th, a.Tx,
-                         a.Ty, a.near_plane, a.dil, a.sigmas, __ldg(mu), __ldg(mu + 1), __ldg(mu + 2), __ldg(ls),
-                         __ldg(ls + 1), __ldg(ls + 2), q.x, q.y, q.z, q.w);
+        o = spec_project(s_cam, s_cam + 9, s_cam[12], s_cam[13], s_cam[14], s_cam[15], s_cam[16], s_cam[17],
+                         a.itw, a.ith, a.Tx, a.Ty, a.near_plane, a.dil, a.sigmas, __ldg(mu), __ldg(mu + 1),
+                         __ldg(mu + 2), __ldg(ls), __ldg(ls + 1), __ldg(ls + 2), q.x, q.y, q.z, q.w);
     }
     uint32_t cnt = 0;
     if (o.visible) {
@@ -76,10 +83,15 @@ __device__ __forceinline__ float warp_sum(float x) {
 __global__ void __launch_bounds__(kChunk) k_project_bwd(ProjBwdArgs a) {
     const int v = blockIdx.y;
     __shared__ ViewEntry s_ve;
-    __shared__ float s_cam[16];
+    __shared__ float s_cam[18];
     __shared__ float s_red[kChunk / 32][6];
     if (threadIdx.x == 0) s_ve = a.views[v];
     if (threadIdx.x < 16) s_cam[threadIdx.x] = reinterpret_cast<const float *>(a.cams + v)[threadIdx.x];
+    if (threadIdx.x == 32) {      // the forward's clamp limits, the same operations
+        const gs_camera &c = a.cams[v];
+        s_cam[16] = fp::div(fp::mul(0.65f, (float)a.W), c.fx);
+        s_cam[17] = fp::div(fp::mul(0.65f, (float)a.H), c.fy);
+    }
     __syncthreads();
     if ((long long)blockIdx.x * kChunk >= s_ve.count) return;   // whole block idle: no partial slot
     const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
@@ -119,8 +131,7 @@ __global__ void __launch_bounds__(kChunk) k_project_bwd(ProjBwdArgs a) {
                 for (int k = 0; k < 3; ++k) M[3 * j + k] = Rq[3 * j + k] * s[k];
             // clamp decisions as in the forward decision chain
             const float izs = fp::div(1.0f, zc);
-            const float limx = fp::div(fp::mul(0.65f, (float)a.W), fx);
-            const float limy = fp::div(fp::mul(0.65f, (float)a.H), fy);
+            const float limx = s_cam[16], limy = s_cam[17];
             const float uxs = fp::mul(xc, izs), uys = fp::mul(yc, izs);
             const bool clx = (uxs < -limx) || (uxs > limx);
             const bool cly = (uys < -limy) || (uys > limy);

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_scan_emit(BinArgs a) {
             const long long f = pbase + li;
             const float4 r0 = a.proj[3 * f], r1 = a.proj[3 * f + 1];
             int x0, x1, y0, y1;
-            spec_rect(r0.x, r0.y, r1.w, a.tw, a.th, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
+            spec_rect(r0.x, r0.y, r1.w, a.itw, a.ith, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
             const int v = view_of_pair(a.views, a.V, f);
             if ((uint32_t)((x1 - x0) * (y1 - y0)) != b1 - b0 || x1 <= x0) record_error(a.st, GS_ERR_DEVICE_FAULT, 3);
             es.g0[li] = (uint32_t)((unsigned long long)v * a.Tx * a.Ty + (unsigned long long)(y0 * a.Tx + x0));
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(kChunk) k_emit_bucket(BinArgs a) {
     unsigned long long word = 0;
     if (vis) {
         const float4 r0 = a.proj[3 * f], r1 = a.proj[3 * f + 1];
-        spec_rect(r0.x, r0.y, r1.w, a.tw, a.th, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
+        spec_rect(r0.x, r0.y, r1.w, a.itw, a.ith, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
         word = ((unsigned long long)__float_as_uint(r1.z) << 32) | (unsigned long long)(uint32_t)f;
     }
     uint64_t *keys = a.keys[0];

@@ -215,6 +215,22 @@ class Problem:
                                        _stream()), "gs_render_bwd")
         return grads
 
+    def render_bwd_composite(self, img: dict, d_rgb=None, d_depth=None, d_alpha=None):
+        """The compositing adjoint alone (2-D gradients into the workspace)."""
+        fi = L.gs_image(None, None, None, _ptr(img["final_T"]), _ptr(img["last_idx"]))
+        di = L.gs_image_grad(_ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha))
+        L.check(self.lib.gs_render_bwd_composite(self.pb, _ptr(self.ws), C.byref(fi), C.byref(di), _stream()),
+                "gs_render_bwd_composite")
+
+    def project_bwd(self, g: Gaussians, grads: Gaussians) -> Gaussians:
+        """The projection adjoint alone, accumulated into grads (after render_bwd_composite)."""
+        gs_ = g.struct()
+        go = L.gs_grads(*[getattr(grads, k).data_ptr() for k in ("means", "log_scales", "quats", "opacities",
+                                                                   "colors")])
+        L.check(self.lib.gs_project_bwd(self.pb, C.byref(gs_), _ptr(self.ws), C.byref(go), _stream()),
+                "gs_project_bwd")
+        return grads
+
     def pose_grad(self, out: torch.Tensor | None = None) -> torch.Tensor:
         out = out if out is not None else torch.empty(self.V, 6, device=self.device)
         L.check(self.lib.gs_pose_grad(self.pb, _ptr(self.ws), _ptr(out), _stream()), "gs_pose_grad")
@@ -252,12 +268,7 @@ def loss_l1(rgb, rgb_t, depth=None, depth_t=None, w_rgb=1.0, w_depth=0.0, d_rgb=
     return loss, d_rgb, d_depth
 
 
-def normal_scratch(V, H, W, device="cuda") -> torch.Tensor:
-    n = L.load().gs_normal_scratch_size(V, W, H)
-    return torch.empty(int(n), dtype=torch.uint8, device=device)
-
-
-def loss_normal(depth, prior, cams, weight=1e-2, d_depth=None, loss=None, scratch=None):
+def loss_normal(depth, prior, cams, weight=1e-2, d_depth=None, loss=None):
     """Normal term of the mapping loss (Eq. 4, lambda_n = 1e-2): weight * mean over all pixels of
     |1 - N_hat . N_bar| for the depth-induced normal N_hat and the prior N_bar [V,3,H,W].  ADDS the
     loss to `loss` and dL/d depth to `d_depth` (zero tensors are created when None); returns both."""
@@ -266,10 +277,8 @@ def loss_normal(depth, prior, cams, weight=1e-2, d_depth=None, loss=None, scratc
         d_depth = torch.zeros_like(depth)
     if loss is None:
         loss = torch.zeros(1, dtype=torch.float64, device=depth.device)
-    if scratch is None:
-        scratch = normal_scratch(V, H, W, depth.device)
     L.check(L.load().gs_loss_normal(V, W, H, _ptr(depth), _ptr(prior), _ptr(cams), float(weight), _ptr(d_depth),
-                                    _ptr(loss), _ptr(scratch), _stream()), "gs_loss_normal")
+                                    _ptr(loss), _stream()), "gs_loss_normal")
     return loss, d_depth
 
 

@@ -117,19 +117,14 @@ def test_follow_up_calls_reject_bad_arguments_without_launching(lib):
 
 
 def test_normal_loss_rejects_bad_arguments_without_launching(lib):
-    assert lib.gs_normal_scratch_size(2, 16, 8) == 24 * 2 * 16 * 8
-    assert lib.gs_normal_scratch_size(0, 16, 8) == 0
     one = C.c_void_p(1 << 20)
-    args = [one, one, one, C.c_float(0.01), one, one, one, None]   # depth, prior, cams, w, d_depth, loss, scratch
+    args = [one, one, one, C.c_float(0.01), one, one, None]   # depth, prior, cams, weight, d_depth, loss, stream
     assert lib.gs_loss_normal(0, 16, 8, *args) == L.GS_ERR_INVALID_ARG            # no views
     assert lib.gs_loss_normal(1, 0, 8, *args) == L.GS_ERR_INVALID_ARG             # empty image
     for k in (0, 1, 2, 4, 5):                                                      # a missing pointer
         bad = list(args)
         bad[k] = None
         assert lib.gs_loss_normal(1, 16, 8, *bad) == L.GS_ERR_INVALID_ARG
-    bad = list(args)
-    bad[6] = C.c_void_p((1 << 20) + 8)                                             # scratch not 256-B aligned
-    assert lib.gs_loss_normal(1, 16, 8, *bad) == L.GS_ERR_INVALID_ARG
     bad = list(args)
     bad[3] = C.c_float(float("nan"))                                               # weight
     assert lib.gs_loss_normal(1, 16, 8, *bad) == L.GS_ERR_INVALID_ARG

@@ -1,5 +1,5 @@
-"""GPU parity of the normal term of Eq. 4 (gs_loss_normal) against the FP64 oracle.  Kept in a
-file of its own that runs after the other GPU suites."""
+"""GPU parity of the normal term of Eq. 4 (gs_loss_normal) against the FP64 oracle, on images that
+are and are not multiples of the kernel's 32 x 8 pixel tile, down to images with no interior pixel."""
 import numpy as np
 import pytest
 
@@ -40,7 +40,7 @@ def _normal_case(rng, V, H, W):
     return depth.astype(np.float32), prior.astype(np.float32), intr.astype(np.float32).astype(np.float64), cams
 
 
-@pytest.mark.parametrize("V,H,W", [(2, 37, 53), (1, 680, 1200)])
+@pytest.mark.parametrize("V,H,W", [(2, 37, 53), (3, 9, 33), (1, 2, 3), (1, 680, 1200)])
 def test_normal_loss_matches_oracle(R, V, H, W):
     rng = np.random.default_rng(V * H + W)
     depth, prior, intr, cams = _normal_case(rng, V, H, W)

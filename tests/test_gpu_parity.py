@@ -156,10 +156,12 @@ def test_parity_tiles_longer_than_one_shared_memory_sort(R, mode):
     compare_all(gpu, orc)
 
 
-def test_parity_room500k_full_size(R):
-    """The benchmark workload (500k-Gaussian room, one 1200x680 view), compared in full."""
+@pytest.mark.parametrize("mode", SORT_MODES)
+def test_parity_room500k_full_size(R, mode):
+    """The benchmark workload (500k-Gaussian room, one 1200x680 view) with about the benchmark's key
+    capacity (270k keys), compared in full, in both binning modes."""
     wl = S.workload("room500k")
-    gpu = run_gpu(R, wl)
+    gpu = run_gpu(R, wl, params=R.default_params(sort_mode=mode), key_capacity=400_000)
     assert gpu["rc"] == 0 and gpu["rc_end"] == 0
     orc = run_oracle(wl, up=gpu["up"])
     compare_all(gpu, orc)
