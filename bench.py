@@ -128,9 +128,10 @@ class Clocks:
 class Pipeline:
     """One fwd+bwd mapping step of a problem, every stage a libgs call."""
 
-    def __init__(self, R, S, wl, views, target_seed=21, key_capacity=None):
+    def __init__(self, R, S, wl, views, target_seed=21, key_capacity=None, w_depth=0.1, uniform_target=False):
         import torch
         self.R, self.torch = R, torch
+        self.w_depth = w_depth
         sov = wl.scene_of_view[views]
         vb = wl.scene_offsets[sov]
         vc = wl.scene_offsets[sov + 1] - vb
@@ -139,7 +140,8 @@ class Pipeline:
         self.g = R.Gaussians.from_scene(wl.scene)
         V, H, W = len(views), wl.height, wl.width
         self.V = V
-        tgt = np.stack([S.smooth_image(W, H, target_seed + v) for v in range(V)])
+        tgt = np.stack([S.uniform_image(W, H, target_seed + v) if uniform_target else
+                        S.smooth_image(W, H, target_seed + v) for v in range(V)])
         dtg = np.stack([S.smooth_image(W, H, target_seed + 100 + v, channels=1, lo=0.5, hi=5.0)[0] for v in range(V)])
         self.rgb_t = torch.from_numpy(tgt).cuda()
         self.depth_t = torch.from_numpy(dtg).cuda()
@@ -168,10 +170,10 @@ class Pipeline:
             lambda: pb.project(self.g),
             lambda: pb.bin_sort(),
             # forward compositing with the L1 loss and its gradient in the same kernel's epilogue
-            lambda: pb.render_fwd_l1(self.img, self.rgb_t, self.depth_t, 1.0, 0.1, self.d_rgb, self.d_depth,
-                                     self.loss),
-            lambda: (zero and self.zero_grads(),
-                     pb.render_bwd(self.g, self.img, self.d_rgb, self.d_depth, None, self.grads)),
+            lambda: pb.render_fwd_l1(self.img, self.rgb_t, self.depth_t, 1.0, self.w_depth, self.d_rgb,
+                                     self.d_depth, self.loss),
+            lambda: pb.render_bwd_composite(self.img, self.d_rgb, self.d_depth, None),
+            lambda: (zero and self.zero_grads(), pb.project_bwd(self.g, self.grads)),
             lambda: pb.pose_grad(self.pose),
         ]
 
@@ -201,7 +203,8 @@ class Pipeline:
                 fn()
             self.graphs.append(gr)
         # the whole step: the gradient zeroing runs on a forked branch of the graph, concurrently
-        # with the projection, the sort and the forward (it only has to finish before the backward)
+        # with the projection, the sort and the forward (joined before the backward: a zeroing
+        # still running beside the persistent compositing adjoint would wait for free SMs)
         self.whole = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
         with torch.cuda.graph(self.whole):
@@ -235,7 +238,7 @@ class Pipeline:
             ev[len(STAGES)].record()
 
 
-STAGES = ["project", "bin_sort", "render_fwd_l1", "render_bwd", "pose_grad"]
+STAGES = ["project", "bin_sort", "render_fwd_l1", "render_bwd", "project_bwd", "pose_grad"]
 
 
 def l2_flush(buf):
@@ -351,6 +354,23 @@ def time_e2e(pipes, steps, torch, flush_buf):
     run(4)                                             # warm-up
     ms = run(steps)
     return ms, h2d, d2h
+
+
+def cloud_bench(R, S, torch, flush_buf, steps=30, warmup=5):
+    """Config 1 (cloud10k: 10k Gaussians, one 320x240 view, L1 against a U[0,1] target, pose
+    gradient): the same step as the headline, replayed as one graph with L2 flushed before each."""
+    wl = workload(S, "cloud10k")
+    pipe = Pipeline(R, S, wl, [0], target_seed=2, w_depth=0.0, uniform_target=True)
+    pipe.capture()
+    step_ms, _, _ = time_steps(pipe, steps, warmup, flush_buf, torch, graphs=True, whole=True)
+    rc, _ = pipe.pb.check_status()
+    ms = statistics.median(step_ms)
+    st = pipe.pb.stats()
+    out = {"workload": "cloud10k: 10k Gaussians, 1 view 320x240, L1(rgb) vs a U[0,1] target + pose gradient",
+           "ms_per_step": ms, "views_per_s": 1e3 / ms, "keys": st["num_keys"], "fwd_pairs": st["fwd_pairs"],
+           "status": rc}
+    del pipe
+    return out
 
 
 def batched_speedup(R, S, torch, flush_buf, reps=3):
@@ -484,8 +504,8 @@ BYTES_PHO = 28
 
 def normal_bench(R, S, torch, reps=20):
     """Normal term of Eq. 4 over 8 views at 1200x680: a smooth synthetic depth surface per view and a
-    random camera-facing unit prior; inputs, scratch and gradient (~290 MB) exceed L2, so nothing is
-    flushed between calls."""
+    random camera-facing unit prior; inputs and gradient (~130 MB) exceed L2, and the L2 is flushed
+    between timed calls."""
     V, H, W = 8, 680, 1200
     rng = np.random.default_rng(31)
     y, x = np.mgrid[0:H, 0:W].astype(np.float32)
@@ -501,30 +521,31 @@ def normal_bench(R, S, torch, reps=20):
     d, p, c = t(depth), t(prior), t(cams)
     d_depth = torch.zeros_like(d)
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
-    scratch = R.normal_scratch(V, H, W)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(3):
-        R.loss_normal(d, p, c, 1e-2, d_depth, loss, scratch)
+        R.loss_normal(d, p, c, 1e-2, d_depth, loss)
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     n0 = R.L.load().gs_launch_count()
-    ev0.record(st)
-    for _ in range(reps):
-        R.loss_normal(d, p, c, 1e-2, d_depth, loss, scratch)
-    ev1.record(st)
+    for e0, e1 in evs:
+        l2_flush(flush)
+        e0.record(st)
+        R.loss_normal(d, p, c, 1e-2, d_depth, loss)
+        e1.record(st)
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / reps
+    ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in evs)
     px = V * H * W
-    # depth 4 B + prior 12 B read, adjoints 24 B written and read back, d_depth 4 B read + 4 B written
-    ach = 72.0 * px / (ms * 1e-3) / 1e9
+    # depth 4 B + prior 12 B read, d_depth 4 B read + 4 B written
+    ach = 24.0 * px / (ms * 1e-3) / 1e9
     peaks = _peaks()
     return {"workload": "8 views 1200x680, smooth synthetic depth, random camera-facing prior, lambda_n 1e-2",
             "ms_per_call": ms, "pixels_per_s": px / (ms * 1e-3),
             "launches_per_call": (R.L.load().gs_launch_count() - n0) // reps,
             "loss_per_call": loss.item() / (reps + 3),
-            "roofline": {"kernel": "k_normal_terms + k_normal_gather", "bound": "hbm", "achieved": ach,
+            "roofline": {"kernel": "k_normal", "bound": "hbm", "achieved": ach,
                          "unit": "GB/s", "peak": peaks["hbm_gbs"], "frac": ach / peaks["hbm_gbs"],
-                         "bytes_per_pixel": 72}}
+                         "bytes_per_pixel": 24}}
 
 
 def pho_bench(R, S, torch, reps=20):
@@ -669,47 +690,78 @@ def fused_map(R, S, torch, steps=3):
     return out
 
 
-def cpu_baseline(seconds=12.0):
-    """The FP64 oracle as it stands, timed on this host's cores on the same workload."""
+# CPU-baseline samples: (workload, views, loss weight of depth, label).  The agents8x4 sample is
+# the first camera of four of its rooms (50k, 120k, 200k and 330k Gaussians): a labelled subset.
+CPU_SAMPLES = {
+    "cloud10k": (None, 0.0, "cloud10k: 10k Gaussians, 1 view 320x240, L1(rgb)"),
+    "room500k": (None, 0.1, "room500k: 500k-Gaussian room, 1 view 1200x680, L1(rgb) + 0.1 L1(depth)"),
+    "agents8x4": ([0, 9, 18, 27], 0.1, "agents8x4 subset: views 0, 9, 18, 27 (rooms of 50k, 120k, 200k, 330k "
+                                       "Gaussians) at 1200x680, L1(rgb) + 0.1 L1(depth)"),
+}
+
+
+def oracle_pass(S, wl, views, w_depth, seed=21):
+    """One full oracle fwd + bwd pass over the given views: a closure to time."""
     from oracle import losses as OL
     from oracle.oracle import Oracle
-    from paper_2605_10760_gb300 import scenes as S
-    wl = S.workload("room500k")
+    views = list(range(len(wl.cameras))) if views is None else list(views)
     W, H = wl.width, wl.height
-    tgt = S.smooth_image(W, H, 21)[None]
-    dtg = S.smooth_image(W, H, 121, channels=1, lo=0.5, hi=5.0)
+    tgt = np.stack([S.smooth_image(W, H, seed + i) for i in range(len(views))])
+    dtg = np.stack([S.smooth_image(W, H, seed + 100 + i, channels=1, lo=0.5, hi=5.0)[0] for i in range(len(views))])
+
+    def one():
+        orc = Oracle.from_workload(wl, views=views)
+        fw = orc.forward()
+        _, g_rgb, g_d = OL.mapping_l1_loss(fw["rgb"], tgt, fw["depth"], dtg, 1.0, w_depth)
+        orc.backward(g_rgb, g_d)
+    return one, len(views)
+
+
+def cpu_sample(name, seconds):
+    """Time the oracle as it stands on one CPU sample; the process's OMP_NUM_THREADS sets its threads."""
+    from paper_2605_10760_gb300 import scenes as S
+    views, w_depth, label = CPU_SAMPLES[name]
+    wl = S.workload(name)
+    one, nv = oracle_pass(S, wl, views, w_depth)
     n, t0 = 0, time.perf_counter()
     while True:
-        orc = Oracle.from_workload(wl)
-        fw = orc.forward()
-        _, g_rgb, g_d = OL.mapping_l1_loss(fw["rgb"], tgt, fw["depth"], dtg, 1.0, 0.1)
-        orc.backward(g_rgb, g_d)
+        one()
         n += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": n / el, "unit": "views/s", "cores": threads, "kind": "oracle",
-            "sample": "%d full fwd+bwd passes of the room500k view (FP64 values, FP32 decisions)" % n}
+    return {"value": n * nv / el, "unit": "views/s", "cores": threads, "kind": "oracle",
+            "sample": "%d fwd+bwd pass(es) of %s (FP64 values, FP32 decisions)" % (n, label)}
+
+
+def cpu_baseline(seconds=4.0):
+    """The FP64 oracle as it stands, timed on this host's cores: configs 1-3 on all cores and on one
+    core, each sample in a child process whose OMP_NUM_THREADS is the core count (the oracle's
+    OpenMP pool is sized once per process).  The headline figure is room500k on all cores."""
+    allc = os.cpu_count() or 1
+    out = {"all_cores": {}, "one_core": {}}
+    for key, threads in (("all_cores", allc), ("one_core", 1)):
+        for name in CPU_SAMPLES:
+            env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", name,
+                                "--cpu-seconds", str(seconds)], env=env, capture_output=True, text=True)
+            try:
+                out[key][name] = json.loads(r.stdout.strip().splitlines()[-1])
+            except (IndexError, ValueError):
+                out[key][name] = {"error": (r.stderr or r.stdout)[-300:]}
+    head = out["all_cores"].get("room500k", {})
+    return {"value": head.get("value"), "unit": "views/s", "cores": allc, "kind": "oracle",
+            "sample": head.get("sample"), **out}
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from oracle import losses as OL
-    from oracle.oracle import Oracle
     from paper_2605_10760_gb300 import scenes as S
     wl = S.workload("room500k")
-    W, H = wl.width, wl.height
-    tgt = S.smooth_image(W, H, 21)[None]
-    dtg = S.smooth_image(W, H, 121, channels=1, lo=0.5, hi=5.0)
-
-    def one():
-        orc = Oracle.from_workload(wl)
-        fw = orc.forward()
-        _, g_rgb, g_d = OL.mapping_l1_loss(fw["rgb"], tgt, fw["depth"], dtg, 1.0, 0.1)
-        orc.backward(g_rgb, g_d)
+    one, _ = oracle_pass(S, wl, None, 0.1)
 
     for _ in range(args.warmup):
         one()
@@ -739,9 +791,14 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the graph-loop and 4M/64-view measurements")
+    ap.add_argument("--cpu-sample", choices=sorted(CPU_SAMPLES), help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-seconds", type=float, default=4.0, help=argparse.SUPPRESS)
     ap.add_argument("--only", choices=["photometric", "normal", "fusion", "mapping", "refine", "fused", "batched"],
                     help="run one secondary measurement alone and print its JSON (not the headline line)")
     args = ap.parse_args()
+    if args.cpu_sample:       # child process of cpu_baseline(): one oracle timing, no GPU
+        print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_seconds)))
+        return 0
     if args.impl == "reference":
         return reference_arm(args)
     if args.only:
@@ -809,6 +866,7 @@ def main():
         "bin_sort": (P * 8 + K * 12 + passes * K * 24 + K * 8 + pipe.pb.V * 3225 * 8) if onesweep else
                     (pipe.pb.V * 3225 * 8 + vis * 32 + K * 12 + K * 116),
         "render_fwd_l1": npx * 48,
+        "project_bwd": P * 60,
         "pose_grad": 0,
     }
     fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s at max SM clock
@@ -825,6 +883,7 @@ def main():
         ach = alg_bytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": traffic.get(dom), "peak_note": "of %s" % peaks["src"]}
+    cloud = cloud_bench(R, S, torch, flush)
     batched = None if args.no_batched else batched_speedup(R, S, torch, flush)
     graph_loop = None if args.no_extra else mapping_graph(R, S, torch)
     refine = None if args.no_extra else refine_graph(R, S, torch)
@@ -856,6 +915,7 @@ def main():
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches_per_step * args.steps,
         "launches_per_step": launches_per_step,
+        "cloud10k": cloud,
         "batched": batched,
         "mapping_graph": graph_loop,
         "refine_graph": refine,

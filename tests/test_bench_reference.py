@@ -43,3 +43,15 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, ["--gpus", "2", "--steps", "1", "--warmup", "0"])
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+
+
+def test_cpu_baseline_sample_reports_its_thread_count():
+    """A CPU-baseline child (one oracle timing on one sample) prints views/s and the OMP thread count
+    it ran with; the benchmark runs one per config on all cores and on one core."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-sample", "cloud10k",
+                        "--cpu-seconds", "0.05"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["cores"] == 1 and d["kind"] == "oracle" and d["unit"] == "views/s" and d["value"] > 0
+    assert d["sample"].startswith("1 fwd+bwd pass(es) of cloud10k")

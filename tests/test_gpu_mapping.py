@@ -134,3 +134,102 @@ def test_floor4m_full_size_sampled_tiles(R):
         assert rel_l2(pose[v], bw["pose"][j]) <= TOL_GRAD
     others = [v for v in range(V) if v not in views]
     assert np.abs(pose[others]).max() == 0.0
+
+
+def test_room1m_full_size_iteration_sampled_tiles(R):
+    """The graph-captured mapping workload at full size (1M-Gaussian room, 8 views at 1200x680 in one
+    batched problem) for one iteration: tile lists, images, every Gaussian and pose gradient and the
+    in-kernel Adam step (config-4 learning rates, opacity through its logit) against the oracle on
+    24 sampled tiles of two views.  The upstream gradient is seeded and non-zero only on the sampled
+    tiles, so the oracle's tile-restricted backward is the exact expected gradient of every Gaussian
+    and pose.  The L1 + SSIM loss of the loop is checked at the same full size on seeded images of
+    the same shape (its inputs do not come from the GPU render)."""
+    from oracle import losses as OL
+    wl = S.workload("room1m")
+    V = len(wl.cameras)
+    H, W = wl.height, wl.width
+    # (a) the mapping loss at full size: 0.8 L1 + 0.2 (1 - SSIM) over [8, 3, 680, 1200]
+    rng = np.random.default_rng(4)
+    y = np.stack([S.uniform_image(W, H, 40 + v) for v in range(V)])
+    x = np.clip(y + rng.normal(0, 0.05, y.shape), 0, 1).astype(np.float32)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    loss, d_loss = R.loss_l1_ssim(t(x), t(y), 0.8, 0.2)
+    Lr, gr = OL.l1_ssim_loss(x, y, 0.8, 0.2)
+    assert abs(loss.item() - Lr) <= 1e-5 * abs(Lr)
+    assert rel_l2(d_loss.cpu().numpy(), gr) <= 1e-4
+    del d_loss
+    # (b) forward, backward, pose gradients and one Adam step of the 8-view problem
+    pb, g = gpu_problem(wl)
+    img = pb.forward_checked(g)
+    ws = pb.workspace()
+    Tx, Ty = pb.tiles
+    tpv = Tx * Ty
+    views = [1, 6]
+    sampled = {v: rng.choice(tpv, 24, replace=False) for v in views}
+    d_rgb = np.zeros((V, 3, H, W), np.float32)
+    d_depth = np.zeros((V, H, W), np.float32)
+    for v in views:
+        for tt in sampled[v]:
+            ty, tx = divmod(int(tt), Tx)
+            sl = (slice(ty * 16, min(H, ty * 16 + 16)), slice(tx * 16, min(W, tx * 16 + 16)))
+            d_rgb[v][(slice(None),) + sl] = rng.choice([-1.0, 1.0], (3,) + d_rgb[v][(0,) + sl].shape) * 1e-6
+            d_depth[v][sl] = rng.choice([-1.0, 1.0], d_depth[v][sl].shape) * 1e-7
+    grads = pb.render_bwd(g, img, t(d_rgb), t(d_depth), None)
+    pose = pb.pose_grad().cpu().numpy()
+    gpu_grads = {k: getattr(grads, k).cpu().numpy() for k in ("means", "log_scales", "quats", "opacities", "colors")}
+    lrs = {"means": 1.6e-4, "log_scales": 5e-3, "quats": 1e-3, "logit": 5e-2, "colors": 2.5e-3}
+    before = {k: getattr(g, k).cpu().numpy().astype(np.float64) for k in ("means", "log_scales", "quats", "colors")}
+    o0 = g.opacities.cpu().numpy().astype(np.float64)
+    adam = R.AdamState(g, lr=(lrs["means"], lrs["log_scales"], lrs["quats"], lrs["logit"], lrs["colors"]))
+    logit0 = adam.logits.cpu().numpy().astype(np.float64)
+    adam.apply(grads, zero_grads=True)
+    torch.cuda.synchronize()
+    assert pb.check_status()[0] == 0
+    ranges = ws["tile_ranges"].cpu().numpy().view(np.uint32)
+    vals = ws["sorted_vals"].cpu().numpy().view(np.uint32)
+    N = wl.scene.n
+    mask = np.zeros(len(views) * tpv, np.uint8)
+    for j, v in enumerate(views):
+        mask[j * tpv + sampled[v]] = 1
+    orc = Oracle.from_workload(wl, views=views, tile_mask=mask)
+    ob, fw = orc.bins(), orc.forward()
+    bw = orc.backward(d_rgb[views].astype(np.float64), d_depth[views].astype(np.float64))
+    last = img["last_idx"].cpu().numpy()
+    rgb = img["rgb"].cpu().numpy()
+    for j, v in enumerate(views):
+        for tt in sampled[v]:
+            gs_, ge_ = (int(u) for u in ranges[v * tpv + tt])
+            os_, oe_ = (int(u) for u in ob["ranges"][j * tpv + tt])
+            np.testing.assert_array_equal(vals[gs_:ge_].astype(np.int64) - v * N,
+                                          ob["vals"][os_:oe_].astype(np.int64) - j * N)
+            ty, tx = divmod(int(tt), Tx)
+            sl = (slice(ty * 16, min(H, ty * 16 + 16)), slice(tx * 16, min(W, tx * 16 + 16)))
+            np.testing.assert_array_equal(last[v][sl], fw["last"][j][sl])
+            assert np.abs(rgb[v][(slice(None),) + sl] - fw["rgb"][j][(slice(None),) + sl]).max() <= TOL_IMAGE
+    for k in ("means", "log_scales", "quats", "opacities", "colors"):
+        assert rel_l2(gpu_grads[k], bw[k]) <= TOL_GRAD, k
+    for j, v in enumerate(views):
+        assert rel_l2(pose[v], bw["pose"][j]) <= TOL_GRAD
+    assert np.abs(pose[[v for v in range(V) if v not in views]]).max() == 0.0
+    # Adam, first step from zero moments: m = 0.1 g, v = 0.001 g^2, theta -= lr g / (|g| + eps)
+    go = dict(bw)
+    go["logit"] = bw["opacities"] * o0 * (1 - o0)
+    after = {k: getattr(g, k).cpu().numpy().astype(np.float64) for k in ("means", "log_scales", "quats", "colors")}
+    after["logit"] = adam.logits.cpu().numpy().astype(np.float64)
+    before["logit"] = logit0
+    m_gpu = adam.m.cpu().numpy().astype(np.float64)
+    off = {"means": 0, "log_scales": 3 * N, "quats": 6 * N, "logit": 10 * N, "colors": 11 * N}
+    for k in ("means", "log_scales", "quats", "logit", "colors"):
+        gk = go[k].reshape(N, -1)
+        ref, m_ref, _ = OL.adam_step(before[k].reshape(N, -1), gk, 0.0, 0.0, 1, lrs[k])
+        mk = m_gpu[off[k]:off[k] + gk.size].reshape(gk.shape)
+        assert rel_l2(mk, m_ref) <= TOL_GRAD, k
+        # where the gradient is well above its FP32 noise its sign is certain and the update exact;
+        # everywhere else the step is bounded by the learning rate, and zero where nothing touched
+        sure = np.abs(gk) > 1e-3 * np.abs(gk).max()
+        a_k = after[k].reshape(N, -1)
+        assert sure.sum() > 1000, k
+        np.testing.assert_allclose(a_k[sure], ref[sure], rtol=1e-6, atol=1e-7 * lrs[k] / 1e-4)
+        assert np.all(np.abs(a_k - before[k].reshape(N, -1)) <= lrs[k] * (1 + 1e-5) + 1e-6 * np.abs(a_k))
+        untouched = np.all(gk == 0.0, axis=1)
+        np.testing.assert_array_equal(a_k[untouched], before[k].reshape(N, -1)[untouched].astype(np.float32))
