@@ -645,10 +645,15 @@ def fusion_bench(R, S, torch, voxel=0.05, k=3.0, stride=2, reps=3):
     kept = int(keep.sum().item())
     ms = {key: statistics.median(val) for key, val in t.items()}
     hbm = _peaks()["hbm_gbs"]
-    # streaming kernels: Sim(3) reads and writes 56 B per Gaussian; the keep pass reads a mean (12 B)
-    # and writes a flag (1 B) per Gaussian besides its two hash lookups
+    # Sim(3) reads and writes 56 B per Gaussian.  The keep pass reads a mean (12 B) and writes a
+    # flag (1 B) per Gaussian, and each distinct voxel of the borrowed means needs one 32-byte sector
+    # of each voxel table (256 MB each, far larger than L2, so a first probe is a random DRAM
+    # sector; Gaussians that share a voxel share its sectors)
     sim3_gbs = bor.n * 112 / (ms["sim3"] * 1e-3) / 1e9
-    keep_gbs = bor.n * 13 / (ms["keep"] * 1e-3) / 1e9
+    vk = np.floor(moved.means.cpu().numpy().astype(np.float64) / voxel).astype(np.int64)
+    distinct = int(np.unique(vk[:, 0] * (1 << 42) + vk[:, 1] * (1 << 21) + vk[:, 2]).size)
+    keep_bytes = bor.n * 13 + distinct * 64
+    keep_gbs = keep_bytes / (ms["keep"] * 1e-3) / 1e9
     rays = 8 * ((wl.width + stride - 1) // stride) * ((wl.height + stride - 1) // stride)
     return {"workload": "floor4m halves: 2M target / 2M borrowed Gaussians, 8 keyframes 1200x680 (stride 2), "
                         "voxel %.2f m, k = %g" % (voxel, k),
@@ -657,7 +662,9 @@ def fusion_bench(R, S, torch, voxel=0.05, k=3.0, stride=2, reps=3):
             "roofline": {"sim3": {"bound": "hbm", "achieved": sim3_gbs, "peak": hbm, "unit": "GB/s",
                                   "frac": sim3_gbs / hbm},
                          "keep": {"bound": "hbm", "achieved": keep_gbs, "peak": hbm, "unit": "GB/s",
-                                  "frac": keep_gbs / hbm},
+                                  "frac": keep_gbs / hbm, "bytes": keep_bytes, "distinct_voxels": distinct,
+                                  "note": "13 B per Gaussian + one 32-byte sector of each table per distinct "
+                                          "voxel (random DRAM sectors)"},
                          "occupied_gaussians_per_s": tgt.n / (ms["occupied"] * 1e-3),
                          "free_rays_per_s": rays / (ms["free"] * 1e-3),
                          "note": "hash insertion (occupied, free) is bound by L2 compare-and-swap traffic"}}

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kNormalThreads) k_normal(NormalArgs a) {
     const long long HW = (long long)a.H * a.W;
     const int tiles_x = (a.W + kNTW - 1) / kNTW, tiles_y = (a.H + kNTH - 1) / kNTH;
     const long long tiles = (long long)a.V * tiles_x * tiles_y;
-    double acc = 0.0;
+    double acc = 0.0;      // the CTA's loss, summed per item in FP32 then once per item in FP64
     NormalStage st;
     long long item = blockIdx.x;
     int v = 0, x0 = 0, y0 = 0;
@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(kNormalThreads) k_normal(NormalArgs a) {
         const gs_camera &cam = a.cams[cv];
         const float ifx = 1.0f / cam.fx, ify = 1.0f / cam.fy;
         __syncthreads();
+        float acc_item = 0.f;
         for (int i = threadIdx.x; i < kNGH * kNGW; i += kNormalThreads) {
             const int gy_ = i / kNGW, gx_ = i - gy_ * kNGW;
             const int x = cx0 - 1 + gx_, y = cy0 - 1 + gy_;
@@ -154,13 +155,15 @@ __global__ void __launch_bounds__(kNormalThreads) k_normal(NormalArgs a) {
                     const float3 tx = make_float3(dr * rxr - dl * rxl, (dr - dl) * ryc, dr - dl);
                     const float3 ty = make_float3((dd - du) * rxc, dd * ryd - du * ryu, dd - du);
                     const float3 u = nm_cross(ty, tx);
-                    const float nu = sqrtf(nm_dot(u, u));
-                    if (nu > 0.0f) {
-                        const float inu = 1.0f / nu;
+                    const float uu = nm_dot(u, u);
+                    // 1/|u| by the hardware reciprocal square root (a value, not a decision: the
+                    // validity test is on |u|^2 > 0, in FP32 like the oracle's |u| > 0)
+                    if (uu > 0.0f) {
+                        const float inu = rsqrtf(uu);
                         const float3 nh = make_float3(u.x * inu, u.y * inu, u.z * inu);
                         const float3 nb = make_float3(s_p[0][gy_][gx_], s_p[1][gy_][gx_], s_p[2][gy_][gx_]);
                         const float c = 1.0f - nm_dot(nh, nb);
-                        if (gx_ >= 1 && gx_ <= kNTW && gy_ >= 1 && gy_ <= kNTH) acc += (double)fabsf(c);   // own pixel
+                        if (gx_ >= 1 && gx_ <= kNTW && gy_ >= 1 && gy_ <= kNTH) acc_item += fabsf(c);   // own pixel
                         const float k = c > 0.f ? -a.scale : (c < 0.f ? a.scale : 0.f);   // -scale sign(c)
                         const float3 gn = make_float3(k * nb.x, k * nb.y, k * nb.z);
                         const float pn = nm_dot(nh, gn);
@@ -174,6 +177,7 @@ __global__ void __launch_bounds__(kNormalThreads) k_normal(NormalArgs a) {
             s_g[0][gy_][gx_] = gx.x; s_g[1][gy_][gx_] = gx.y; s_g[2][gy_][gx_] = gx.z;
             s_g[3][gy_][gx_] = gy.x; s_g[4][gy_][gx_] = gy.y; s_g[5][gy_][gx_] = gy.z;
         }
+        acc += (double)acc_item;
         __syncthreads();
         const int tx_ = threadIdx.x % kNTW, ty_ = threadIdx.x / kNTW;
         const int x = cx0 + tx_, y = cy0 + ty_;
@@ -193,8 +197,14 @@ __global__ void __launch_bounds__(kNormalThreads) k_normal(NormalArgs a) {
 }
 
 int launch_loss_normal(const NormalArgs &a, cudaStream_t s) {
+    // persistent: as many CTAs as are resident at once (a second wave would only add a tail)
+    static int occ = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_normal, kNormalThreads, 0) != cudaSuccess || b < 1) b = 1;
+        return b;
+    }();
     const long long tiles = (long long)a.V * ((a.W + kNTW - 1) / kNTW) * ((a.H + kNTH - 1) / kNTH);
-    const long long grid = std::max<long long>(1, std::min<long long>(tiles, (long long)device_sm_count() * 8));
+    const long long grid = std::max<long long>(1, std::min<long long>(tiles, (long long)device_sm_count() * occ));
     k_normal<<<(unsigned)grid, kNormalThreads, 0, s>>>(a);
     count_launches(1);
     return check_launch();
