@@ -194,6 +194,21 @@ int gs_check_status(const gs_problem *pb, void *ws, void *stream, int64_t *requi
 /* Synchronises `stream` and reads the statistics counters. */
 int gs_read_stats(const gs_problem *pb, void *ws, void *stream, gs_stats *out);
 
+/* Workspace guard blocks (no counterpart in the paper; a check of the library itself): 256-byte
+ * blocks of a fixed byte pattern, written by gs_workspace_init, follow every workspace buffer that
+ * kernels index with data (projection records, tile counts, both key and value buffers, the tile
+ * ranges and lists, the records in list order, the 2-D gradients, the pose partials).  This call
+ * synchronises `stream` and returns GS_OK when every block is intact, else GS_ERR_DEVICE_FAULT with
+ * *first_bad (may be NULL) = the index of the first changed block in that order. */
+int gs_check_guards(const gs_problem *pb, void *ws, void *stream, int32_t *first_bad);
+
+/* 1 in the bounds-checked build of the library (libgs_checked.so, compiled with GS_CHECKED=1):
+ * there every index a kernel takes from data (a record's pair index, a key's tile, a tile range,
+ * a scatter position, a bilinear tap) is compared with its buffer's length first, and a violation
+ * records GS_ERR_DEVICE_FAULT (read by gs_check_status) and skips the access instead of making it.
+ * 0 in the release build (libgs.so), where these comparisons are compiled out. */
+int32_t gs_checked_build(void);
+
 /* EWA projection of every (view, Gaussian) pair (Eq. 19 covariance form, world-to-camera poses
  * of Eq. 15): camera transform, 2-D conic with dilation, radius, tile rectangle, touched-tile
  * count; writes proj and tiles_touched in the workspace (and, with GS_SORT_TILE_BUCKET, the key

@@ -134,6 +134,8 @@ _SIGS = {
                                           _P]),
     "gs_project_bwd": (C.c_int, [C.POINTER(gs_problem), C.POINTER(gs_gaussians), _P, C.POINTER(gs_grads), _P]),
     "gs_pose_grad": (C.c_int, [C.POINTER(gs_problem), _P, _P, _P]),
+    "gs_check_guards": (C.c_int, [C.POINTER(gs_problem), _P, _P, C.POINTER(C.c_int32)]),
+    "gs_checked_build": (C.c_int32, []),
     "gs_loss_normal": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, C.c_float, _P, _P, _P]),
     "gs_loss_l1": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, C.c_float, C.c_float, _P, _P, _P,
                              _P]),
@@ -174,8 +176,14 @@ _SIGS = {
 _lib = None
 
 
+def variant() -> str:
+    """'checked' when GS_LIBGS_VARIANT=checked selects the bounds-checked build, else 'release'."""
+    return "checked" if os.environ.get("GS_LIBGS_VARIANT", "") == "checked" else "release"
+
+
 def lib_path() -> str:
-    return os.path.join(_HERE, "_build", "libgs.so")
+    name = "libgs_checked.so" if variant() == "checked" else "libgs.so"
+    return os.path.join(_HERE, "_build", name)
 
 
 def load(build_if_missing: bool = True):
@@ -187,7 +195,7 @@ def load(build_if_missing: bool = True):
     if build_if_missing:
         from . import build as _build
         try:
-            path = _build.build()
+            path = _build.build(variant=variant())
         except Exception as e:  # noqa: BLE001
             if not os.path.exists(path):
                 raise ImportError("libgs could not be built: %s" % e) from e

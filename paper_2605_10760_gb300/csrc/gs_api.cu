@@ -93,23 +93,38 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     L->sort_parts = std::max<long long>(1, (L->cap + sort_tile - 1) / sort_tile);
     long long chunks_total = 0;
     for (int v = 0; v < L->V; ++v) chunks_total += (pb->view_gauss_count[v] + kChunk - 1) / kChunk;
+    L->chunks_total = chunks_total;
     size_t o = 0;
+    int ng = 0;   // a guard block of kGuardBytes follows each buffer that kernels index with data
+    auto guard = [&]() {
+        if (ng < kNumGuards) L->o_guard[ng] = o;
+        ++ng;
+        o += kGuardBytes;
+    };
     L->o_status = o; o = align256(o + sizeof(DevStatus));
     L->o_views = o; o = align256(o + sizeof(ViewEntry) * L->V);
     L->o_proj = o; o = align256(o + sizeof(float) * 12 * (size_t)std::max<long long>(P, 1));
+    guard();
     L->o_touched = o; o = align256(o + sizeof(uint32_t) * (size_t)std::max<long long>(P, 1) + 64);
-    for (int k = 0; k < 2; ++k) { L->o_keys[k] = o; o = align256(o + sizeof(uint64_t) * (size_t)L->cap); }
-    for (int k = 0; k < 2; ++k) { L->o_vals[k] = o; o = align256(o + sizeof(uint32_t) * (size_t)L->cap); }
+    guard();
+    for (int k = 0; k < 2; ++k) { L->o_keys[k] = o; o = align256(o + sizeof(uint64_t) * (size_t)L->cap); guard(); }
+    for (int k = 0; k < 2; ++k) { L->o_vals[k] = o; o = align256(o + sizeof(uint32_t) * (size_t)L->cap); guard(); }
     // scan_state .. ranges are adjacent: the onesweep binning clears them with one memset
     L->o_scan_state = o; o = align256(o + sizeof(unsigned long long) * L->scan_parts);
     L->o_hist = o; o = align256(o + sizeof(uint32_t) * kMaxPasses * 256);
     L->o_sort_state = o; o = align256(o + sizeof(uint32_t) * 256 * (size_t)L->sort_parts * L->passes);
     L->o_ranges = o; o = align256(o + sizeof(uint32_t) * 2 * (size_t)L->G);
+    guard();
     L->o_tcnt = o; o = align256(o + sizeof(uint32_t) * ((size_t)L->G + 1) + 64);
     L->o_tlist = o; o = align256(o + sizeof(uint32_t) * (size_t)L->G);
+    guard();
     L->o_srec = o; o = align256(o + sizeof(float) * 12 * (size_t)L->cap);
+    guard();
     L->o_g2d = o; o = align256(o + sizeof(float) * 12 * (size_t)std::max<long long>(P, 1));
+    guard();
     L->o_pose_part = o; o = align256(o + sizeof(float) * 8 * (size_t)std::max<long long>(chunks_total, 1));
+    guard();
+    if (ng != kNumGuards) return GS_ERR_INVALID_ARG;   // the layout and kNumGuards disagree: a build error
     L->total = o;
     return GS_OK;
 }
@@ -196,6 +211,8 @@ int gs_workspace_init(const gs_problem *pb, void *ws, void *stream) {
         chunk += (ve[v].count + kChunk - 1) / kChunk;
     }
     if (cudaMemsetAsync(ws_ptr<void>(ws, L.o_status), 0, sizeof(DevStatus), s) != cudaSuccess) return GS_ERR_CUDA;
+    for (int k = 0; k < kNumGuards; ++k)
+        if (cudaMemsetAsync(ws_ptr<void>(ws, L.o_guard[k]), kGuardByte, kGuardBytes, s) != cudaSuccess) return GS_ERR_CUDA;
     ViewEntry *dst = ws_ptr<ViewEntry>(ws, L.o_views);
     for (int v0 = 0; v0 < L.V; v0 += 8) {
         ViewEntry e[8];
@@ -246,6 +263,58 @@ int gs_check_status(const gs_problem *pb, void *ws, void *stream, int64_t *requi
     return h.code;
 }
 
+}  // extern "C"
+
+namespace gs {
+
+struct GuardPtrs {
+    const uint32_t *p[kNumGuards];
+};
+
+// one CTA: thread t compares word t of every guard block with the fill pattern
+__global__ void k_check_guards(GuardPtrs g, int32_t *bad) {
+    const uint32_t want = 0x01010101u * (uint32_t)kGuardByte;
+    for (int k = 0; k < kNumGuards; ++k)
+        for (int t = threadIdx.x; t < (int)(kGuardBytes / 4); t += blockDim.x)
+            if (g.p[k][t] != want) atomicMin(bad, k);
+}
+
+int run_check_guards(const unsigned char *const *guards, DevStatus *st, int32_t *first_bad, cudaStream_t s) {
+    GuardPtrs g;
+    for (int k = 0; k < kNumGuards; ++k) g.p[k] = reinterpret_cast<const uint32_t *>(guards[k]);
+    const int32_t none = kNumGuards;
+    if (cudaMemcpyAsync(&st->guard_bad, &none, sizeof(none), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    k_check_guards<<<1, 64, 0, s>>>(g, &st->guard_bad);
+    count_launches(1);
+    int32_t h = none;
+    if (cudaMemcpyAsync(&h, &st->guard_bad, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GS_ERR_CUDA;
+    *first_bad = h < kNumGuards ? h : -1;
+    return GS_OK;
+}
+
+}  // namespace gs
+
+extern "C" {
+
+int gs_check_guards(const gs_problem *pb, void *ws, void *stream, int32_t *first_bad) {
+    Layout L;
+    int rc = compute_layout(pb, &L);
+    if (rc) return rc;
+    if (!ws_ok(ws)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned char *g[kNumGuards];
+    for (int k = 0; k < kNumGuards; ++k) g[k] = ws_ptr<const unsigned char>(ws, L.o_guard[k]);
+    int32_t bad = -1;
+    rc = run_check_guards(g, ws_ptr<DevStatus>(ws, L.o_status), &bad, s);
+    if (first_bad) *first_bad = bad;
+    if (rc) return rc;
+    return bad >= 0 ? GS_ERR_DEVICE_FAULT : GS_OK;
+}
+
+int32_t gs_checked_build(void) { return GS_CHECKED ? 1 : 0; }
+
 int gs_read_stats(const gs_problem *pb, void *ws, void *stream, gs_stats *out) {
     Layout L;
     int rc = compute_layout(pb, &L);
@@ -288,6 +357,8 @@ int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stre
     a.near_plane = pb->params.near_plane; a.dil = pb->params.dilation; a.sigmas = pb->params.radius_sigmas;
     a.alpha_min = pb->params.alpha_min;
     a.tile_cnt = L.sort_mode == GS_SORT_TILE_BUCKET ? ws_ptr<uint32_t>(ws, L.o_tcnt) : nullptr;
+    a.P = L.P;
+    a.st = ws_ptr<DevStatus>(ws, L.o_status);
     a.Txi = L.Tx;
     a.Ty_i = L.Ty;
     launch_project(L, a, (cudaStream_t)stream);
@@ -347,6 +418,7 @@ static int render_fwd_impl(const gs_problem *pb, void *ws, const gs_image *out, 
     a.rgb = out->rgb; a.depth = out->depth; a.alpha = out->alpha; a.finalT = out->final_T; a.last = out->last_idx;
     a.st = ws_ptr<DevStatus>(ws, L.o_status);
     a.W = L.W; a.H = L.H; a.Tx = L.Tx; a.Ty = L.Ty; a.G = L.G; a.P = std::max<long long>(L.P, 1);
+    a.cap = L.cap;
     const gs_params &p = pb->params;
     a.amax = p.alpha_max; a.amin = p.alpha_min; a.tmin = p.t_min;
     a.bg0 = p.bg[0]; a.bg1 = p.bg[1]; a.bg2 = p.bg[2];
@@ -394,6 +466,7 @@ int gs_render_bwd_composite(const gs_problem *pb, void *ws, const gs_image *fwd,
     a.g2d = ws_ptr<float>(ws, L.o_g2d);
     a.st = ws_ptr<DevStatus>(ws, L.o_status);
     a.W = L.W; a.H = L.H; a.Tx = L.Tx; a.Ty = L.Ty; a.G = L.G; a.P = std::max<long long>(L.P, 1);
+    a.cap = L.cap;
     const gs_params &p = pb->params;
     a.amax = p.alpha_max; a.amin = p.alpha_min;
     a.bg0 = p.bg[0]; a.bg1 = p.bg[1]; a.bg2 = p.bg[2];
@@ -421,6 +494,10 @@ int gs_project_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const 
     b.pose_part = ws_ptr<float>(ws, L.o_pose_part);
     b.W = L.W; b.H = L.H;
     b.dil = pb->params.dilation;
+    b.P = L.P;
+    b.N = L.N;
+    b.chunks = L.chunks_total;
+    b.st = ws_ptr<DevStatus>(ws, L.o_status);
     launch_project_bwd(L, b, (cudaStream_t)stream);
     return check_launch();
 }
@@ -441,6 +518,7 @@ int gs_pose_grad(const gs_problem *pb, void *ws, float *pose_grad, void *stream)
     if (rc) return rc;
     if (!ws_ok(ws) || !pose_grad) return GS_ERR_INVALID_ARG;
     launch_pose_reduce(L, ws_ptr<ViewEntry>(ws, L.o_views), ws_ptr<float>(ws, L.o_pose_part), pose_grad,
+                       ws_ptr<DevStatus>(ws, L.o_status),
                        (cudaStream_t)stream);
     return check_launch();
 }

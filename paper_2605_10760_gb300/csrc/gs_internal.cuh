@@ -44,6 +44,8 @@ struct DevStatus {
     unsigned long long bwd_pairs;
     uint32_t bwd_items, bwd_pad;
     uint32_t ctr[kNumCounters];
+    int32_t guard_bad;            // gs_check_guards: index of the first changed guard block
+    int32_t guard_pad;
 };
 
 struct ViewEntry {                // per-view table in the workspace (32 bytes)
@@ -56,17 +58,43 @@ struct ViewEntry {                // per-view table in the workspace (32 bytes)
 struct Layout {
     int V, W, H, tw, th, Tx, Ty, passes;
     long long G, P, N, cap, max_count, max_chunks;
-    long long scan_parts, sort_parts;
+    long long scan_parts, sort_parts, chunks_total;
     int sort_mode, nb;                 // binning mode; records per staged render batch
     size_t o_status, o_views, o_proj, o_touched, o_scan_state, o_keys[2], o_vals[2], o_hist,
         o_sort_state, o_ranges, o_tcnt, o_tlist, o_srec, o_g2d, o_pose_part, total;
+    size_t o_guard[11];                // guard blocks after proj, touched, keys x2, vals x2, ranges,
+                                       // the tile lists, srec, g2d and the pose partials
 };
+constexpr int kNumGuards = 11;
+constexpr size_t kGuardBytes = 256;
+constexpr int kGuardByte = 0x5A;       // every byte of an intact guard block
+
+// ------------------------------------------------------------------------------------------
+// bounds-checked build (-DGS_CHECKED=1, libgs_checked.so): every index that comes from data (a
+// record's pair index, a key's tile, a range, a scatter position, a hash or tap position) is
+// compared with its buffer's length before the access; a violation records GS_ERR_DEVICE_FAULT
+// with site 100 + `site` and the access is skipped.  In the release build gs_guard is `true`.
+// ------------------------------------------------------------------------------------------
+#ifndef GS_CHECKED
+#define GS_CHECKED 0
+#endif
 
 // ------------------------------------------------------------------------------------------
 // error recording (first error wins)
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ void record_error(DevStatus *st, int code, int where) {
     if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
+}
+
+__device__ __forceinline__ bool gs_guard(DevStatus *st, bool ok, int site) {
+#if GS_CHECKED
+    if (!ok) record_error(st, GS_ERR_DEVICE_FAULT, 100 + site);
+    return ok;
+#else
+    (void)st;
+    (void)site;
+    return ok || true;
+#endif
 }
 
 // ------------------------------------------------------------------------------------------
@@ -335,6 +363,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // host side
 // ------------------------------------------------------------------------------------------
 int compute_layout(const gs_problem *pb, Layout *L);
+// scans the guard blocks (synchronises the stream); *first_bad = index of the first changed block or -1
+int run_check_guards(const unsigned char *const *guards, DevStatus *st, int32_t *first_bad, cudaStream_t s);
 void count_launches(int n);
 int device_sm_count();
 int check_launch();

@@ -17,6 +17,8 @@ struct ProjArgs {
     float near_plane, dil, sigmas, alpha_min;
     uint32_t *tile_cnt;         // [G] key count per global tile (tile-bucket binning), else null
     int Txi, Ty_i;
+    long long P;                // (view, Gaussian) pairs: the length of proj and touched
+    DevStatus *st;              // bounds-checked build: where a violated index is recorded
 };
 
 struct ProjBwdArgs {
@@ -30,11 +32,14 @@ struct ProjBwdArgs {
     float *pose_part;               // [chunks, 8]
     int W, H;
     float dil;
+    long long P, N, chunks;         // lengths of g2d / touched, of the gradient arrays, of pose_part
+    DevStatus *st;                  // bounds-checked build: where a violated index is recorded
 };
 
 void launch_project(const Layout &L, const ProjArgs &a, cudaStream_t s);
 void launch_project_bwd(const Layout &L, const ProjBwdArgs &a, cudaStream_t s);
-void launch_pose_reduce(const Layout &L, const ViewEntry *views, const float *part, float *out, cudaStream_t s);
+void launch_pose_reduce(const Layout &L, const ViewEntry *views, const float *part, float *out, DevStatus *st,
+                        cudaStream_t s);
 
 // ---------------- binning ----------------
 struct BinArgs {
@@ -77,7 +82,7 @@ struct FwdArgs {
     int32_t *last;
     DevStatus *st;
     int W, H, Tx, Ty;
-    long long G, P;
+    long long G, P, cap;               // global tiles, pairs, key capacity (the length of srec)
     float amax, amin, tmin, bg0, bg1, bg2;
     // optional L1 epilogue (Eq. 4's photometric and depth terms): null rgb_t = none
     const float *rgb_t, *depth_t;
@@ -95,7 +100,7 @@ struct BwdArgs {
     float *g2d;                        // [P,12]
     DevStatus *st;
     int W, H, Tx, Ty;
-    long long G, P;
+    long long G, P, cap;               // global tiles, pairs, key capacity (the length of srec)
     float amax, amin, bg0, bg1, bg2;
 };
 

@@ -40,6 +40,8 @@ __global__ void __launch_bounds__(kChunk) k_project(ProjArgs a) {
                          __ldg(mu + 2), __ldg(ls), __ldg(ls + 1), __ldg(ls + 2), q.x, q.y, q.z, q.w);
     }
     uint32_t cnt = 0;
+    const bool fok = gs_guard(a.st, !in || f < a.P, 1);   // the pair index comes from the views table
+    if (!fok) o.visible = false;
     if (o.visible) {
         cnt = (uint32_t)((o.x1 - o.x0) * (o.y1 - o.y0));
         const float *col = a.colors + 3 * gi;
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(kChunk) k_project(ProjArgs a) {
         for (int ty = o.y0; ty < o.y1; ++ty)
             for (int tx = o.x0; tx < o.x1; ++tx) atomicAdd(row + ty * a.Txi + tx, 1u);
     }
-    if (in) a.touched[f] = cnt;
+    if (in && fok) a.touched[f] = cnt;
 }
 
 void launch_project(const Layout &L, const ProjArgs &a, cudaStream_t s) {
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(kChunk) k_project_bwd(ProjBwdArgs a) {
     if ((long long)blockIdx.x * kChunk >= s_ve.count) return;   // whole block idle: no partial slot
     const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
     float pose[6] = {0, 0, 0, 0, 0, 0};
-    if (i < s_ve.count) {
+    if (i < s_ve.count && gs_guard(a.st, s_ve.pair_off + i < a.P && s_ve.gauss_begin + i < a.N, 2)) {
         const long long f = s_ve.pair_off + i;
         const uint32_t prev = (f > 0 && !a.touched_is_count) ? a.touched_incl[f - 1] : 0u;
         if (a.touched_incl[f] != prev) {
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(kChunk) k_project_bwd(ProjBwdArgs a) {
         if (lane == 0) s_red[warp][k] = r;
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
+    if (threadIdx.x < 6 && gs_guard(a.st, s_ve.chunk_off + blockIdx.x < a.chunks, 3)) {
         float r = 0.f;
 #pragma unroll
         for (int wi = 0; wi < kChunk / 32; ++wi) r += s_red[wi][threadIdx.x];
@@ -254,13 +256,15 @@ void launch_project_bwd(const Layout &L, const ProjBwdArgs &a, cudaStream_t s) {
 
 // deterministic per-view sum of the pose partials: one 256-thread block per (view, component),
 // fixed per-thread strides and a fixed reduction tree
-__global__ void __launch_bounds__(256) k_pose_reduce(const ViewEntry *views, const float *pose_part, float *out) {
+__global__ void __launch_bounds__(256) k_pose_reduce(const ViewEntry *views, const float *pose_part, float *out,
+                                                     long long total_chunks, DevStatus *st) {
     __shared__ float s_w[8];
     const int v = blockIdx.x, k = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const ViewEntry ve = views[v];
     const long long chunks = (ve.count + kChunk - 1) / kChunk;
     float acc = 0.f;
-    for (long long c = threadIdx.x; c < chunks; c += 256) acc += pose_part[(ve.chunk_off + c) * 8 + k];
+    for (long long c = threadIdx.x; c < chunks; c += 256)
+        if (gs_guard(st, ve.chunk_off + c < total_chunks, 4)) acc += pose_part[(ve.chunk_off + c) * 8 + k];
     acc = warp_sum(acc);
     if (lane == 0) s_w[warp] = acc;
     __syncthreads();
@@ -272,8 +276,9 @@ __global__ void __launch_bounds__(256) k_pose_reduce(const ViewEntry *views, con
     }
 }
 
-void launch_pose_reduce(const Layout &L, const ViewEntry *views, const float *part, float *out, cudaStream_t s) {
-    k_pose_reduce<<<dim3(L.V, 6), 256, 0, s>>>(views, part, out);
+void launch_pose_reduce(const Layout &L, const ViewEntry *views, const float *part, float *out, DevStatus *st,
+                        cudaStream_t s) {
+    k_pose_reduce<<<dim3(L.V, 6), 256, 0, s>>>(views, part, out, std::max<long long>(L.chunks_total, 1), st);
     count_launches(1);
 }
 

@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
         const int ty = tl / a.Tx, tx = tl - ty * a.Tx;
         const int x = tx * TW + lx, y0 = ty * TH + ly;
         const uint32_t start = a.ranges[2 * g], end = a.ranges[2 * g + 1];
-        const int n = (int)(end - start);
+        // the tile's list must lie inside the records (its batches are copied by TMA)
+        const int n = gs_guard(a.st, end >= start && (long long)end <= a.cap, 10) ? (int)(end - start) : 0;
         // per-pixel state of the thread's two pixels, packed (component p = pixel p)
         static_assert(kPPT == 2, "two pixels per thread, one per packed component");
         bool done[kPPT];
@@ -406,8 +407,8 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
         const int tl = (int)(g - (long long)v * tpv);
         const int ty = tl / a.Tx, tx = tl - ty * a.Tx;
         const int x = tx * TW + lx, y0 = ty * TH + ly;
-        const uint32_t start = a.ranges[2 * g];
-        const int n = (int)(a.ranges[2 * g + 1] - start);
+        const uint32_t start = a.ranges[2 * g], end = a.ranges[2 * g + 1];
+        const int n = gs_guard(a.st, end >= start && (long long)end <= a.cap, 11) ? (int)(end - start) : 0;
         const float px = (float)x + 0.5f;
         // per-pixel state of the thread's two pixels, packed (component p = pixel p)
         static_assert(kPPT == 2, "two pixels per thread, one per packed component");
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
                 if (__any_sync(0xffffffffu, contrib)) {
                     warp_transpose_reduce16(gv, lane);
                     const uint32_t f = __float_as_uint(r1.w);
-                    if (issuer) atomicAdd(a.g2d + 12 * (size_t)f + comp, gv[0]);
+                    if (issuer && gs_guard(a.st, (long long)f < a.P, 12)) atomicAdd(a.g2d + 12 * (size_t)f + comp, gv[0]);
                 }
               }
             }

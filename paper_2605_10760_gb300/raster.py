@@ -159,6 +159,12 @@ class Problem:
         rc = self.lib.gs_check_status(self.pb, _ptr(self.ws), _stream(), C.byref(req))
         return rc, int(req.value)
 
+    def check_guards(self):
+        """(status, index of the first overwritten workspace guard block or -1); synchronises."""
+        bad = C.c_int32(-1)
+        rc = self.lib.gs_check_guards(self.pb, _ptr(self.ws), _stream(), C.byref(bad))
+        return rc, int(bad.value)
+
     def stats(self) -> dict:
         s = L.gs_stats()
         L.check(self.lib.gs_read_stats(self.pb, _ptr(self.ws), _stream(), C.byref(s)), "gs_read_stats")

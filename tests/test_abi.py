@@ -128,3 +128,18 @@ def test_normal_loss_rejects_bad_arguments_without_launching(lib):
     bad = list(args)
     bad[3] = C.c_float(float("nan"))                                               # weight
     assert lib.gs_loss_normal(1, 16, 8, *bad) == L.GS_ERR_INVALID_ARG
+
+
+def test_both_library_builds_export_the_abi_and_name_their_variant():
+    """libgs.so (release) and libgs_checked.so (bounds-checked) export the same calls; each says
+    which build it is."""
+    import os
+    from paper_2605_10760_gb300 import build as B
+    B.build()
+    names = L.header_symbols()
+    for fname, want in (("libgs.so", 0), ("libgs_checked.so", 1)):
+        lib = C.CDLL(os.path.join(B.OUT, fname))
+        for n in names:
+            assert hasattr(lib, n), (fname, n)
+        lib.gs_checked_build.restype = C.c_int32
+        assert lib.gs_checked_build() == want

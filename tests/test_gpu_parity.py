@@ -59,6 +59,7 @@ def run_gpu(R, wl, views=None, params=None, key_capacity=None, grads=True, seed=
     rc2, _ = pb.check_status()
     out["rc_end"] = rc2
     out["stats"] = pb.stats()
+    assert pb.check_guards() == (0, -1), "a workspace guard block was overwritten"
     return out
 
 
@@ -104,6 +105,14 @@ def compare_all(gpu, orc, check_grads=True):
     for v in range(gpu["pose"].shape[0]):
         e = rel_l2(gpu["pose"][v], bw["pose"][v])
         assert e <= TOL_GRAD, ("pose", v, e, gpu["pose"][v], bw["pose"][v])
+
+
+def test_library_variant_is_the_requested_one(R):
+    """GS_LIBGS_VARIANT=checked loads the bounds-checked build (tests/test_gpu_checked_build.py runs
+    this module that way), anything else the release build."""
+    import os
+    want = 1 if os.environ.get("GS_LIBGS_VARIANT", "") == "checked" else 0
+    assert R.L.load().gs_checked_build() == want
 
 
 def test_debug_expf_bitwise_vs_oracle_and_cuda(R):
