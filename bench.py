@@ -151,12 +151,13 @@ class Pipeline:
         self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
         self.grads = R.zeros_like_grads(self.g)
         self.pose = torch.zeros(V, 6, device="cuda")
-        # size the key capacity once (outside any timing)
+        # size the key and visible-pair capacities once (outside any timing)
         self.pb.forward_checked(self.g, self.img)
         torch.cuda.synchronize()
-        k = self.pb.stats()["num_keys"]
+        st = self.pb.stats()
+        k, nv = st["num_keys"], st["num_visible"]
         if key_capacity is None and k * 1.3 + 4096 < self.pb.cap:
-            self.pb.set_capacity(int(k * 1.3) + 4096)
+            self.pb.set_capacity(int(k * 1.3) + 4096, visible=int(nv * 1.3) + 4096)
 
     def zero_grads(self):
         import ctypes as C

@@ -105,7 +105,12 @@ typedef struct gs_params {
 typedef struct gs_problem {
     int32_t num_views;                 /* V, 1..GS_MAX_VIEWS                          */
     int32_t width, height;             /* image size, pixels                          */
-    int32_t reserved;
+    int32_t visible_capacity;          /* max visible (view, Gaussian) pairs whose projection
+                                          records and 2-D gradients the workspace holds; 0 = the
+                                          pair count (always enough).  More visible pairs record
+                                          GS_ERR_CAPACITY and drop the excess (K is then counted
+                                          without their keys); gs_read_stats reports the visible
+                                          count needed. */
     int64_t num_gaussians;             /* N                                           */
     const int64_t *view_gauss_begin;   /* host [V]                                    */
     const int64_t *view_gauss_count;   /* host [V]                                    */
@@ -149,17 +154,19 @@ typedef struct gs_grads {
  * with G = V * ceil(W/tile_w) * ceil(H/tile_h); grad2d [P,12] float (dL/d mean_x, mean_y,
  * conic A, B, C, opacity, depth, r, g, b, 0, 0); num_keys -> uint32 K. */
 typedef struct gs_ws_view {
-    float *proj;
+    float *proj;                       /* [visible_capacity, 12] projection records, by slot */
     uint32_t *tiles_touched;
     uint64_t *sorted_keys;
-    uint32_t *sorted_vals;
+    uint32_t *sorted_vals;             /* flattened (view, Gaussian) pair indices */
     uint32_t *tile_ranges;
-    float *grad2d;
+    float *grad2d;                     /* [visible_capacity, 12] 2-D gradients, by slot */
     uint32_t *num_keys;
     int64_t num_pairs;                 /* P */
     int64_t num_tiles;                 /* G */
     int32_t sort_passes;               /* 8-bit LSD passes of the onesweep sort */
     int32_t reserved;
+    uint32_t *pair_slot;               /* [P] slot of each visible pair, 0xffffffff if culled */
+    int64_t visible_capacity;          /* slots in proj and grad2d */
 } gs_ws_view;
 
 /* Statistics of the last calls, read by gs_read_stats (synchronises the stream). */
@@ -167,6 +174,8 @@ typedef struct gs_stats {
     int64_t num_keys;                  /* K of the last gs_bin_sort                           */
     int64_t fwd_pairs;                 /* (pixel, list entry) pairs evaluated by the forward  */
     int64_t bwd_pairs;                 /* (pixel, list entry) pairs walked by the backward    */
+    int64_t num_visible;               /* visible pairs of the last gs_project (also beyond
+                                          visible_capacity: the capacity a retry needs)       */
 } gs_stats;
 
 const char *gs_error_string(int code);
@@ -197,7 +206,8 @@ int gs_read_stats(const gs_problem *pb, void *ws, void *stream, gs_stats *out);
 /* Workspace guard blocks (no counterpart in the paper; a check of the library itself): 256-byte
  * blocks of a fixed byte pattern, written by gs_workspace_init, follow every workspace buffer that
  * kernels index with data (projection records, tile counts, both key and value buffers, the tile
- * ranges and lists, the records in list order, the 2-D gradients, the pose partials).  This call
+ * ranges and lists, the records in list order, the 2-D gradients, the pose partials, the pair
+ * slots).  This call
  * synchronises `stream` and returns GS_OK when every block is intact, else GS_ERR_DEVICE_FAULT with
  * *first_bad (may be NULL) = the index of the first changed block in that order. */
 int gs_check_guards(const gs_problem *pb, void *ws, void *stream, int32_t *first_bad);

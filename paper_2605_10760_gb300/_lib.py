@@ -43,7 +43,8 @@ class gs_params(C.Structure):
 
 
 class gs_problem(C.Structure):
-    _fields_ = [("num_views", C.c_int32), ("width", C.c_int32), ("height", C.c_int32), ("reserved", C.c_int32),
+    _fields_ = [("num_views", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
+                ("visible_capacity", C.c_int32),
                 ("num_gaussians", C.c_int64), ("view_gauss_begin", C.POINTER(C.c_int64)),
                 ("view_gauss_count", C.POINTER(C.c_int64)), ("cameras", C.c_void_p),
                 ("key_capacity", C.c_int64), ("params", gs_params)]
@@ -72,11 +73,13 @@ class gs_ws_view(C.Structure):
     _fields_ = [("proj", C.c_void_p), ("tiles_touched", C.c_void_p), ("sorted_keys", C.c_void_p),
                 ("sorted_vals", C.c_void_p), ("tile_ranges", C.c_void_p), ("grad2d", C.c_void_p),
                 ("num_keys", C.c_void_p), ("num_pairs", C.c_int64), ("num_tiles", C.c_int64),
-                ("sort_passes", C.c_int32), ("reserved", C.c_int32)]
+                ("sort_passes", C.c_int32), ("reserved", C.c_int32), ("pair_slot", C.c_void_p),
+                ("visible_capacity", C.c_int64)]
 
 
 class gs_stats(C.Structure):
-    _fields_ = [("num_keys", C.c_int64), ("fwd_pairs", C.c_int64), ("bwd_pairs", C.c_int64)]
+    _fields_ = [("num_keys", C.c_int64), ("fwd_pairs", C.c_int64), ("bwd_pairs", C.c_int64),
+                ("num_visible", C.c_int64)]
 
 
 class gs_gaussian_arrays(C.Structure):

@@ -81,6 +81,8 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     }
     if (P >= 0xffffffffLL) return GS_ERR_INVALID_ARG;   // pair indices are 32-bit
     L->P = P;
+    if (pb->visible_capacity < 0) return GS_ERR_INVALID_ARG;
+    L->vcap = pb->visible_capacity > 0 ? (long long)pb->visible_capacity : std::max<long long>(1, P);
     L->max_count = maxc;
     L->max_chunks = std::max<long long>(1, (maxc + kChunk - 1) / kChunk);
     int gbits = 0;
@@ -103,7 +105,7 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     };
     L->o_status = o; o = align256(o + sizeof(DevStatus));
     L->o_views = o; o = align256(o + sizeof(ViewEntry) * L->V);
-    L->o_proj = o; o = align256(o + sizeof(float) * 12 * (size_t)std::max<long long>(P, 1));
+    L->o_proj = o; o = align256(o + sizeof(float) * 12 * (size_t)L->vcap);
     guard();
     L->o_touched = o; o = align256(o + sizeof(uint32_t) * (size_t)std::max<long long>(P, 1) + 64);
     guard();
@@ -120,9 +122,11 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     guard();
     L->o_srec = o; o = align256(o + sizeof(float) * 12 * (size_t)L->cap);
     guard();
-    L->o_g2d = o; o = align256(o + sizeof(float) * 12 * (size_t)std::max<long long>(P, 1));
+    L->o_g2d = o; o = align256(o + sizeof(float) * 12 * (size_t)L->vcap);
     guard();
     L->o_pose_part = o; o = align256(o + sizeof(float) * 8 * (size_t)std::max<long long>(chunks_total, 1));
+    guard();
+    L->o_slot = o; o = align256(o + sizeof(uint32_t) * (size_t)std::max<long long>(P, 1));
     guard();
     if (ng != kNumGuards) return GS_ERR_INVALID_ARG;   // the layout and kNumGuards disagree: a build error
     L->total = o;
@@ -241,6 +245,8 @@ int gs_workspace_view(const gs_problem *pb, void *ws, gs_ws_view *out) {
     out->num_tiles = L.G;
     out->sort_passes = L.passes;
     out->reserved = 0;
+    out->pair_slot = ws_ptr<uint32_t>(ws, L.o_slot);
+    out->visible_capacity = L.vcap;
     return GS_OK;
 }
 
@@ -329,6 +335,7 @@ int gs_read_stats(const gs_problem *pb, void *ws, void *stream, gs_stats *out) {
     out->num_keys = (int64_t)h.num_keys;
     out->fwd_pairs = (int64_t)h.fwd_pairs;
     out->bwd_pairs = (int64_t)h.bwd_pairs;
+    out->num_visible = (int64_t)h.num_visible;
     return GS_OK;
 }
 
@@ -344,6 +351,9 @@ int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stre
         cudaMemsetAsync(ws_ptr<uint32_t>(ws, L.o_tcnt), 0, sizeof(uint32_t) * ((size_t)L.G + 1),
                         (cudaStream_t)stream) != cudaSuccess)
         return GS_ERR_CUDA;
+    DevStatus *st = ws_ptr<DevStatus>(ws, L.o_status);
+    if (cudaMemsetAsync(&st->num_visible, 0, sizeof(st->num_visible), (cudaStream_t)stream) != cudaSuccess)
+        return GS_ERR_CUDA;
     if (L.P == 0) return GS_OK;
     ProjArgs a;
     a.views = ws_ptr<ViewEntry>(ws, L.o_views);
@@ -358,7 +368,9 @@ int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stre
     a.alpha_min = pb->params.alpha_min;
     a.tile_cnt = L.sort_mode == GS_SORT_TILE_BUCKET ? ws_ptr<uint32_t>(ws, L.o_tcnt) : nullptr;
     a.P = L.P;
-    a.st = ws_ptr<DevStatus>(ws, L.o_status);
+    a.st = st;
+    a.slot = ws_ptr<uint32_t>(ws, L.o_slot);
+    a.vcap = L.vcap;
     a.Txi = L.Tx;
     a.Ty_i = L.Ty;
     launch_project(L, a, (cudaStream_t)stream);
@@ -385,6 +397,8 @@ static BinArgs make_bin_args(const Layout &L, void *ws) {
     a.V = L.V; a.Tx = L.Tx; a.Ty = L.Ty; a.passes = L.passes;
     a.itw = 1.0f / (float)L.tw; a.ith = 1.0f / (float)L.th;
     a.P = L.P; a.cap = L.cap; a.sort_parts = L.sort_parts; a.max_chunks = L.max_chunks; a.G = L.G;
+    a.slot = ws_ptr<const uint32_t>(ws, L.o_slot);
+    a.vcap = L.vcap;
     a.fault_scan_part = -1;
     a.spin_limit = kSpinLimit;
     a.sort_mode = L.sort_mode;
@@ -465,7 +479,7 @@ int gs_render_bwd_composite(const gs_problem *pb, void *ws, const gs_image *fwd,
     a.d_rgb = dimg->d_rgb; a.d_depth = dimg->d_depth; a.d_alpha = dimg->d_alpha;
     a.g2d = ws_ptr<float>(ws, L.o_g2d);
     a.st = ws_ptr<DevStatus>(ws, L.o_status);
-    a.W = L.W; a.H = L.H; a.Tx = L.Tx; a.Ty = L.Ty; a.G = L.G; a.P = std::max<long long>(L.P, 1);
+    a.W = L.W; a.H = L.H; a.Tx = L.Tx; a.Ty = L.Ty; a.G = L.G; a.P = L.vcap;   // g2d slots
     a.cap = L.cap;
     const gs_params &p = pb->params;
     a.amax = p.alpha_max; a.amin = p.alpha_min;
@@ -496,6 +510,8 @@ int gs_project_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const 
     b.dil = pb->params.dilation;
     b.P = L.P;
     b.N = L.N;
+    b.slot = ws_ptr<const uint32_t>(ws, L.o_slot);
+    b.vcap = L.vcap;
     b.chunks = L.chunks_total;
     b.st = ws_ptr<DevStatus>(ws, L.o_status);
     launch_project_bwd(L, b, (cudaStream_t)stream);

@@ -46,6 +46,7 @@ struct DevStatus {
     uint32_t ctr[kNumCounters];
     int32_t guard_bad;            // gs_check_guards: index of the first changed guard block
     int32_t guard_pad;
+    unsigned long long num_visible;   // visible pairs of the last projection (slot counter)
 };
 
 struct ViewEntry {                // per-view table in the workspace (32 bytes)
@@ -58,20 +59,22 @@ struct ViewEntry {                // per-view table in the workspace (32 bytes)
 struct Layout {
     int V, W, H, tw, th, Tx, Ty, passes;
     long long G, P, N, cap, max_count, max_chunks;
+    long long vcap;                    // slots of the projection records and 2-D gradients
     long long scan_parts, sort_parts, chunks_total;
     int sort_mode, nb;                 // binning mode; records per staged render batch
     size_t o_status, o_views, o_proj, o_touched, o_scan_state, o_keys[2], o_vals[2], o_hist,
-        o_sort_state, o_ranges, o_tcnt, o_tlist, o_srec, o_g2d, o_pose_part, total;
-    size_t o_guard[11];                // guard blocks after proj, touched, keys x2, vals x2, ranges,
-                                       // the tile lists, srec, g2d and the pose partials
+        o_sort_state, o_ranges, o_tcnt, o_tlist, o_srec, o_g2d, o_pose_part, o_slot, total;
+    size_t o_guard[12];                // guard blocks after proj, touched, keys x2, vals x2, ranges,
+                                       // the tile lists, srec, g2d, the pose partials and the slots
 };
-constexpr int kNumGuards = 11;
+constexpr int kNumGuards = 12;
+constexpr uint32_t kNoSlot = 0xffffffffu;   // pair_slot of a culled pair
 constexpr size_t kGuardBytes = 256;
 constexpr int kGuardByte = 0x5A;       // every byte of an intact guard block
 
 // ------------------------------------------------------------------------------------------
 // bounds-checked build (-DGS_CHECKED=1, libgs_checked.so): every index that comes from data (a
-// record's pair index, a key's tile, a range, a scatter position, a hash or tap position) is
+// record's slot, a key's tile, a range, a scatter position, a hash or tap position) is
 // compared with its buffer's length before the access; a violation records GS_ERR_DEVICE_FAULT
 // with site 100 + `site` and the access is skipped.  In the release build gs_guard is `true`.
 // ------------------------------------------------------------------------------------------

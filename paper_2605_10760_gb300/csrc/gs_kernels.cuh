@@ -17,8 +17,10 @@ struct ProjArgs {
     float near_plane, dil, sigmas, alpha_min;
     uint32_t *tile_cnt;         // [G] key count per global tile (tile-bucket binning), else null
     int Txi, Ty_i;
-    long long P;                // (view, Gaussian) pairs: the length of proj and touched
-    DevStatus *st;              // bounds-checked build: where a violated index is recorded
+    long long P;                // (view, Gaussian) pairs: the length of touched and slot
+    DevStatus *st;              // errors; num_visible is the slot counter
+    uint32_t *slot;             // [P] slot of each visible pair in proj (kNoSlot when culled)
+    long long vcap;             // slots in proj
 };
 
 struct ProjBwdArgs {
@@ -32,8 +34,10 @@ struct ProjBwdArgs {
     float *pose_part;               // [chunks, 8]
     int W, H;
     float dil;
-    long long P, N, chunks;         // lengths of g2d / touched, of the gradient arrays, of pose_part
+    long long P, N, chunks;         // lengths of touched / slot, of the gradient arrays, of pose_part
     DevStatus *st;                  // bounds-checked build: where a violated index is recorded
+    const uint32_t *slot;           // [P] slot of each visible pair in g2d
+    long long vcap;                 // slots in g2d
 };
 
 void launch_project(const Layout &L, const ProjArgs &a, cudaStream_t s);
@@ -65,6 +69,8 @@ struct BinArgs {
     int sort_mode;                     // GS_SORT_TILE_BUCKET or GS_SORT_ONESWEEP
     uint32_t *tile_cnt;                // [G + 1] per-tile key counts -> slice starts (bucket mode)
     uint32_t *tile_list;               // [G] tiles whose slices are sorted by k_tile_sort_long
+    const uint32_t *slot;              // [P] slot of each visible pair in proj and g2d
+    long long vcap;                    // slots in proj and g2d
 };
 
 // onesweep: scan with key emission and digit histograms -> onesweep passes -> ranges; tile bucket: scan of the
@@ -76,7 +82,7 @@ int run_scan_only(const BinArgs &a, cudaStream_t s);
 
 // ---------------- rendering ----------------
 struct FwdArgs {
-    const float4 *srec;                // [K,3] records in list order (r1.w = pair index bits)
+    const float4 *srec;                // [K,3] records in list order (r1.w = the pair's slot, as bits)
     const uint32_t *ranges;
     float *rgb, *depth, *alpha, *finalT;
     int32_t *last;
@@ -100,7 +106,7 @@ struct BwdArgs {
     float *g2d;                        // [P,12]
     DevStatus *st;
     int W, H, Tx, Ty;
-    long long G, P, cap;               // global tiles, pairs, key capacity (the length of srec)
+    long long G, P, cap;               // global tiles, slots of g2d, key capacity (the length of srec)
     float amax, amin, bg0, bg1, bg2;
 };
 

@@ -42,10 +42,33 @@ __global__ void __launch_bounds__(kChunk) k_project(ProjArgs a) {
     uint32_t cnt = 0;
     const bool fok = gs_guard(a.st, !in || f < a.P, 1);   // the pair index comes from the views table
     if (!fok) o.visible = false;
+    // slot of each visible pair in the records: the block's visible pairs take consecutive slots
+    // (ballot + warp counts), the block's first slot comes from one atomic on the slot counter;
+    // slots beyond the capacity record GS_ERR_CAPACITY and their pairs are dropped
+    __shared__ uint32_t s_wcnt[kChunk / 32];
+    __shared__ unsigned long long s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned vmask = __ballot_sync(0xffffffffu, o.visible);
+    if (lane == 0) s_wcnt[warp] = (uint32_t)__popc(vmask);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < kChunk / 32; ++w) tot += s_wcnt[w];
+        s_base = tot ? atomicAdd(&a.st->num_visible, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long slot = s_base + (unsigned long long)__popc(vmask & lanemask_lt());
+    for (int w = 0; w < warp; ++w) slot += s_wcnt[w];
+    if (o.visible && slot >= (unsigned long long)a.vcap) {
+        record_error(a.st, GS_ERR_CAPACITY, 11);
+        o.visible = false;
+    }
+    if (in && fok) a.slot[f] = o.visible ? (uint32_t)slot : kNoSlot;
     if (o.visible) {
         cnt = (uint32_t)((o.x1 - o.x0) * (o.y1 - o.y0));
         const float *col = a.colors + 3 * gi;
-        float4 *rec = a.proj + 3 * f;
+        float4 *rec = a.proj + 3 * slot;
         const float op = __ldg(a.opacities + gi);
         // sigma beyond which alpha < alpha_min is certain (see gs_render.cu); +inf disables the cut
         float cut = __int_as_float(0x7f800000);
@@ -101,11 +124,12 @@ __global__ void __launch_bounds__(kChunk) k_project_bwd(ProjBwdArgs a) {
     if (i < s_ve.count && gs_guard(a.st, s_ve.pair_off + i < a.P && s_ve.gauss_begin + i < a.N, 2)) {
         const long long f = s_ve.pair_off + i;
         const uint32_t prev = (f > 0 && !a.touched_is_count) ? a.touched_incl[f - 1] : 0u;
-        if (a.touched_incl[f] != prev) {
+        const uint32_t sl = a.slot[f];   // visible pairs only hold a valid slot
+        if (a.touched_incl[f] != prev && gs_guard(a.st, sl < (unsigned long long)a.vcap, 5)) {
             const long long gi = s_ve.gauss_begin + i;
             const float *R = s_cam, *t = s_cam + 9;
             const float fx = s_cam[12], fy = s_cam[13];
-            const float4 g0 = a.g2d[3 * f], g1 = a.g2d[3 * f + 1], g2 = a.g2d[3 * f + 2];
+            const float4 g0 = a.g2d[3 * (size_t)sl], g1 = a.g2d[3 * (size_t)sl + 1], g2 = a.g2d[3 * (size_t)sl + 2];
             const float gmx = g0.x, gmy = g0.y, gA = g0.z, gB = g0.w, gC = g1.x, gop = g1.y, gz = g1.z;
             atomicAdd(a.g_op + gi, gop);
             atomicAdd(a.g_col + 3 * gi, g1.w);

@@ -547,8 +547,8 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
                     warp_transpose_reduce16(gv, lane);
-                    const uint32_t f = __float_as_uint(r1.w);
-                    if (issuer && gs_guard(a.st, (long long)f < a.P, 12)) atomicAdd(a.g2d + 12 * (size_t)f + comp, gv[0]);
+                    const uint32_t sl = __float_as_uint(r1.w);   // the record's slot in g2d
+                    if (issuer && gs_guard(a.st, (long long)sl < a.P, 12)) atomicAdd(a.g2d + 12 * (size_t)sl + comp, gv[0]);
                 }
               }
             }

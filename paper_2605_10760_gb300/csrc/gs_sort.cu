@@ -266,7 +266,12 @@ __global__ void __launch_bounds__(kEmitThreads) k_scan_emit(BinArgs a) {
             const uint32_t b1 = es.inc[li], b0 = li ? es.inc[li - 1] : pstart;
             if (b1 == b0) continue;
             const long long f = pbase + li;
-            const float4 r0 = a.proj[3 * f], r1 = a.proj[3 * f + 1];
+            const uint32_t sl = a.slot[f];      // a pair with keys is visible and holds a slot
+            if (sl >= (unsigned long long)a.vcap) {   // only after an earlier recorded failure
+                record_error(a.st, GS_ERR_DEVICE_FAULT, 7);
+                continue;
+            }
+            const float4 r0 = a.proj[3 * (size_t)sl], r1 = a.proj[3 * (size_t)sl + 1];
             int x0, x1, y0, y1;
             spec_rect(r0.x, r0.y, r1.w, a.itw, a.ith, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
             const int v = view_of_pair(a.views, a.V, f);
@@ -275,9 +280,9 @@ __global__ void __launch_bounds__(kEmitThreads) k_scan_emit(BinArgs a) {
             es.wr[li] = (uint32_t)max(x1 - x0, 1);
             es.z[li] = __float_as_uint(r1.z);
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            a.g2d[3 * f] = z4;
-            a.g2d[3 * f + 1] = z4;
-            a.g2d[3 * f + 2] = z4;
+            a.g2d[3 * (size_t)sl] = z4;
+            a.g2d[3 * (size_t)sl + 1] = z4;
+            a.g2d[3 * (size_t)sl + 2] = z4;
         }
         __syncthreads();
         // (3) per key, up to the capacity (< 2^30, so the counter cannot wrap even when the sums
@@ -520,8 +525,9 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
 // ------------------------------------------------------------------------------------------
 // 4. tile ranges
 // ------------------------------------------------------------------------------------------
-__global__ void k_ranges(const uint64_t *keys, const uint32_t *vals, const float4 *proj, float4 *srec, DevStatus *st,
-                         long long cap, long long G, long long P, uint32_t *ranges) {
+__global__ void k_ranges(const uint64_t *keys, const uint32_t *vals, const float4 *proj, const uint32_t *slot,
+                         long long vcap, float4 *srec, DevStatus *st, long long cap, long long G, long long P,
+                         uint32_t *ranges) {
     const unsigned long long K = min(st->num_keys, (unsigned long long)cap);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < K;
          i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -534,12 +540,17 @@ __global__ void k_ranges(const uint64_t *keys, const uint32_t *vals, const float
         if (i == 0 || (keys[i - 1] >> 32) != g) ranges[2 * g] = (uint32_t)i;
         if (i == K - 1 || (keys[i + 1] >> 32) != g) ranges[2 * g + 1] = (uint32_t)(i + 1);
         // the entry's record in list order, so a tile's batch is one contiguous block;
-        // the radius slot (used only by key emission) carries the pair index instead
-        float4 r1 = proj[3 * (size_t)f + 1];
-        r1.w = __uint_as_float(f);
-        srec[3 * i] = proj[3 * (size_t)f];
+        // the radius field (used only by key emission) carries the pair's slot instead
+        const uint32_t sl = slot[f];
+        if (sl >= (unsigned long long)vcap) {   // only after an earlier recorded failure
+            record_error(st, GS_ERR_DEVICE_FAULT, 8);
+            continue;
+        }
+        float4 r1 = proj[3 * (size_t)sl + 1];
+        r1.w = __uint_as_float(sl);
+        srec[3 * i] = proj[3 * (size_t)sl];
         srec[3 * i + 1] = r1;
-        srec[3 * i + 2] = proj[3 * (size_t)f + 2];
+        srec[3 * i + 2] = proj[3 * (size_t)sl + 2];
     }
 }
 
@@ -554,11 +565,12 @@ __global__ void __launch_bounds__(kChunk) k_emit_bucket(BinArgs a) {
     if ((long long)blockIdx.x * kChunk >= s_ve.count) return;   // whole block past the view
     const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
     const long long f = s_ve.pair_off + (i < s_ve.count ? i : 0);
-    const bool vis = i < s_ve.count && a.touched[f] != 0u;
+    const uint32_t sl = i < s_ve.count ? a.slot[f] : kNoSlot;
+    const bool vis = i < s_ve.count && a.touched[f] != 0u && sl < (unsigned long long)a.vcap;
     int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
     unsigned long long word = 0;
     if (vis) {
-        const float4 r0 = a.proj[3 * f], r1 = a.proj[3 * f + 1];
+        const float4 r0 = a.proj[3 * (size_t)sl], r1 = a.proj[3 * (size_t)sl + 1];
         spec_rect(r0.x, r0.y, r1.w, a.itw, a.ith, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
         word = ((unsigned long long)__float_as_uint(r1.z) << 32) | (unsigned long long)(uint32_t)f;
     }
@@ -589,9 +601,9 @@ __global__ void __launch_bounds__(kChunk) k_emit_bucket(BinArgs a) {
     }
     if (vis) {
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        a.g2d[3 * f] = z4;
-        a.g2d[3 * f + 1] = z4;
-        a.g2d[3 * f + 2] = z4;
+        a.g2d[3 * (size_t)sl] = z4;
+        a.g2d[3 * (size_t)sl + 1] = z4;
+        a.g2d[3 * (size_t)sl + 2] = z4;
     }
 }
 
@@ -679,11 +691,16 @@ __device__ __forceinline__ void tile_emit(const BinArgs &a, uint64_t *kout, uint
     }
     kout[pos] = ((unsigned long long)g << 32) | (w >> 32);
     vout[pos] = f;
-    float4 r1 = a.proj[3 * (size_t)f + 1];
-    r1.w = __uint_as_float(f);
-    a.srec[3 * pos] = a.proj[3 * (size_t)f];
+    const uint32_t sl = a.slot[f];
+    if (sl >= (unsigned long long)a.vcap) {   // only after an earlier recorded failure
+        record_error(a.st, GS_ERR_DEVICE_FAULT, 9);
+        return;
+    }
+    float4 r1 = a.proj[3 * (size_t)sl + 1];
+    r1.w = __uint_as_float(sl);
+    a.srec[3 * pos] = a.proj[3 * (size_t)sl];
     a.srec[3 * pos + 1] = r1;
-    a.srec[3 * pos + 2] = a.proj[3 * (size_t)f + 2];
+    a.srec[3 * pos + 2] = a.proj[3 * (size_t)sl + 2];
 }
 
 // One warp per tile: every warp claims tiles from a counter, publishes the tile's range and sorts
@@ -891,7 +908,8 @@ int run_bin_sort(const BinArgs &a, cudaStream_t s) {
     }
     const int rc2 = sweep_passes<kSortIPT>(a, s);
     if (rc2) return rc2;
-    k_ranges<<<sms * 8, 256, 0, s>>>(a.keys[a.passes & 1], a.vals[a.passes & 1], a.proj, a.srec, a.st, a.cap, a.G,
+    k_ranges<<<sms * 8, 256, 0, s>>>(a.keys[a.passes & 1], a.vals[a.passes & 1], a.proj, a.slot, a.vcap, a.srec, a.st,
+                                      a.cap, a.G,
                                       a.P, a.ranges);
     count_launches(1);
     return check_launch();

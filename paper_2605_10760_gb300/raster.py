@@ -79,7 +79,8 @@ class Problem:
     """
 
     def __init__(self, view_gauss_begin, view_gauss_count, num_gaussians, width, height, cameras=None,
-                 params: L.gs_params | None = None, key_capacity: int | None = None, device="cuda"):
+                 params: L.gs_params | None = None, key_capacity: int | None = None, device="cuda",
+                 visible_capacity: int = 0):
         self.lib = L.load()
         self.device = torch.device(device)
         self.vb = np.ascontiguousarray(view_gauss_begin, dtype=np.int64)
@@ -92,6 +93,7 @@ class Problem:
         if key_capacity is None:
             key_capacity = int(min((1 << 30) - 1, max(1 << 20, 4 * self.P)))
         self.cap = int(key_capacity)
+        self.vcap = int(visible_capacity)          # 0: min(pairs, key capacity), always enough
         self.cameras = cameras
         self._pb = L.gs_problem()
         self._sync_struct()
@@ -106,6 +108,7 @@ class Problem:
         pb.view_gauss_count = self.vc.ctypes.data_as(C.POINTER(C.c_int64))
         pb.cameras = None if self.cameras is None else self.cameras.data_ptr()
         pb.key_capacity = self.cap
+        pb.visible_capacity = self.vcap
         pb.params = self.params
 
     @property
@@ -120,8 +123,11 @@ class Problem:
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
         L.check(self.lib.gs_workspace_init(self.pb, _ptr(self.ws), _stream()), "gs_workspace_init")
 
-    def set_capacity(self, cap: int):
+    def set_capacity(self, cap: int, visible: int | None = None):
+        """Re-size the workspace for `cap` keys (and `visible` visible pairs when given)."""
         self.cap = int(min((1 << 30) - 1, cap))
+        if visible is not None:
+            self.vcap = int(min((1 << 31) - 1, visible))
         self._alloc()
 
     def set_cameras(self, cameras: torch.Tensor):
@@ -145,14 +151,25 @@ class Problem:
             nbytes = count * torch.empty((), dtype=dtype).element_size()
             return self.ws[off:off + nbytes].view(dtype)
 
-        P, G = int(v.num_pairs), int(v.num_tiles)
-        return dict(proj=sl(v.proj, 12 * P, torch.float32).view(P, 12),
-                    tiles_touched=sl(v.tiles_touched, P, torch.int32),
+        P, G, VC = int(v.num_pairs), int(v.num_tiles), int(v.visible_capacity)
+        slot = sl(v.pair_slot, P, torch.int32)
+        proj_s = sl(v.proj, 12 * VC, torch.float32).view(VC, 12)
+        g2d_s = sl(v.grad2d, 12 * VC, torch.float32).view(VC, 12)
+
+        def by_pair(t):
+            # inspection copy in pair order (zero rows for culled pairs): records live by slot
+            out = torch.zeros(P, 12, dtype=t.dtype, device=t.device)
+            s64 = slot.long() & 0xffffffff
+            ok = s64 < VC
+            out[ok] = t[s64[ok]]
+            return out
+
+        return dict(proj=by_pair(proj_s), grad2d=by_pair(g2d_s), proj_slots=proj_s, grad2d_slots=g2d_s,
+                    pair_slot=slot, tiles_touched=sl(v.tiles_touched, P, torch.int32),
                     sorted_keys=sl(v.sorted_keys, self.cap, torch.int64),
                     sorted_vals=sl(v.sorted_vals, self.cap, torch.int32),
                     tile_ranges=sl(v.tile_ranges, 2 * G, torch.int32).view(G, 2),
-                    grad2d=sl(v.grad2d, 12 * P, torch.float32).view(P, 12),
-                    num_keys=sl(v.num_keys, 2, torch.int32), passes=int(v.sort_passes))
+                    num_keys=sl(v.num_keys, 2, torch.int32), passes=int(v.sort_passes), visible_capacity=VC)
 
     def check_status(self):
         req = C.c_int64()
@@ -168,7 +185,8 @@ class Problem:
     def stats(self) -> dict:
         s = L.gs_stats()
         L.check(self.lib.gs_read_stats(self.pb, _ptr(self.ws), _stream(), C.byref(s)), "gs_read_stats")
-        return dict(num_keys=int(s.num_keys), fwd_pairs=int(s.fwd_pairs), bwd_pairs=int(s.bwd_pairs))
+        return dict(num_keys=int(s.num_keys), fwd_pairs=int(s.fwd_pairs), bwd_pairs=int(s.bwd_pairs),
+                    num_visible=int(s.num_visible))
 
     # -- stages ----------------------------------------------------------------------------
     def project(self, g: Gaussians):
@@ -243,13 +261,16 @@ class Problem:
         return out
 
     def forward_checked(self, g: Gaussians, img: dict | None = None, max_retries: int = 2) -> dict:
-        """project + bin_sort + render_fwd, growing the key capacity when K exceeds it (syncs)."""
+        """project + bin_sort + render_fwd, growing the key capacity when K exceeds it and the
+        visible-pair capacity when the visible pairs exceed it (syncs)."""
         for _ in range(max_retries + 1):
             self.project(g)
             self.bin_sort()
             rc, req = self.check_status()
             if rc == L.GS_ERR_CAPACITY:
-                self.set_capacity(int(req * 1.25) + 1024)
+                nv = self.stats()["num_visible"]
+                vis = int(nv * 1.25) + 1024 if self.vcap and nv > self.vcap else None
+                self.set_capacity(max(self.cap, int(req * 1.25) + 1024) if req > self.cap else self.cap, vis)
                 continue
             L.check(rc, "gs_bin_sort")
             return self.render_fwd(img)

@@ -57,14 +57,24 @@ def test_workspace_size_and_validation(lib):
     n = C.c_size_t()
     pb = _problem()
     assert lib.gs_workspace_size(C.byref(pb), C.byref(n)) == 0
-    # proj + grad2d (48 B each per pair), keys + values (2 x 12 B per key) and the records in list
-    # order (48 B per key) dominate
+    # proj + grad2d (48 B each per visible-pair slot: all 500k pairs by default), keys + values
+    # (2 x 12 B per key) and the records in list order (48 B per key) dominate
     assert 500_000 * 96 + (1 << 21) * 72 < n.value < 500_000 * 140 + (1 << 21) * 90
+    n_full = C.c_size_t(n.value)
     bad = [_problem(V=0), _problem(W=0), _problem(cap=0), _problem(cap=1 << 30), _problem(tile_w=8),
            _problem(alpha_max=1.5), _problem(t_min=0.0), _problem(near_plane=0.0), _problem(sort_mode=2),
            _problem(batch_records=100), _problem(batch_records=256, tile_h=8)]
+    neg = _problem()
+    neg.visible_capacity = -1
+    bad.append(neg)
     for b in bad:
         assert lib.gs_workspace_size(C.byref(b), C.byref(n)) == L.GS_ERR_INVALID_ARG
+    # a visible-pair capacity below the pair count shrinks the records and 2-D gradients (96 B each)
+    small = _problem()
+    small.visible_capacity = 100_000
+    m = C.c_size_t()
+    assert lib.gs_workspace_size(C.byref(small), C.byref(m)) == 0
+    assert m.value == n_full.value - 400_000 * 96
     pb = _problem(V=2)
     vc = np.array([10, 20], np.int64)
     vb = np.array([0, 500_000 - 5], np.int64)       # second view overruns the arrays

@@ -232,6 +232,27 @@ def test_capacity_overflow_reports_required_keys(R, mode):
     assert ok["rc"] == 0 and ok["K"] == orc.K
 
 
+@pytest.mark.parametrize("mode", SORT_MODES)
+def test_visible_capacity_overflow_reports_and_recovers(R, mode):
+    """A visible-pair capacity below the number of visible pairs records GS_ERR_CAPACITY and reports
+    the count needed; forward_checked then grows it and the result is the oracle's."""
+    wl = S.workload("cloud10k", scale=0.3)
+    p = R.default_params(sort_mode=mode)
+    pb, g = gpu_problem(wl, params=p)
+    pb.set_capacity(pb.cap, visible=100)
+    pb.project(g)
+    pb.bin_sort()
+    rc, _ = pb.check_status()
+    nv = pb.stats()["num_visible"]
+    orc = run_oracle(wl, params=p)
+    vis_oracle = int((orc["proj"]["touched"] > 0).sum())
+    assert rc == R.L.GS_ERR_CAPACITY and nv == vis_oracle > 100
+    img = pb.forward_checked(g)
+    assert pb.vcap >= nv
+    np.testing.assert_array_equal(img["last_idx"].cpu().numpy(), orc["fwd"]["last"])
+    assert np.abs(img["rgb"].cpu().numpy() - orc["fwd"]["rgb"]).max() <= TOL_IMAGE
+
+
 def test_bounded_wait_times_out_and_recovers(R):
     import ctypes as C
     L = R.L.load()
