@@ -167,6 +167,12 @@ typedef struct gs_ws_view {
     int32_t reserved;
     uint32_t *pair_slot;               /* [P] slot of each visible pair, 0xffffffff if culled */
     int64_t visible_capacity;          /* slots in proj and grad2d */
+    uint32_t *claim_count;             /* [32] items in each claim class */
+    uint32_t *claim_list;              /* [32, G] the (view, tile) items of each claim class k in
+                                          claim_list[k*G .. k*G + claim_count[k]); class k holds
+                                          lists of n entries with 2 min(floor(log2 n), 15) + (the
+                                          bit below the leading one) = 31 - k.  The compositing
+                                          kernels claim class 0 (longest lists) first. */
 } gs_ws_view;
 
 /* Statistics of the last calls, read by gs_read_stats (synchronises the stream). */
@@ -207,7 +213,7 @@ int gs_read_stats(const gs_problem *pb, void *ws, void *stream, gs_stats *out);
  * blocks of a fixed byte pattern, written by gs_workspace_init, follow every workspace buffer that
  * kernels index with data (projection records, tile counts, both key and value buffers, the tile
  * ranges and lists, the records in list order, the 2-D gradients, the pose partials, the pair
- * slots).  This call
+ * slots, the claim-class lists).  This call
  * synchronises `stream` and returns GS_OK when every block is intact, else GS_ERR_DEVICE_FAULT with
  * *first_bad (may be NULL) = the index of the first changed block in that order. */
 int gs_check_guards(const gs_problem *pb, void *ws, void *stream, int32_t *first_bad);
@@ -227,8 +233,10 @@ int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stre
 
 /* Tile binning (params.sort_mode selects the algorithm, see GS_SORT_*): per-tile lists ordered by
  * (depth bits, flattened pair index), their [start, end) ranges, the sorted keys/values and the
- * projection records in list order.  K > key_capacity records GS_ERR_CAPACITY (keys beyond
- * capacity dropped). */
+ * projection records in list order, and the order in which the compositing kernels claim the
+ * (view, tile) work items: longer lists first (no counterpart in the paper: scheduling only, no
+ * result depends on it), so that a persistent launch does not end on a long tile claimed last.
+ * K > key_capacity records GS_ERR_CAPACITY (keys beyond capacity dropped). */
 int gs_bin_sort(const gs_problem *pb, void *ws, void *stream);
 
 /* Front-to-back compositing of every (view, tile) of the problem in one persistent launch.

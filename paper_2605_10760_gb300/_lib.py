@@ -74,7 +74,7 @@ class gs_ws_view(C.Structure):
                 ("sorted_vals", C.c_void_p), ("tile_ranges", C.c_void_p), ("grad2d", C.c_void_p),
                 ("num_keys", C.c_void_p), ("num_pairs", C.c_int64), ("num_tiles", C.c_int64),
                 ("sort_passes", C.c_int32), ("reserved", C.c_int32), ("pair_slot", C.c_void_p),
-                ("visible_capacity", C.c_int64)]
+                ("visible_capacity", C.c_int64), ("claim_count", C.c_void_p), ("claim_list", C.c_void_p)]
 
 
 class gs_stats(C.Structure):

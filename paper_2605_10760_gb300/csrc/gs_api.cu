@@ -116,6 +116,7 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     L->o_hist = o; o = align256(o + sizeof(uint32_t) * kMaxPasses * 256);
     L->o_sort_state = o; o = align256(o + sizeof(uint32_t) * 256 * (size_t)L->sort_parts * L->passes);
     L->o_ranges = o; o = align256(o + sizeof(uint32_t) * 2 * (size_t)L->G);
+    L->o_tword = o; o = align256(o + sizeof(unsigned long long) * (size_t)L->G);
     guard();
     L->o_tcnt = o; o = align256(o + sizeof(uint32_t) * ((size_t)L->G + 1) + 64);
     L->o_tlist = o; o = align256(o + sizeof(uint32_t) * (size_t)L->G);
@@ -127,6 +128,8 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     L->o_pose_part = o; o = align256(o + sizeof(float) * 8 * (size_t)std::max<long long>(chunks_total, 1));
     guard();
     L->o_slot = o; o = align256(o + sizeof(uint32_t) * (size_t)std::max<long long>(P, 1));
+    guard();
+    L->o_clist = o; o = align256(o + sizeof(uint32_t) * kClaimClasses * (size_t)std::max<long long>(L->G, 1));
     guard();
     if (ng != kNumGuards) return GS_ERR_INVALID_ARG;   // the layout and kNumGuards disagree: a build error
     L->total = o;
@@ -247,6 +250,8 @@ int gs_workspace_view(const gs_problem *pb, void *ws, gs_ws_view *out) {
     out->reserved = 0;
     out->pair_slot = ws_ptr<uint32_t>(ws, L.o_slot);
     out->visible_capacity = L.vcap;
+    out->claim_count = ws_ptr<DevStatus>(ws, L.o_status)->claim_cnt;
+    out->claim_list = ws_ptr<uint32_t>(ws, L.o_clist);
     return GS_OK;
 }
 
@@ -404,8 +409,10 @@ static BinArgs make_bin_args(const Layout &L, void *ws) {
     a.sort_mode = L.sort_mode;
     a.tile_cnt = ws_ptr<uint32_t>(ws, L.o_tcnt);
     a.tile_list = ws_ptr<uint32_t>(ws, L.o_tlist);
+    a.tword = ws_ptr<unsigned long long>(ws, L.o_tword);
+    a.clist = ws_ptr<uint32_t>(ws, L.o_clist);
     a.clear_begin = ws_ptr<unsigned char>(ws, L.o_scan_state);
-    a.clear_bytes = L.o_ranges + sizeof(uint32_t) * 2 * (size_t)L.G - L.o_scan_state;
+    a.clear_bytes = L.o_tword + sizeof(unsigned long long) * (size_t)L.G - L.o_scan_state;
     return a;
 }
 
@@ -429,6 +436,7 @@ static int render_fwd_impl(const gs_problem *pb, void *ws, const gs_image *out, 
     FwdArgs a;
     a.srec = ws_ptr<const float4>(ws, L.o_srec);
     a.ranges = ws_ptr<const uint32_t>(ws, L.o_ranges);
+    a.clist = ws_ptr<const uint32_t>(ws, L.o_clist);
     a.rgb = out->rgb; a.depth = out->depth; a.alpha = out->alpha; a.finalT = out->final_T; a.last = out->last_idx;
     a.st = ws_ptr<DevStatus>(ws, L.o_status);
     a.W = L.W; a.H = L.H; a.Tx = L.Tx; a.Ty = L.Ty; a.G = L.G; a.P = std::max<long long>(L.P, 1);
@@ -475,6 +483,7 @@ int gs_render_bwd_composite(const gs_problem *pb, void *ws, const gs_image *fwd,
     BwdArgs a;
     a.srec = ws_ptr<const float4>(ws, L.o_srec);
     a.ranges = ws_ptr<const uint32_t>(ws, L.o_ranges);
+    a.clist = ws_ptr<const uint32_t>(ws, L.o_clist);
     a.finalT = fwd->final_T; a.last = fwd->last_idx;
     a.d_rgb = dimg->d_rgb; a.d_depth = dimg->d_depth; a.d_alpha = dimg->d_alpha;
     a.g2d = ws_ptr<float>(ws, L.o_g2d);

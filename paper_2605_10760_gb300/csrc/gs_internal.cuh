@@ -44,6 +44,7 @@ struct DevStatus {
     unsigned long long bwd_pairs;
     uint32_t bwd_items, bwd_pad;
     uint32_t ctr[kNumCounters];
+    uint32_t claim_cnt[32];       // items in each claim class (cleared with ctr by gs_bin_sort)
     int32_t guard_bad;            // gs_check_guards: index of the first changed guard block
     int32_t guard_pad;
     unsigned long long num_visible;   // visible pairs of the last projection (slot counter)
@@ -56,6 +57,8 @@ struct ViewEntry {                // per-view table in the workspace (32 bytes)
     long long chunk_off;
 };
 
+constexpr int kNumGuards = 13;
+
 struct Layout {
     int V, W, H, tw, th, Tx, Ty, passes;
     long long G, P, N, cap, max_count, max_chunks;
@@ -63,12 +66,16 @@ struct Layout {
     long long scan_parts, sort_parts, chunks_total;
     int sort_mode, nb;                 // binning mode; records per staged render batch
     size_t o_status, o_views, o_proj, o_touched, o_scan_state, o_keys[2], o_vals[2], o_hist,
-        o_sort_state, o_ranges, o_tcnt, o_tlist, o_srec, o_g2d, o_pose_part, o_slot, total;
-    size_t o_guard[12];                // guard blocks after proj, touched, keys x2, vals x2, ranges,
-                                       // the tile lists, srec, g2d, the pose partials and the slots
+        o_sort_state, o_ranges, o_tword, o_tcnt, o_tlist, o_srec, o_g2d, o_pose_part, o_slot, o_clist, total;
+    size_t o_guard[kNumGuards];        // guard blocks after proj, touched, keys x2, vals x2, ranges,
+                                       // the tile lists, srec, g2d, the pose partials, the slots
+                                       // and the claim-class lists
 };
-constexpr int kNumGuards = 12;
 constexpr uint32_t kNoSlot = 0xffffffffu;   // pair_slot of a culled pair
+// The compositing kernels claim (view, tile) items class by class: class k lists the items whose
+// list length n has 2 min(floor(log2 n), 15) + (the bit below the leading one) = 31 - k, so class
+// 0 holds the longest lists and class 31 the lists of 0 or 1 entries (k = 0 from 2^16 entries on).
+constexpr int kClaimClasses = 32;
 constexpr size_t kGuardBytes = 256;
 constexpr int kGuardByte = 0x5A;       // every byte of an intact guard block
 

@@ -71,6 +71,8 @@ struct BinArgs {
     uint32_t *tile_list;               // [G] tiles whose slices are sorted by k_tile_sort_long
     const uint32_t *slot;              // [P] slot of each visible pair in proj and g2d
     long long vcap;                    // slots in proj and g2d
+    unsigned long long *tword;         // [G] start/end combining words of the ranges kernel
+    uint32_t *clist;                   // [kClaimClasses, G] out: the items of each claim class
 };
 
 // onesweep: scan with key emission and digit histograms -> onesweep passes -> ranges; tile bucket: scan of the
@@ -84,6 +86,7 @@ int run_scan_only(const BinArgs &a, cudaStream_t s);
 struct FwdArgs {
     const float4 *srec;                // [K,3] records in list order (r1.w = the pair's slot, as bits)
     const uint32_t *ranges;
+    const uint32_t *clist;             // [kClaimClasses, G] items of each claim class (counts in st)
     float *rgb, *depth, *alpha, *finalT;
     int32_t *last;
     DevStatus *st;
@@ -100,6 +103,7 @@ struct FwdArgs {
 struct BwdArgs {
     const float4 *srec;
     const uint32_t *ranges;
+    const uint32_t *clist;             // [kClaimClasses, G] items of each claim class (counts in st)
     const float *finalT;
     const int32_t *last;
     const float *d_rgb, *d_depth, *d_alpha;

@@ -124,6 +124,44 @@ __device__ __forceinline__ uint32_t warp_region_mask(const float4 &r0, const flo
 
 constexpr unsigned long long kTmaWaitLimit = 1ull << 22;   // polls of a batch's mbarrier before giving up
 
+// Claim order: the binning lists every (view, tile) item under its claim class (class 0 the
+// longest lists); coff[k] is the number of items in classes below k (coff[kClaimClasses] = all),
+// so the counter's value c falls in the class k with coff[k] <= c < coff[k + 1].
+__device__ __forceinline__ void claim_offsets(const DevStatus *st, uint32_t *coff) {
+    if (threadIdx.x < 32) {
+        static_assert(kClaimClasses == 32, "one class per lane");
+        const uint32_t x = st->claim_cnt[threadIdx.x];
+        uint32_t y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
+            if ((int)threadIdx.x >= o) y += t;
+        }
+        coff[threadIdx.x] = y - x;
+        if (threadIdx.x == 31) coff[32] = y;
+    }
+}
+
+// Next work item of a persistent compositing CTA (thread 0), -1 when all are taken.  Class lists
+// inconsistent with G (only after an earlier binning failure) record a device fault; the claim then
+// falls back to the counter's own value.
+__device__ __forceinline__ long long claim_item(DevStatus *st, unsigned int *ctr, const uint32_t *coff,
+                                                const uint32_t *clist, long long G) {
+    const long long c = (long long)atomicAdd(ctr, 1u);
+    if (c >= min((long long)coff[kClaimClasses], G)) return -1;
+    int k = 0;   // the largest k with coff[k] <= c (coff[0] = 0)
+#pragma unroll
+    for (int step = kClaimClasses / 2; step > 0; step >>= 1)
+        if ((long long)coff[k + step] <= c) k += step;
+    const long long r = c - (long long)coff[k];
+    const uint32_t g = r < G ? clist[(size_t)k * G + r] : 0xffffffffu;
+    if ((long long)g >= G) {
+        record_error(st, GS_ERR_DEVICE_FAULT, 10);
+        return c;
+    }
+    return (long long)g;
+}
+
 // Shared memory of one render CTA: two batches of records (double buffer filled by TMA), the
 // per-entry warp-region masks of each batch, one mbarrier per buffer.
 // NB records per staged batch: 64, 128 or 256, at most one per pixel of the tile (two buffers of
@@ -135,6 +173,7 @@ struct __align__(128) RenderSmem {
     uint64_t bar[2];
     long long item;
     int maxlast;
+    uint32_t coff[kClaimClasses + 1];   // claim-class offsets (claim_offsets)
 };
 
 // Waits for both buffers' outstanding copies (bounded) after a failed wait, so that the CTA never
@@ -166,15 +205,16 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
         mbar_init(&sm.bar[1], 1);
         fence_proxy_async_smem();
     }
+    claim_offsets(a.st, sm.coff);
     __syncthreads();
     uint32_t parity[2] = {0u, 0u};
     unsigned long long pairs = 0;
     float l1_rgb = 0.f, l1_d = 0.f;      // per-thread sums of |rendered - target| (L1 epilogue)
     for (;;) {
-        if (tid == 0) sm.item = (long long)atomicAdd(&a.st->fwd_items, 1u);
+        if (tid == 0) sm.item = claim_item(a.st, &a.st->fwd_items, sm.coff, a.clist, a.G);
         __syncthreads();
         const long long g = sm.item;
-        if (g >= a.G) break;
+        if (g < 0) break;
         const int v = (int)(g / tpv);
         const int tl = (int)(g - (long long)v * tpv);
         const int ty = tl / a.Tx, tx = tl - ty * a.Tx;
@@ -392,17 +432,18 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
         mbar_init(&sm.bar[1], 1);
         fence_proxy_async_smem();
     }
+    claim_offsets(a.st, sm.coff);
     __syncthreads();
     uint32_t parity[2] = {0u, 0u};
     unsigned long long pairs = 0;
     for (;;) {
         if (tid == 0) {
-            sm.item = (long long)atomicAdd(&a.st->bwd_items, 1u);
+            sm.item = claim_item(a.st, &a.st->bwd_items, sm.coff, a.clist, a.G);
             sm.maxlast = 0;
         }
         __syncthreads();
         const long long g = sm.item;
-        if (g >= a.G) break;
+        if (g < 0) break;
         const int v = (int)(g / tpv);
         const int tl = (int)(g - (long long)v * tpv);
         const int ty = tl / a.Tx, tx = tl - ty * a.Tx;

@@ -15,7 +15,10 @@
 //                  places the partition in digit order in shared memory, looks back over its
 //                  predecessors' counts (bounded spins) and writes each digit run contiguously;
 //   4. k_ranges    [start, end) of every global tile in the sorted keys, and every entry's record
-//                  copied into list order (so a tile's list is one contiguous block for TMA).
+//                  copied into list order (so a tile's list is one contiguous block for TMA);
+//                  As it finds each tile's list length it appends the tile to the list of its
+//                  claim class (half-octave length classes: the compositing kernels claim the
+//                  longest lists first).
 // Depth is positive (z > near > 0), so its float bit pattern orders like its value, and the sort is
 // stable, so equal keys keep the emission order (ascending flattened index).
 //
@@ -30,8 +33,9 @@
 //      exactly (depth bits, index)); slices above kWarpSortMax words go to k_tile_sort_long, one
 //      CTA per tile, with slices above kTileSortMax words as sorted runs merged pairwise in global
 //      memory.  Both write the tile's range, the sorted keys and values and the records in list
-//      order.
+//      order, and append each tile to its claim class.
 #include <algorithm>
+#include <cstddef>
 
 #include "gs_kernels.cuh"
 
@@ -523,12 +527,49 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------
-// 4. tile ranges
+// 4. claim classes of the compositing kernels' work items
 // ------------------------------------------------------------------------------------------
-__global__ void k_ranges(const uint64_t *keys, const uint32_t *vals, const float4 *proj, const uint32_t *slot,
-                         long long vcap, float4 *srec, DevStatus *st, long long cap, long long G, long long P,
-                         uint32_t *ranges) {
+// The persistent compositing kernels claim (view, tile) items from a counter.  Claimed in tile
+// order, a long list taken near the end keeps its CTA running after the others have finished;
+// claimed longest first, the last items are the short ones.  So every item is appended, once its
+// list length is known, to the list of its claim class (half-octave length classes, class 0 the
+// longest), and the kernels claim class by class.  The position inside a class is arbitrary: the
+// order moves no result, only when each tile is composited.
+__device__ __forceinline__ int claim_class(uint32_t n) {
+    const int e = 31 - __clz(n | 1u);
+    if (e > 15) return 0;
+    const int half = e >= 1 ? (int)((n >> (e - 1)) & 1u) : 0;
+    return kClaimClasses - 1 - (2 * e + half);
+}
+
+// items first .. first + count - 1 into class c's list (one atomic for the run)
+__device__ __forceinline__ void claim_append(DevStatus *st, uint32_t *clist, long long G, int c, long long first,
+                                             long long count) {
+    const unsigned long long pos = atomicAdd(&st->claim_cnt[c], (uint32_t)count);
+    if ((long long)pos + count > G) {   // only after an earlier failure (an item listed twice)
+        record_error(st, GS_ERR_DEVICE_FAULT, 12);
+        return;
+    }
+    uint32_t *dst = clist + (size_t)c * G + pos;
+    for (long long j = 0; j < count; ++j) dst[j] = (uint32_t)(first + j);
+}
+
+// ------------------------------------------------------------------------------------------
+// 5. tile ranges
+// ------------------------------------------------------------------------------------------
+constexpr int kRangesThreads = 256;
+__global__ void __launch_bounds__(kRangesThreads) k_ranges(const uint64_t *keys, const uint32_t *vals,
+                                                           const float4 *proj, const uint32_t *slot, long long vcap,
+                                                           float4 *srec, DevStatus *st, long long cap, long long G,
+                                                           long long P, uint32_t *ranges, unsigned long long *tword,
+                                                           uint32_t *clist) {
     const unsigned long long K = min(st->num_keys, (unsigned long long)cap);
+    if (K == 0) {   // every tile empty: all in the last claim class, in tile order
+        for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x)
+            clist[(size_t)(kClaimClasses - 1) * G + g] = (uint32_t)g;
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->claim_cnt[kClaimClasses - 1] = (uint32_t)G;
+        return;
+    }
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < K;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long g = keys[i] >> 32;
@@ -537,8 +578,28 @@ __global__ void k_ranges(const uint64_t *keys, const uint32_t *vals, const float
             record_error(st, GS_ERR_DEVICE_FAULT, 5);
             continue;
         }
-        if (i == 0 || (keys[i - 1] >> 32) != g) ranges[2 * g] = (uint32_t)i;
-        if (i == K - 1 || (keys[i + 1] >> 32) != g) ranges[2 * g + 1] = (uint32_t)(i + 1);
+        const bool first = i == 0 || (keys[i - 1] >> 32) != g;
+        const unsigned long long gn = i == K - 1 ? (unsigned long long)G : keys[i + 1] >> 32;
+        const bool last = gn != g;
+        if (first) ranges[2 * g] = (uint32_t)i;
+        if (last) ranges[2 * g + 1] = (uint32_t)(i + 1);
+        // claim class of the tile: the thread at its first entry and the one at its last add
+        // (1 << 56) + 2^33 - start and (1 << 56) + end to the tile's word; the second one to add
+        // sees one arrival in the top bits and takes n = end - start from the sum
+        if (first && last) {
+            claim_append(st, clist, G, claim_class(1u), (long long)g, 1);
+        } else if (first || last) {
+            const unsigned long long mine = (1ull << 56) + (first ? (1ull << 33) - i : i + 1);
+            const unsigned long long old = atomicAdd(&tword[g], mine);
+            if ((old >> 56) == 1ull) {
+                const unsigned long long n = ((old + mine) & ((1ull << 56) - 1)) - (1ull << 33);
+                claim_append(st, clist, G, claim_class((uint32_t)min(n, 0xffffffffull)), (long long)g, 1);
+            }
+        }
+        // empty tiles: those between this tile and the next key's (or the end), and before the first key
+        if (last && gn > g + 1)
+            claim_append(st, clist, G, kClaimClasses - 1, (long long)g + 1, (long long)(gn - g - 1));
+        if (i == 0 && g > 0) claim_append(st, clist, G, kClaimClasses - 1, 0, (long long)g);
         // the entry's record in list order, so a tile's batch is one contiguous block;
         // the radius field (used only by key emission) carries the pair's slot instead
         const uint32_t sl = slot[f];
@@ -723,6 +784,7 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(BinArgs a) {
         if (lane == 0) {   // an empty tile reads [0, 0), as the onesweep path leaves it
             a.ranges[2 * g] = n > 0 ? (uint32_t)s : 0u;
             a.ranges[2 * g + 1] = n > 0 ? (uint32_t)(s + n) : 0u;
+            claim_append(a.st, a.clist, a.G, claim_class((uint32_t)n), g, 1);
         }
         if (n == 0) continue;
         if (n > kWarpSortMax) {
@@ -887,8 +949,10 @@ static int sweep_passes(const BinArgs &a, cudaStream_t s) {
 }
 
 int run_bin_sort(const BinArgs &a, cudaStream_t s) {
-    // counters of the scan, of every sort pass and of the per-tile sort
-    if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t) * (kCtrTileLong + 1), s) != cudaSuccess)
+    // counters of the scan, of every sort pass and of the per-tile sort, and the claim-class counts
+    static_assert(offsetof(DevStatus, claim_cnt) == offsetof(DevStatus, ctr) + sizeof(uint32_t) * kNumCounters,
+                  "the claim-class counts follow the counters");
+    if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t) * (kNumCounters + kClaimClasses), s) != cudaSuccess)
         return GS_ERR_CUDA;
     if (a.sort_mode == GS_SORT_TILE_BUCKET) return run_bucket(a, s);
     // look-back words of the scan and of every pass, digit histograms and tile ranges
@@ -908,9 +972,8 @@ int run_bin_sort(const BinArgs &a, cudaStream_t s) {
     }
     const int rc2 = sweep_passes<kSortIPT>(a, s);
     if (rc2) return rc2;
-    k_ranges<<<sms * 8, 256, 0, s>>>(a.keys[a.passes & 1], a.vals[a.passes & 1], a.proj, a.slot, a.vcap, a.srec, a.st,
-                                      a.cap, a.G,
-                                      a.P, a.ranges);
+    k_ranges<<<sms * 8, kRangesThreads, 0, s>>>(a.keys[a.passes & 1], a.vals[a.passes & 1], a.proj, a.slot, a.vcap,
+                                                 a.srec, a.st, a.cap, a.G, a.P, a.ranges, a.tword, a.clist);
     count_launches(1);
     return check_launch();
 }

@@ -93,7 +93,7 @@ class Problem:
         if key_capacity is None:
             key_capacity = int(min((1 << 30) - 1, max(1 << 20, 4 * self.P)))
         self.cap = int(key_capacity)
-        self.vcap = int(visible_capacity)          # 0: min(pairs, key capacity), always enough
+        self.vcap = int(visible_capacity)          # 0: all pairs, always enough
         self.cameras = cameras
         self._pb = L.gs_problem()
         self._sync_struct()
@@ -169,7 +169,9 @@ class Problem:
                     sorted_keys=sl(v.sorted_keys, self.cap, torch.int64),
                     sorted_vals=sl(v.sorted_vals, self.cap, torch.int32),
                     tile_ranges=sl(v.tile_ranges, 2 * G, torch.int32).view(G, 2),
-                    num_keys=sl(v.num_keys, 2, torch.int32), passes=int(v.sort_passes), visible_capacity=VC)
+                    num_keys=sl(v.num_keys, 2, torch.int32), passes=int(v.sort_passes), visible_capacity=VC,
+                    claim_count=sl(v.claim_count, 32, torch.int32),
+                    claim_list=sl(v.claim_list, 32 * G, torch.int32).view(32, G))
 
     def check_status(self):
         req = C.c_int64()

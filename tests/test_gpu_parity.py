@@ -42,6 +42,7 @@ def run_gpu(R, wl, views=None, params=None, key_capacity=None, grads=True, seed=
     out["keys"] = ws["sorted_keys"][:K].cpu().numpy().view(np.uint64)
     out["vals"] = ws["sorted_vals"][:K].cpu().numpy().view(np.uint32)
     out["ranges"] = ws["tile_ranges"].cpu().numpy().view(np.uint32)
+    out["claim"] = (ws["claim_count"].cpu().numpy().view(np.uint32), ws["claim_list"].cpu().numpy().view(np.uint32))
     img = pb.render_fwd()
     out["img"] = {k: v.cpu().numpy() for k, v in img.items()}
     if grads:
@@ -71,6 +72,29 @@ def run_oracle(wl, views=None, params=None, up=None):
     return res
 
 
+def claim_class(n):
+    """Claim class of a list of n entries: 31 - (2 floor(log2 n) + the bit below the leading one),
+    so class 0 holds the longest lists; lengths 0 and 1 are class 31, lengths from 2^16 on class 0."""
+    n = np.maximum(np.asarray(n, np.int64), 1)
+    e = np.floor(np.log2(n)).astype(np.int64)
+    half = np.where(e >= 1, (n >> np.maximum(e - 1, 0)) & 1, 0)
+    return np.where(e > 15, 0, 31 - (2 * e + half))
+
+
+def check_claim_classes(count, lists, ranges):
+    """The compositing kernels claim the (view, tile) items class by class, longest lists first: every
+    item is listed exactly once, under the class of its list length (scheduling only: the images and
+    gradients do not depend on it; the order inside a class is arbitrary)."""
+    G = ranges.shape[0]
+    assert count.shape == (32,) and lists.shape == (32, G)
+    assert int(count.astype(np.int64).sum()) == G
+    items = [lists[k, :count[k]].astype(np.int64) for k in range(32)]
+    np.testing.assert_array_equal(np.sort(np.concatenate(items)), np.arange(G))
+    cls = claim_class(np.diff(ranges.astype(np.int64), axis=1)[:, 0])
+    for k in range(32):
+        assert (cls[items[k]] == k).all(), k
+
+
 def compare_all(gpu, orc, check_grads=True):
     op = orc["proj"]
     np.testing.assert_array_equal(gpu["touched"], op["touched"])
@@ -85,6 +109,7 @@ def compare_all(gpu, orc, check_grads=True):
     np.testing.assert_array_equal(gpu["keys"], ob["keys"])
     np.testing.assert_array_equal(gpu["vals"], ob["vals"])
     np.testing.assert_array_equal(gpu["ranges"].reshape(-1, 2), ob["ranges"])
+    check_claim_classes(*gpu["claim"], ob["ranges"])
     of, gi = orc["fwd"], gpu["img"]
     np.testing.assert_array_equal(gi["last_idx"], of["last"])
     for k, ko in (("rgb", "rgb"), ("depth", "depth"), ("alpha", "alpha"), ("final_T", "final_T")):
