@@ -57,7 +57,7 @@ struct ViewEntry {                // per-view table in the workspace (32 bytes)
     long long chunk_off;
 };
 
-constexpr int kNumGuards = 13;
+constexpr int kNumGuards = 15;
 
 struct Layout {
     int V, W, H, tw, th, Tx, Ty, passes;
@@ -66,10 +66,11 @@ struct Layout {
     long long scan_parts, sort_parts, chunks_total;
     int sort_mode, nb;                 // binning mode; records per staged render batch
     size_t o_status, o_views, o_proj, o_touched, o_scan_state, o_keys[2], o_vals[2], o_hist,
-        o_sort_state, o_ranges, o_tword, o_tcnt, o_tlist, o_srec, o_g2d, o_pose_part, o_slot, o_clist, total;
+        o_sort_state, o_ranges, o_tword, o_tcnt, o_tlist, o_srec, o_g2d, o_pose_part, o_slot, o_clist, o_slane,
+        o_blk, total;
     size_t o_guard[kNumGuards];        // guard blocks after proj, touched, keys x2, vals x2, ranges,
-                                       // the tile lists, srec, g2d, the pose partials, the slots
-                                       // and the claim-class lists
+                                       // the tile lists, srec, g2d, the pose partials, the slots,
+                                       // the claim-class lists, the slot lanes, the block slot ranges
 };
 constexpr uint32_t kNoSlot = 0xffffffffu;   // pair_slot of a culled pair
 // The compositing kernels claim (view, tile) items class by class: class k lists the items whose

@@ -21,15 +21,19 @@ struct ProjArgs {
     DevStatus *st;              // errors; num_visible is the slot counter
     uint32_t *slot;             // [P] slot of each visible pair in proj (kNoSlot when culled)
     long long vcap;             // slots in proj
+    uint8_t *slane;             // [vcap] thread (pair) of its projection block that holds each slot
+    uint4 *blk;                 // [chunks] first slot and visible-pair count of each projection
+                                //   block's two rounds
+    long long chunks;           // projection blocks over all views (the length of blk)
 };
 
 struct ProjBwdArgs {
     const ViewEntry *views;
     const gs_camera *cams;
     const float *means, *log_scales, *quats;
-    const uint32_t *touched_incl;   // inclusive prefix sums (nonzero increment = visible), or
-    int touched_is_count;           // ... the counts themselves (nonzero = visible) when 1
-    const float4 *g2d;              // [P,3] float4
+    const uint8_t *slane;           // [vcap] thread of its projection block that holds each slot
+    const uint4 *blk;               // [chunks] first slot and visible count of the block's two rounds
+    const float4 *g2d;              // [vcap,3] float4
     float *g_means, *g_ls, *g_quats, *g_op, *g_col;
     float *pose_part;               // [chunks, 8]
     int W, H;

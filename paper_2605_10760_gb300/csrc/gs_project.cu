@@ -1,7 +1,9 @@
 // gs_project.cu -- EWA projection of (view, Gaussian) pairs and its adjoint.
 //
-// Forward: the FP32 decision chain of gs_internal.cuh; one thread per pair, grid (chunk, view).
-// Backward: the chain rule through the same projection in FP32 value arithmetic, accumulating
+// Forward: the FP32 decision chain of gs_internal.cuh, grid (chunk, view), a pre-test per pair and
+// the chain on the block's compacted candidates.
+// Backward: per block, one thread per visible pair of the forward's block (its slot range); the
+// chain rule through the same projection in FP32 value arithmetic, accumulating
 // dL/d(mean, log-scale, quaternion, opacity, colour) with atomics (several views of one scene add
 // into the same Gaussian; a reduction is issued without waiting for a result, which also makes it
 // cheaper than a load and a store where no two views share a Gaussian) and the per-view SE(3) pose
@@ -12,85 +14,182 @@ namespace gs {
 
 
 
-__global__ void __launch_bounds__(kChunk) k_project(ProjArgs a) {
+// Pre-test of a pair before the decision chain: false only when the chain certainly finds the pair
+// invisible.  The near-plane test and the mean are the chain's own operations; the radius is
+// bounded from above: lambda_max(Sigma_2) <= trace = |U|_F^2 + 2 dilation with
+// |U|_F <= |W|_F |M|_F, |M|_F^2 = s0^2 + s1^2 + s2^2 (unit quaternion) and
+// |W|_F^2 <= (wx^2 + wy^2) / z^2 (wx = |fx| (|R_0| + |limx| |R_2|), wy likewise: the clamped
+// Jacobian and the camera rows; `wb2` = wx^2 + wy^2 per view).  The bound is padded by 2 % in
+// lambda, 1 % in the radius and one pixel, far above the FP32 error of either side, and the tile
+// rectangle grows monotonically with the radius; a non-finite bound or a non-positive sigma
+// multiplier never rejects.
+__device__ __forceinline__ bool may_be_visible(const float *R, const float *t, float fx, float fy, float cx, float cy,
+                                               float wb2, float itw, float ith, float Tx, float Ty, float near_plane,
+                                               float dil, float sigmas, float m0, float m1, float m2,
+                                               const float *ls) {
+    using namespace fp;
+    const float xc = fma(R[0], m0, fma(R[1], m1, fma(R[2], m2, t[0])));
+    const float yc = fma(R[3], m0, fma(R[4], m1, fma(R[5], m2, t[1])));
+    const float zc = fma(R[6], m0, fma(R[7], m1, fma(R[8], m2, t[2])));
+    if (!(zc > near_plane)) return false;
+    if (!(sigmas > 0.0f)) return true;
+    const float iz = div(1.0f, zc);
+    const float mx = fma(fx, mul(xc, iz), cx), my = fma(fy, mul(yc, iz), cy);
+    const float ssum = __expf(2.0f * __ldg(ls)) + __expf(2.0f * __ldg(ls + 1)) + __expf(2.0f * __ldg(ls + 2));
+    const float lam = (wb2 * iz * iz * ssum + 2.0f * fmaxf(dil, 0.0f)) * 1.02f;
+    const float rb = sigmas * sqrtf(lam) * 1.01f + 1.0f;
+    if (!(rb >= 0.0f && rb < 1e30f)) return true;
+    int x0, x1, y0, y1;
+    spec_rect(mx, my, rb, itw, ith, Tx, Ty, x0, x1, y0, y1);
+    return x1 > x0 && y1 > y0;
+}
+
+// One block of kProjThreads threads = the 256 pairs (chunk) of one view.  Phase 1: each thread
+// pre-tests two pairs (may_be_visible); the candidates are compacted in pair order.  Phase 2: the
+// candidates run the decision chain on dense lanes, kProjThreads at a time; the visible pairs of
+// each round take consecutive slots (ballot + warp counts; the round's first slot from one atomic
+// on the slot counter).  The block records each round's first slot and count (blk: at most two
+// rounds) and, per slot, the pair's position in the chunk (slane): the adjoint walks exactly these
+// slots.  Slots beyond the capacity record GS_ERR_CAPACITY and their pairs are dropped.
+constexpr int kProjThreads = 128;
+constexpr int kProjRounds = kChunk / kProjThreads;
+static_assert(kProjRounds == 2, "blk holds two slot ranges per chunk");
+
+__global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
     const int v = blockIdx.y;
     __shared__ ViewEntry s_ve;
-    __shared__ float s_cam[18];   // R, t, fx, fy, cx, cy, then the view's Jacobian clamp limits
+    __shared__ float s_cam[19];   // R, t, fx, fy, cx, cy, the clamp limits, then wb2
+    __shared__ uint8_t s_cl[kChunk];
+    __shared__ uint32_t s_wcnt[kProjRounds][kProjThreads / 32];
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_rng[2 * kProjRounds];
     if (threadIdx.x == 0) s_ve = a.views[v];
     if (threadIdx.x < 16) s_cam[threadIdx.x] = reinterpret_cast<const float *>(a.cams + v)[threadIdx.x];
     if (threadIdx.x == 32) {      // once per view and block, the same operations as the per-pair chain
         const gs_camera &c = a.cams[v];
-        s_cam[16] = fp::div(fp::mul(0.65f, (float)a.W), c.fx);
-        s_cam[17] = fp::div(fp::mul(0.65f, (float)a.H), c.fy);
+        const float limx = fp::div(fp::mul(0.65f, (float)a.W), c.fx);
+        const float limy = fp::div(fp::mul(0.65f, (float)a.H), c.fy);
+        s_cam[16] = limx;
+        s_cam[17] = limy;
+        const float n0 = sqrtf(c.R[0] * c.R[0] + c.R[1] * c.R[1] + c.R[2] * c.R[2]);
+        const float n1 = sqrtf(c.R[3] * c.R[3] + c.R[4] * c.R[4] + c.R[5] * c.R[5]);
+        const float n2 = sqrtf(c.R[6] * c.R[6] + c.R[7] * c.R[7] + c.R[8] * c.R[8]);
+        const float wx = fabsf(c.fx) * (n0 + fabsf(limx) * n2), wy = fabsf(c.fy) * (n1 + fabsf(limy) * n2);
+        s_cam[18] = wx * wx + wy * wy;
     }
+    if (threadIdx.x < 2 * kProjRounds) s_rng[threadIdx.x] = 0u;
     __syncthreads();
-    const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
-    const bool in = i < s_ve.count;
-    const long long gi = s_ve.gauss_begin + (in ? i : 0);
-    const long long f = s_ve.pair_off + (in ? i : 0);
-    SpecProj o;
-    o.visible = false;
-    o.x0 = o.x1 = o.y0 = o.y1 = 0;
-    if (in) {
-        const float *mu = a.means + 3 * gi;
-        const float *ls = a.log_scales + 3 * gi;
-        const float4 q = __ldg(reinterpret_cast<const float4 *>(a.quats) + gi);
-        o = spec_project(s_cam, s_cam + 9, s_cam[12], s_cam[13], s_cam[14], s_cam[15], s_cam[16], s_cam[17],
-                         a.itw, a.ith, a.Tx, a.Ty, a.near_plane, a.dil, a.sigmas, __ldg(mu), __ldg(mu + 1),
-                         __ldg(mu + 2), __ldg(ls), __ldg(ls + 1), __ldg(ls + 2), q.x, q.y, q.z, q.w);
-    }
-    uint32_t cnt = 0;
-    const bool fok = gs_guard(a.st, !in || f < a.P, 1);   // the pair index comes from the views table
-    if (!fok) o.visible = false;
-    // slot of each visible pair in the records: the block's visible pairs take consecutive slots
-    // (ballot + warp counts), the block's first slot comes from one atomic on the slot counter;
-    // slots beyond the capacity record GS_ERR_CAPACITY and their pairs are dropped
-    __shared__ uint32_t s_wcnt[kChunk / 32];
-    __shared__ unsigned long long s_base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned vmask = __ballot_sync(0xffffffffu, o.visible);
-    if (lane == 0) s_wcnt[warp] = (uint32_t)__popc(vmask);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t tot = 0;
+    const long long base_i = (long long)blockIdx.x * kChunk;
+    // phase 1: pairs base_i + k kProjThreads + thread
+    unsigned cmask[kProjRounds];
 #pragma unroll
-        for (int w = 0; w < kChunk / 32; ++w) tot += s_wcnt[w];
-        s_base = tot ? atomicAdd(&a.st->num_visible, (unsigned long long)tot) : 0ull;
+    for (int k = 0; k < kProjRounds; ++k) {
+        const int li = k * kProjThreads + threadIdx.x;
+        const long long i = base_i + li;
+        const bool in = i < s_ve.count;
+        const long long f = s_ve.pair_off + (in ? i : 0);
+        const bool fok = gs_guard(a.st, !in || f < a.P, 1);   // the pair index comes from the views table
+        bool cand = false;
+        if (in && fok) {
+            const long long gi = s_ve.gauss_begin + i;
+            const float *mu = a.means + 3 * gi;
+            cand = may_be_visible(s_cam, s_cam + 9, s_cam[12], s_cam[13], s_cam[14], s_cam[15], s_cam[18], a.itw,
+                                  a.ith, a.Tx, a.Ty, a.near_plane, a.dil, a.sigmas, __ldg(mu), __ldg(mu + 1),
+                                  __ldg(mu + 2), a.log_scales + 3 * gi);
+            if (!cand) {
+                a.touched[f] = 0u;
+                a.slot[f] = kNoSlot;
+            }
+        }
+        cmask[k] = __ballot_sync(0xffffffffu, cand);
+        if (lane == 0) s_wcnt[k][warp] = (uint32_t)__popc(cmask[k]);
     }
     __syncthreads();
-    unsigned long long slot = s_base + (unsigned long long)__popc(vmask & lanemask_lt());
-    for (int w = 0; w < warp; ++w) slot += s_wcnt[w];
-    if (o.visible && slot >= (unsigned long long)a.vcap) {
-        record_error(a.st, GS_ERR_CAPACITY, 11);
+    uint32_t ncand = 0;
+#pragma unroll
+    for (int k = 0; k < kProjRounds; ++k) {
+        uint32_t pre = ncand + (uint32_t)__popc(cmask[k] & lanemask_lt());
+        for (int w = 0; w < warp; ++w) pre += s_wcnt[k][w];
+        if ((cmask[k] >> lane) & 1u) s_cl[pre] = (uint8_t)(k * kProjThreads + threadIdx.x);
+#pragma unroll
+        for (int w = 0; w < kProjThreads / 32; ++w) ncand += s_wcnt[k][w];
+    }
+    __syncthreads();   // s_cl complete; s_wcnt is reused below
+    // phase 2: candidates r kProjThreads + thread through the decision chain
+    const int rounds = (int)((ncand + kProjThreads - 1) / kProjThreads);
+    for (int r = 0; r < rounds; ++r) {
+        const int t = r * kProjThreads + threadIdx.x;
+        const bool act = (uint32_t)t < ncand;
+        const int li = act ? (int)s_cl[t] : 0;
+        const long long i = base_i + li;
+        const long long gi = s_ve.gauss_begin + i;
+        const long long f = s_ve.pair_off + i;
+        SpecProj o;
         o.visible = false;
-    }
-    if (in && fok) a.slot[f] = o.visible ? (uint32_t)slot : kNoSlot;
-    if (o.visible) {
-        cnt = (uint32_t)((o.x1 - o.x0) * (o.y1 - o.y0));
-        const float *col = a.colors + 3 * gi;
-        float4 *rec = a.proj + 3 * slot;
-        const float op = __ldg(a.opacities + gi);
-        // sigma beyond which alpha < alpha_min is certain (see gs_render.cu); +inf disables the cut
-        float cut = __int_as_float(0x7f800000);
-        if (a.alpha_min > 0.0f) {
-            if (op > 0.0f) cut = logf(op / a.alpha_min) + 1e-3f;
-            else if (op <= 0.0f) cut = -1.0f;
+        o.x0 = o.x1 = o.y0 = o.y1 = 0;
+        if (act) {
+            const float *mu = a.means + 3 * gi;
+            const float *ls = a.log_scales + 3 * gi;
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(a.quats) + gi);
+            o = spec_project(s_cam, s_cam + 9, s_cam[12], s_cam[13], s_cam[14], s_cam[15], s_cam[16], s_cam[17],
+                             a.itw, a.ith, a.Tx, a.Ty, a.near_plane, a.dil, a.sigmas, __ldg(mu), __ldg(mu + 1),
+                             __ldg(mu + 2), __ldg(ls), __ldg(ls + 1), __ldg(ls + 2), q.x, q.y, q.z, q.w);
         }
-        rec[0] = make_float4(o.mx, o.my, o.A, o.B);
-        rec[1] = make_float4(o.C, op, o.z, o.rf);
-        rec[2] = make_float4(__ldg(col), __ldg(col + 1), __ldg(col + 2), cut);
+        const unsigned vmask = __ballot_sync(0xffffffffu, o.visible);
+        if (lane == 0) s_wcnt[r][warp] = (uint32_t)__popc(vmask);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+#pragma unroll
+            for (int w = 0; w < kProjThreads / 32; ++w) tot += s_wcnt[r][w];
+            const unsigned long long b0 = tot ? atomicAdd(&a.st->num_visible, (unsigned long long)tot) : 0ull;
+            s_base = b0;
+            s_rng[2 * r] = (uint32_t)min(b0, (unsigned long long)a.vcap);
+            s_rng[2 * r + 1] = tot;
+        }
+        __syncthreads();
+        unsigned long long slot = s_base + (unsigned long long)__popc(vmask & lanemask_lt());
+        for (int w = 0; w < warp; ++w) slot += s_wcnt[r][w];
+        if (o.visible && slot >= (unsigned long long)a.vcap) {
+            record_error(a.st, GS_ERR_CAPACITY, 11);
+            o.visible = false;
+        }
+        if (act) a.slot[f] = o.visible ? (uint32_t)slot : kNoSlot;
+        uint32_t cnt = 0;
+        if (o.visible) {
+            cnt = (uint32_t)((o.x1 - o.x0) * (o.y1 - o.y0));
+            a.slane[slot] = (uint8_t)li;
+            const float *col = a.colors + 3 * gi;
+            float4 *rec = a.proj + 3 * slot;
+            const float op = __ldg(a.opacities + gi);
+            // sigma beyond which alpha < alpha_min is certain (see gs_render.cu); +inf disables the cut
+            float cut = __int_as_float(0x7f800000);
+            if (a.alpha_min > 0.0f) {
+                if (op > 0.0f) cut = logf(op / a.alpha_min) + 1e-3f;
+                else if (op <= 0.0f) cut = -1.0f;
+            }
+            rec[0] = make_float4(o.mx, o.my, o.A, o.B);
+            rec[1] = make_float4(o.C, op, o.z, o.rf);
+            rec[2] = make_float4(__ldg(col), __ldg(col + 1), __ldg(col + 2), cut);
+        }
+        if (a.tile_cnt && o.visible) {   // tile-bucket binning: one key per touched tile of this view
+            uint32_t *row = a.tile_cnt + (size_t)v * a.Txi * a.Ty_i;
+            for (int ty = o.y0; ty < o.y1; ++ty)
+                for (int tx = o.x0; tx < o.x1; ++tx) atomicAdd(row + ty * a.Txi + tx, 1u);
+        }
+        if (act) a.touched[f] = cnt;
     }
-    if (a.tile_cnt && o.visible) {   // tile-bucket binning: one key per touched tile of this view
-        uint32_t *row = a.tile_cnt + (size_t)v * a.Txi * a.Ty_i;
-        for (int ty = o.y0; ty < o.y1; ++ty)
-            for (int tx = o.x0; tx < o.x1; ++tx) atomicAdd(row + ty * a.Txi + tx, 1u);
+    if (threadIdx.x == 0) {
+        const long long ch = s_ve.chunk_off + blockIdx.x;
+        if (base_i < s_ve.count && gs_guard(a.st, ch < a.chunks, 6))
+            a.blk[ch] = make_uint4(s_rng[0], s_rng[1], s_rng[2], s_rng[3]);
     }
-    if (in && fok) a.touched[f] = cnt;
 }
 
 void launch_project(const Layout &L, const ProjArgs &a, cudaStream_t s) {
     dim3 grid((unsigned)L.max_chunks, (unsigned)L.V);
-    k_project<<<grid, kChunk, 0, s>>>(a);
+    k_project<<<grid, kProjThreads, 0, s>>>(a);
     count_launches(1);
 }
 
@@ -105,11 +204,17 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
-__global__ void __launch_bounds__(kChunk) k_project_bwd(ProjBwdArgs a) {
+// One block of kProjBwdThreads threads per (chunk, view): the chunk's visible pairs, i.e. the
+// slots of its one or two projection rounds, taken kProjBwdThreads at a time; each thread sums the
+// pose terms of its pairs in order, then the block sums the threads (a fixed tree).
+constexpr int kProjBwdThreads = 64;
+
+__global__ void __launch_bounds__(kProjBwdThreads) k_project_bwd(ProjBwdArgs a) {
     const int v = blockIdx.y;
     __shared__ ViewEntry s_ve;
     __shared__ float s_cam[18];
-    __shared__ float s_red[kChunk / 32][6];
+    __shared__ float s_red[kProjBwdThreads / 32][6];
+    __shared__ uint4 s_blk;
     if (threadIdx.x == 0) s_ve = a.views[v];
     if (threadIdx.x < 16) s_cam[threadIdx.x] = reinterpret_cast<const float *>(a.cams + v)[threadIdx.x];
     if (threadIdx.x == 32) {      // the forward's clamp limits, the same operations
@@ -119,13 +224,20 @@ __global__ void __launch_bounds__(kChunk) k_project_bwd(ProjBwdArgs a) {
     }
     __syncthreads();
     if ((long long)blockIdx.x * kChunk >= s_ve.count) return;   // whole block idle: no partial slot
-    const long long i = (long long)blockIdx.x * kChunk + threadIdx.x;
+    const long long ch = s_ve.chunk_off + blockIdx.x;
+    if (threadIdx.x == 0) s_blk = gs_guard(a.st, ch < a.chunks, 3) ? a.blk[ch] : make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    // the chunk's visible pairs hold the slots [b0, b0 + n0) and [b1, b1 + n1) (beyond the capacity:
+    // dropped by the projection)
+    const unsigned long long vc = (unsigned long long)a.vcap;
+    const unsigned long long b0 = s_blk.x, b1 = s_blk.z;
+    const unsigned long long n0 = b0 < vc ? min((unsigned long long)s_blk.y, vc - b0) : 0ull;
+    const unsigned long long n1 = b1 < vc ? min((unsigned long long)s_blk.w, vc - b1) : 0ull;
     float pose[6] = {0, 0, 0, 0, 0, 0};
-    if (i < s_ve.count && gs_guard(a.st, s_ve.pair_off + i < a.P && s_ve.gauss_begin + i < a.N, 2)) {
-        const long long f = s_ve.pair_off + i;
-        const uint32_t prev = (f > 0 && !a.touched_is_count) ? a.touched_incl[f - 1] : 0u;
-        const uint32_t sl = a.slot[f];   // visible pairs only hold a valid slot
-        if (a.touched_incl[f] != prev && gs_guard(a.st, sl < (unsigned long long)a.vcap, 5)) {
+    for (unsigned long long u = threadIdx.x; u < n0 + n1; u += kProjBwdThreads) {
+        const uint32_t sl = (uint32_t)(u < n0 ? b0 + u : b1 + (u - n0));
+        const long long i = (long long)blockIdx.x * kChunk + a.slane[sl];
+        if (gs_guard(a.st, i < s_ve.count && s_ve.pair_off + i < a.P && s_ve.gauss_begin + i < a.N, 2)) {
             const long long gi = s_ve.gauss_begin + i;
             const float *R = s_cam, *t = s_cam + 9;
             const float fx = s_cam[12], fy = s_cam[13];
@@ -251,10 +363,10 @@ __global__ void __launch_bounds__(kChunk) k_project_bwd(ProjBwdArgs a) {
 #pragma unroll
                 for (int m = 0; m < 3; ++m) N[3 * j + m] = gR[3 * j] * R[3 * m] + gR[3 * j + 1] * R[3 * m + 1] +
                                                           gR[3 * j + 2] * R[3 * m + 2];
-            pose[0] = gpc0; pose[1] = gpc1; pose[2] = gpc2;
-            pose[3] = yc * gpc2 - zc * gpc1 + N[7] - N[5];
-            pose[4] = zc * gpc0 - xc * gpc2 + N[2] - N[6];
-            pose[5] = xc * gpc1 - yc * gpc0 + N[3] - N[1];
+            pose[0] += gpc0; pose[1] += gpc1; pose[2] += gpc2;
+            pose[3] += yc * gpc2 - zc * gpc1 + N[7] - N[5];
+            pose[4] += zc * gpc0 - xc * gpc2 + N[2] - N[6];
+            pose[5] += xc * gpc1 - yc * gpc0 + N[3] - N[1];
         }
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -264,17 +376,17 @@ __global__ void __launch_bounds__(kChunk) k_project_bwd(ProjBwdArgs a) {
         if (lane == 0) s_red[warp][k] = r;
     }
     __syncthreads();
-    if (threadIdx.x < 6 && gs_guard(a.st, s_ve.chunk_off + blockIdx.x < a.chunks, 3)) {
+    if (threadIdx.x < 6 && ch < a.chunks) {
         float r = 0.f;
 #pragma unroll
-        for (int wi = 0; wi < kChunk / 32; ++wi) r += s_red[wi][threadIdx.x];
+        for (int wi = 0; wi < kProjBwdThreads / 32; ++wi) r += s_red[wi][threadIdx.x];
         a.pose_part[(s_ve.chunk_off + blockIdx.x) * 8 + threadIdx.x] = r;
     }
 }
 
 void launch_project_bwd(const Layout &L, const ProjBwdArgs &a, cudaStream_t s) {
     dim3 grid((unsigned)L.max_chunks, (unsigned)L.V);
-    k_project_bwd<<<grid, kChunk, 0, s>>>(a);
+    k_project_bwd<<<grid, kProjBwdThreads, 0, s>>>(a);
     count_launches(1);
 }
 
