@@ -243,7 +243,7 @@ STAGES = ["project", "bin_sort", "render_fwd_l1", "render_bwd", "project_bwd", "
 
 
 def l2_flush(buf):
-    buf.zero_()
+    buf.zero_()   # a 256 MB int64 buffer: 8-byte stores, twice the L2
 
 
 def rank_views(S, wl, rank, world):
@@ -522,7 +522,7 @@ def normal_bench(R, S, torch, reps=20):
     d, p, c = t(depth), t(prior), t(cams)
     d_depth = torch.zeros_like(d)
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(32 << 20, dtype=torch.int64, device="cuda")
     for _ in range(3):
         R.loss_normal(d, p, c, 1e-2, d_depth, loss)
     torch.cuda.synchronize()
@@ -814,7 +814,7 @@ def main():
         from paper_2605_10760_gb300 import raster as R
         from paper_2605_10760_gb300 import scenes as S
         R.L.load()
-        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        flush = torch.empty(32 << 20, dtype=torch.int64, device="cuda")
         fn = {"photometric": pho_bench, "normal": normal_bench, "fusion": fusion_bench, "mapping": mapping_graph,
               "refine": refine_graph,
               "fused": fused_map, "batched": lambda R, S, torch: batched_speedup(R, S, torch, flush)}[args.only]
@@ -834,7 +834,7 @@ def main():
     R.L.load()
     wl = S.workload("room500k")
     pipe = Pipeline(R, S, wl, rank_views(S, wl, rank, world))
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(32 << 20, dtype=torch.int64, device="cuda")
     launches0 = R.L.load().gs_launch_count()
     pipe.step()
     torch.cuda.synchronize()
