@@ -679,20 +679,24 @@ def fused_map(R, S, torch, steps=3):
     pipe = Pipeline(R, S, wl, list(range(V)))
     pipe.step()
     torch.cuda.synchronize()
-    times = []
+    times, stage = [], {k: [] for k in STAGES}
     for _ in range(steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        pipe.step()
-        b.record()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
+        pipe.step(ev)
         torch.cuda.synchronize()
-        times.append(a.elapsed_time(b))
+        times.append(ev[0].elapsed_time(ev[-1]))
+        for i, k in enumerate(STAGES):
+            stage[k].append(ev[i].elapsed_time(ev[i + 1]))
     rc, _ = pipe.pb.check_status()
     st = pipe.pb.stats()
     ms = statistics.median(times)
+    wsv = pipe.pb.workspace()
     out = {"workload": "floor4m: 4M Gaussians (16 submaps), 64 views 1200x680", "views": V, "ms_per_step": ms,
-           "views_per_s": V * 1e3 / ms, "keys": st["num_keys"], "fwd_pairs": st["fwd_pairs"],
-           "bwd_pairs": st["bwd_pairs"], "status": rc, "workspace_gb": pipe.pb.ws_bytes / 1e9}
+           "views_per_s": V * 1e3 / ms, "stages_ms": {k: statistics.median(v) for k, v in stage.items()},
+           "keys": st["num_keys"], "sort_passes": wsv["passes"],
+           "fwd_pairs": st["fwd_pairs"], "bwd_pairs": st["bwd_pairs"], "status": rc,
+           "workspace_gb": pipe.pb.ws_bytes / 1e9}
+    del wsv
     del pipe
     torch.cuda.empty_cache()
     return out
@@ -865,14 +869,14 @@ def main():
     dom = max(stage_ms, key=stage_ms.get)
     P, K = pipe.pb.P, stats["num_keys"]
     wsv = pipe.pb.workspace()
-    passes = wsv["passes"]
+    passes, G = wsv["passes"], wsv["tile_ranges"].shape[0]
     onesweep = pipe.pb.params.sort_mode == R.L.GS_SORT_ONESWEEP
     vis = int((wsv["tiles_touched"] != 0).sum().item()) if not onesweep else 0
     npx = pipe.V * pipe.pb.W * pipe.pb.H
     alg_bytes = {
         "project": P * 60 + 0,
-        "bin_sort": (P * 8 + K * 12 + passes * K * 24 + K * 8 + pipe.pb.V * 3225 * 8) if onesweep else
-                    (pipe.pb.V * 3225 * 8 + vis * 32 + K * 12 + K * 116),
+        "bin_sort": (P * 8 + K * 12 + passes * K * 24 + K * 8 + G * 8) if onesweep else
+                    (G * 8 + vis * 32 + K * 12 + K * 116),
         "render_fwd_l1": npx * 48,
         "project_bwd": P * 60,
         "pose_grad": 0,
@@ -911,7 +915,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "gaussians": pipe.g.n, "width": 1200, "height": 680,
                    "loss": "L1(rgb) + 0.1 L1(depth)", "l2": "flushed between timed steps (256 MB write)",
-                   "keys": K, "fwd_pairs": stats["fwd_pairs"], "bwd_pairs": stats["bwd_pairs"],
+                   "keys": K, "sort_passes": passes,
+                   "fwd_pairs": stats["fwd_pairs"], "bwd_pairs": stats["bwd_pairs"],
                    "status": rc},
         "stages_ms": stage_ms,
         "timing": "value: the whole step replayed as one CUDA graph, events around each step, L2 flushed "

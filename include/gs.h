@@ -303,8 +303,8 @@ int gs_loss_l1(int32_t views, int32_t width, int32_t height, const float *rgb, c
  *   depth [V,H,W] (the rendered depth), prior [V,3,H,W] unit normals in each view's camera frame,
  *   cams [V] device cameras (only the intrinsics are read).  ADDS L to *loss (device double) and
  *   dL/d depth to d_depth [V,H,W] (so it follows gs_loss_l1 / gs_render_fwd_l1, which write
- *   them).  One kernel (a tile of pixels per CTA, the neighbours' terms recomputed in shared
- *   memory), no scratch memory, no synchronisation. */
+ *   them).  One kernel (a warp walks down a strip of 30 columns, the neighbours' terms passed by
+ *   warp shuffles and kept in registers), no scratch memory, no synchronisation. */
 int gs_loss_normal(int32_t views, int32_t width, int32_t height, const float *depth, const float *prior,
                    const gs_camera *cams, float weight, float *d_depth, double *loss, void *stream);
 

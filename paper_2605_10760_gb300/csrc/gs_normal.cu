@@ -2,20 +2,25 @@
 // |1 - N_hat . N_bar| between the normal induced by the rendered depth and a given normal prior,
 // and its gradient with respect to the depth.
 //
-// One persistent kernel; a CTA takes (view, 32 x 8 tile) items in turn.  Per item the tile's depths
-// with a 2-pixel halo and the prior over the tile plus a 1-pixel halo go to shared memory (loaded
-// one item ahead into registers, so the next tile's loads overlap this tile's arithmetic); every
-// pixel of the tile plus a 1-pixel halo computes, from P = D r with
-// r = ((x + 0.5 - cx) / fx, (y + 0.5 - cy) / fy, 1) its pixel ray (nm_ray), the central-difference
-// tangents t_x = P(x+1, y) - P(x-1, y), t_y = P(x, y+1) - P(x, y-1), u = t_y x t_x and
-// N_hat = u / |u| (facing the camera for a surface seen from the front), and the adjoints
-// G_x = dL/dt_x, G_y = dL/dt_y into shared memory (zero where the pixel is invalid: on the image
-// border, a depth of the pixel or of its four neighbours not positive and finite, or |u| = 0).
-// The loss of the tile's own pixels goes to a per-thread FP64 sum (one atomic per CTA).  Then every
-// pixel q of the tile adds r(q) . (G_x(q-x) - G_x(q+x) + G_y(q-y) - G_y(q+y)) to d_depth.  The halo
-// pixels' adjoints are recomputed by each neighbouring tile instead of going through global
-// memory, so a pixel costs its depth, its prior and a read-modify-write of d_depth.  Values in
-// FP32.
+// Per pixel q: P = D r with r = ((x + 0.5 - cx) / fx, (y + 0.5 - cy) / fy, 1) its pixel ray
+// (nm_ray), the central-difference tangents t_x = P(x+1, y) - P(x-1, y),
+// t_y = P(x, y+1) - P(x, y-1), u = t_y x t_x and N_hat = u / |u| (facing the camera for a surface
+// seen from the front), and the adjoints G_x = dL/dt_x, G_y = dL/dt_y (zero where the pixel is
+// invalid: on the image border, a depth of the pixel or of its four neighbours not positive and
+// finite, or |u| = 0).  The depth gradient of q gathers r(q) . (G_x(q-x) - G_x(q+x) + G_y(q-y) -
+// G_y(q+y)).
+//
+// One persistent kernel of independent warps (no CTA barrier until the final loss sum).  A warp
+// takes (view, 16-row strip, 30-column block) items in turn: lane l holds column x0 - 1 + l (lanes
+// 0 and 31 are the block's halo columns) and the warp walks down the strip's rows, one row per
+// step, with the depths of the rows above and below in registers.  A step loads one depth and one
+// prior row (lane 0 and lane 31 one more depth each: the columns beside the halo), computes the
+// normal and the adjoints of its row, and finishes the depth gradient of the row above: the left
+// and right neighbours' G_x come by warp shuffles, G_y of the rows above and below from
+// registers.  Every normal is computed once per item (the two halo columns and the two rows
+// beyond the strip are recomputed by the neighbouring items), and a pixel costs its depth, its
+// prior and a read-modify-write of d_depth.  The next row's loads are issued before the current
+// row's arithmetic.  Values in FP32; the loss in FP32 per item and FP64 per CTA.
 #include <algorithm>
 
 #include "gs_kernels.cuh"
@@ -23,12 +28,13 @@
 namespace gs {
 
 constexpr int kNormalThreads = 256;
+constexpr int kNCols = 30;           // output columns of a warp's item (32 lanes less two halo lanes)
+constexpr int kNRows = 16;           // output rows of an item
 
-__device__ __forceinline__ float3 nm_cross(float3 a, float3 b) {
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ float nm_dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ bool nm_depth_ok(float d) { return d > 0.0f && d < __int_as_float(0x7f800000); }
+
+// the pixel ray of column x / row y (one expression for the normal and for its adjoint)
+__device__ __forceinline__ float nm_ray(int x, float c, float inv_f) { return ((float)x + 0.5f - c) * inv_f; }
 
 // sum of v over the block, added to *out by one FP64 atomic
 __device__ __forceinline__ void nm_block_add(double v, double *out) {
@@ -44,199 +50,132 @@ __device__ __forceinline__ void nm_block_add(double v, double *out) {
     }
 }
 
-constexpr int kNTW = 32, kNTH = 8;                        // output tile
-constexpr int kNDW = kNTW + 4, kNDH = kNTH + 4;            // depths: 2-pixel halo
-constexpr int kNGW = kNTW + 2, kNGH = kNTH + 2;            // adjoints: 1-pixel halo
-static_assert(kNTW * kNTH == kNormalThreads, "one output pixel per thread");
-
-// the pixel ray of column x / row y (one expression for the normal and for its adjoint)
-__device__ __forceinline__ float nm_ray(int x, float c, float inv_f) { return ((float)x + 0.5f - c) * inv_f; }
-
-constexpr int kNDElems = kNDH * kNDW;                    // depths staged per tile
-constexpr int kNPElems = 3 * kNGH * kNGW;                // prior components staged per tile
-constexpr int kNDPer = (kNDElems + kNormalThreads - 1) / kNormalThreads;
-constexpr int kNPPer = (kNPElems + kNormalThreads - 1) / kNormalThreads;
-
-// Global inputs of one (view, tile) item, held in registers from the previous item on: the
-// thread's share of the depth halo and of the prior over the adjoint region, and d_depth of its
-// own output pixel.  Everything is loaded one item ahead, so a CTA's loads for the next tile are in
-// flight while it computes the current one.
-struct NormalStage {
-    float d[kNDPer];
-    float p[kNPPer];
-    float dd;
+// The global inputs of one row step: the lane's depth one row below the row being normalised, its
+// extra depth (lane 0: the column left of the halo, lane 31: the one right of it, of the row
+// itself), the prior of its pixel, and d_depth of its pixel one row above (whose gradient the step
+// finishes).  Every load reads a clamped (in-image) address; out-of-image depths then read as -1
+// (invalid), priors and d_depth as 0.
+struct NormalRow {
+    float d_below, d_ext, p0, p1, p2, dd;
 };
 
-// item = (view, tile) in view-major, row-major tile order (32-bit: the launcher checks the count)
-__device__ __forceinline__ void nm_item(int item, int tiles_x, int tiles_per_view, int &v, int &x0, int &y0) {
-    v = item / tiles_per_view;
-    const int t = item - v * tiles_per_view;
-    const int ty = t / tiles_x;
-    x0 = (t - ty * tiles_x) * kNTW;
-    y0 = ty * kNTH;
+// Per item and lane: the column pointers (clamped into the image) and which of them are real.
+struct NormalCol {
+    const float *d, *de, *p;
+    float *dd;
+    bool xin, xein;
+};
+
+__device__ __forceinline__ void nm_fetch_row(const NormalCol &c, int HW, int W, int H, int y, NormalRow &r) {
+    const int yb = min(max(y + 1, 0), H - 1), yc = min(max(y, 0), H - 1), ya = min(max(y - 1, 0), H - 1);
+    const float db = __ldg(c.d + yb * W), de = __ldg(c.de + yc * W);
+    const float p0 = __ldg(c.p + yc * W), p1 = __ldg(c.p + HW + yc * W), p2 = __ldg(c.p + 2 * HW + yc * W);
+    const float dd = c.dd[ya * W];
+    const bool bin = (unsigned)(y + 1) < (unsigned)H, cin = (unsigned)y < (unsigned)H, ain = (unsigned)(y - 1) < (unsigned)H;
+    r.d_below = c.xin && bin ? db : -1.0f;
+    r.d_ext = c.xein && cin ? de : -1.0f;
+    const bool pin = c.xin && cin;
+    r.p0 = pin ? p0 : 0.0f;
+    r.p1 = pin ? p1 : 0.0f;
+    r.p2 = pin ? p2 : 0.0f;
+    r.dd = c.xin && ain ? dd : 0.0f;
 }
 
-__device__ __forceinline__ void nm_fetch(const NormalArgs &a, int v, int x0, int y0, NormalStage &st) {
-    const size_t HW = (size_t)a.H * a.W;
-    const float *D = a.depth + (size_t)v * HW;
-#pragma unroll
-    for (int k = 0; k < kNDPer; ++k) {
-        const int i = threadIdx.x + k * kNormalThreads;
-        const int ly = i / kNDW, lx = i - ly * kNDW;
-        const int x = x0 - 2 + lx, y = y0 - 2 + ly;
-        st.d[k] = (i < kNDElems && (unsigned)x < (unsigned)a.W && (unsigned)y < (unsigned)a.H)
-                      ? D[(size_t)y * a.W + x] : -1.0f;
-    }
-    const float *Pr = a.prior + (size_t)v * 3 * HW;
-#pragma unroll
-    for (int k = 0; k < kNPPer; ++k) {
-        const int i = threadIdx.x + k * kNormalThreads;
-        const int ch = i / (kNGH * kNGW), r = i - ch * (kNGH * kNGW);
-        const int gy_ = r / kNGW, gx_ = r - gy_ * kNGW;
-        const int x = x0 - 1 + gx_, y = y0 - 1 + gy_;
-        st.p[k] = (i < kNPElems && (unsigned)x < (unsigned)a.W && (unsigned)y < (unsigned)a.H)
-                      ? Pr[(size_t)ch * HW + (size_t)y * a.W + x] : 0.0f;
-    }
-    const int x = x0 + threadIdx.x % kNTW, y = y0 + threadIdx.x / kNTW;
-    st.dd = (x < a.W && y < a.H) ? a.d_depth[(size_t)v * HW + (size_t)y * a.W + x] : 0.0f;
-}
-
-__global__ void __launch_bounds__(kNormalThreads, 4) k_normal(NormalArgs a) {
-    __shared__ float s_d[kNDH][kNDW];
-    __shared__ float s_p[3][kNGH][kNGW];
-    __shared__ float s_g[6][kNGH][kNGW];
-    const long long HW = (long long)a.H * a.W;
-    const int tiles_x = (a.W + kNTW - 1) / kNTW, tiles_y = (a.H + kNTH - 1) / kNTH;
-    const int tpv = tiles_x * tiles_y, tiles = a.V * tpv;
-    double acc = 0.0;      // the CTA's loss, summed per item in FP32 then once per item in FP64
-    NormalStage st;
-    int item = blockIdx.x;
-    int v = 0, x0 = 0, y0 = 0;
-    if (item < tiles) {
-        nm_item(item, tiles_x, tpv, v, x0, y0);
-        nm_fetch(a, v, x0, y0, st);
-    }
-    // persistent over the (view, tile) items, so the loss needs one atomic per CTA, not per tile
-    for (; item < tiles; item += gridDim.x) {
-        __syncthreads();   // the previous item's reads of s_d, s_p and s_g are done
-#pragma unroll
-        for (int k = 0; k < kNDPer; ++k) {
-            const int i = threadIdx.x + k * kNormalThreads;
-            if (i < kNDElems) (&s_d[0][0])[i] = st.d[k];
-        }
-#pragma unroll
-        for (int k = 0; k < kNPPer; ++k) {
-            const int i = threadIdx.x + k * kNormalThreads;
-            if (i < kNPElems) (&s_p[0][0][0])[i] = st.p[k];
-        }
-        const float dd_own = st.dd;
-        const int cv = v, cx0 = x0, cy0 = y0;
-        const int next = item + (int)gridDim.x;
-        if (next < tiles) {   // the next item's inputs, in flight while this one is computed
-            nm_item(next, tiles_x, tpv, v, x0, y0);
-            nm_fetch(a, v, x0, y0, st);
-        }
-        const gs_camera &cam = a.cams[cv];
-        const float ifx = 1.0f / cam.fx, ify = 1.0f / cam.fy;
-        __syncthreads();
+__global__ void __launch_bounds__(kNormalThreads, 3) k_normal(NormalArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int W = a.W, H = a.H, HW = a.H * a.W;      // the launcher checks 3 H W < 2^31
+    const int cblocks = (W + kNCols - 1) / kNCols, strips = (H + kNRows - 1) / kNRows;
+    const int per_view = cblocks * strips;
+    const long long items = (long long)a.V * per_view;
+    const long long nwarps = (long long)gridDim.x * (kNormalThreads / 32);
+    double acc = 0.0;
+    for (long long item = (long long)blockIdx.x * (kNormalThreads / 32) + (threadIdx.x >> 5); item < items;
+         item += nwarps) {
+        const int v = (int)(item / per_view);
+        const int t = (int)(item - (long long)v * per_view);
+        const int sr = t / cblocks;
+        const int y0 = sr * kNRows, x = (t - sr * cblocks) * kNCols - 1 + lane;
+        // lane 0 also reads the column left of it, lane 31 the one right of it
+        const int xe = lane == 0 ? x - 1 : (lane == 31 ? x + 1 : -1);
+        const bool own_col = lane >= 1 && lane <= kNCols && x < W;
+        const gs_camera &cam = a.cams[v];
+        const float ifx = 1.0f / cam.fx, ify = 1.0f / cam.fy, cy = cam.cy;
+        const float rxl = nm_ray(x - 1, cam.cx, ifx), rxc = nm_ray(x, cam.cx, ifx), rxr = nm_ray(x + 1, cam.cx, ifx);
+        const bool colok = x >= 1 && x <= W - 2;
+        NormalCol c;
+        const int xc = min(max(x, 0), W - 1), xec = min(max(xe, 0), W - 1);
+        c.d = a.depth + (size_t)v * HW + xc;
+        c.de = a.depth + (size_t)v * HW + xec;
+        c.p = a.prior + (size_t)v * 3 * HW + xc;
+        c.dd = a.d_depth + (size_t)v * HW + xc;
+        c.xin = (unsigned)x < (unsigned)W;
+        c.xein = (unsigned)xe < (unsigned)W;
+        // rows y0 - 2 and y0 - 1 of the own column, then the first step's inputs (row y0 - 1)
+        const float dm2 = __ldg(c.d + min(max(y0 - 2, 0), H - 1) * W), dm1 = __ldg(c.d + min(max(y0 - 1, 0), H - 1) * W);
+        float d_up = c.xin && y0 >= 2 ? dm2 : -1.0f;
+        float d_mid = c.xin && y0 >= 1 ? dm1 : -1.0f;
+        bool ok_up = nm_depth_ok(d_up), ok_mid = nm_depth_ok(d_mid);
+        float ry_up = nm_ray(y0 - 2, cy, ify), ry_mid = nm_ray(y0 - 1, cy, ify);
+        const int yend = min(y0 + kNRows, H);                // the rows y0 .. yend - 1 are this item's
+        NormalRow cur;
+        nm_fetch_row(c, HW, W, H, y0 - 1, cur);
+        float gxp0 = 0.f, gxp1 = 0.f, gxp2 = 0.f;            // G_x of the row above the current one
+        float gyp0 = 0.f, gyp1 = 0.f, gyp2 = 0.f;            // G_y of the row above
+        float gyq0 = 0.f, gyq1 = 0.f, gyq2 = 0.f;            // G_y two rows above
         float acc_item = 0.f;
-        // two horizontally adjacent pixels per thread, the two components of packed FP32x2
-        // arithmetic (values only: every decision here is a validity test taken per component)
-        static_assert(kNGW % 2 == 0 && kNGH * kNGW / 2 <= kNormalThreads, "one pixel pair per thread");
-        if (threadIdx.x < kNGH * kNGW / 2) {
-            const int gy_ = threadIdx.x / (kNGW / 2), gx0 = 2 * (threadIdx.x % (kNGW / 2));
-            const int x = cx0 - 1 + gx0, y = cy0 - 1 + gy_;      // image coordinates of the first pixel
-            const int cx = gx0 + 1, cy = gy_ + 1;                  // its position in s_d
-            const float2 dc = make_float2(s_d[cy][cx], s_d[cy][cx + 1]);
-            const float2 dl = make_float2(s_d[cy][cx - 1], s_d[cy][cx]);
-            const float2 dr = make_float2(s_d[cy][cx + 1], s_d[cy][cx + 2]);
-            const float2 du = make_float2(s_d[cy - 1][cx], s_d[cy - 1][cx + 1]);
-            const float2 dd = make_float2(s_d[cy + 1][cx], s_d[cy + 1][cx + 1]);
-            const bool rowok = y >= 1 && y <= a.H - 2;
-            bool ok[2];
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int xc = x + c;
-                const float pc = c ? dc.y : dc.x, pl = c ? dl.y : dl.x, pr = c ? dr.y : dr.x, pu = c ? du.y : du.x,
-                            pd = c ? dd.y : dd.x;
-                ok[c] = rowok && xc >= 1 && xc <= a.W - 2 && nm_depth_ok(pc) && nm_depth_ok(pl) && nm_depth_ok(pr) &&
-                        nm_depth_ok(pu) && nm_depth_ok(pd);
-            }
-            float3 gx2[2] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f)};
-            float3 gy2[2] = {gx2[0], gx2[0]};
-            if (ok[0] || ok[1]) {
-                using namespace fp2;
-                const float r0 = nm_ray(x, cam.cx, ifx);
-                const float2 rxc = make_float2(r0, nm_ray(x + 1, cam.cx, ifx));
-                const float2 rxl = make_float2(nm_ray(x - 1, cam.cx, ifx), r0);
-                const float2 rxr = make_float2(rxc.y, nm_ray(x + 2, cam.cx, ifx));
-                const float ryc = nm_ray(y, cam.cy, ify), ryu = nm_ray(y - 1, cam.cy, ify), ryd = nm_ray(y + 1, cam.cy, ify);
+        for (int y = y0 - 1; y <= yend; ++y) {
+            NormalRow nxt;
+            if (y < yend) nm_fetch_row(c, HW, W, H, y + 1, nxt);
+            const float d_dn = cur.d_below;
+            const bool ok_dn = nm_depth_ok(d_dn);
+            const float ry_dn = nm_ray(y + 1, cy, ify);
+            // the row's depths left and right of the lane (lanes 0 and 31 from their extra read)
+            const float d_l0 = __shfl_up_sync(0xffffffffu, d_mid, 1), d_r0 = __shfl_down_sync(0xffffffffu, d_mid, 1);
+            const float d_l = lane == 0 ? cur.d_ext : d_l0, d_r = lane == 31 ? cur.d_ext : d_r0;
+            const bool ok = colok && y >= 1 && y <= H - 2 && ok_mid && ok_up && ok_dn && nm_depth_ok(d_l) &&
+                            nm_depth_ok(d_r);
+            float gx0 = 0.f, gx1 = 0.f, gx2 = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f;
+            if (ok) {
                 // neighbours in a row share the ray's y component, in a column its x component
-                const float2 dx_ = add(dr, neg(dl)), dy_ = add(dd, neg(du));
-                const float2 tx0 = add(mul(dr, rxr), neg(mul(dl, rxl))), tx1 = mul(dx_, splat(ryc)), tx2 = dx_;
-                const float2 ty0 = mul(dy_, rxc), ty1 = add(mul(dd, splat(ryd)), neg(mul(du, splat(ryu)))), ty2 = dy_;
+                const float dx_ = d_r - d_l, dy_ = d_dn - d_up;
+                const float tx0 = d_r * rxr - d_l * rxl, tx1 = dx_ * ry_mid, tx2 = dx_;
+                const float ty0 = dy_ * rxc, ty1 = d_dn * ry_dn - d_up * ry_up, ty2 = dy_;
                 // u = t_y x t_x
-                const float2 u0 = add(mul(ty1, tx2), neg(mul(ty2, tx1)));
-                const float2 u1 = add(mul(ty2, tx0), neg(mul(ty0, tx2)));
-                const float2 u2 = add(mul(ty0, tx1), neg(mul(ty1, tx0)));
-                const float2 uu = fma(u0, u0, fma(u1, u1, mul(u2, u2)));
-                const bool v0 = ok[0] && uu.x > 0.0f, v1 = ok[1] && uu.y > 0.0f;
-                // 1/|u| by the hardware reciprocal square root (a value, not a decision)
-                const float2 inu = make_float2(v0 ? rsqrtf(uu.x) : 0.f, v1 ? rsqrtf(uu.y) : 0.f);
-                const float2 n0 = mul(u0, inu), n1 = mul(u1, inu), n2 = mul(u2, inu);
-                const float2 b0 = make_float2(s_p[0][gy_][gx0], s_p[0][gy_][gx0 + 1]);
-                const float2 b1 = make_float2(s_p[1][gy_][gx0], s_p[1][gy_][gx0 + 1]);
-                const float2 b2 = make_float2(s_p[2][gy_][gx0], s_p[2][gy_][gx0 + 1]);
-                const float2 cc = add(splat(1.0f), neg(fma(n0, b0, fma(n1, b1, mul(n2, b2)))));
-                // own pixels of the tile add their loss; -scale sign(c) weights the adjoint
-                const bool own0 = v0 && gx0 >= 1 && gx0 <= kNTW && gy_ >= 1 && gy_ <= kNTH;
-                const bool own1 = v1 && gx0 + 1 >= 1 && gx0 + 1 <= kNTW && gy_ >= 1 && gy_ <= kNTH;
-                acc_item += (own0 ? fabsf(cc.x) : 0.f) + (own1 ? fabsf(cc.y) : 0.f);   // selects: NaN-safe
-                const float2 kk = make_float2(!v0 ? 0.f : (cc.x > 0.f ? -a.scale : (cc.x < 0.f ? a.scale : 0.f)),
-                                              !v1 ? 0.f : (cc.y > 0.f ? -a.scale : (cc.y < 0.f ? a.scale : 0.f)));
-                const float2 gn0 = mul(kk, b0), gn1 = mul(kk, b1), gn2 = mul(kk, b2);
-                const float2 pn = fma(n0, gn0, fma(n1, gn1, mul(n2, gn2)));
-                const float2 gu0 = mul(add(gn0, neg(mul(n0, pn))), inu);
-                const float2 gu1 = mul(add(gn1, neg(mul(n1, pn))), inu);
-                const float2 gu2 = mul(add(gn2, neg(mul(n2, pn))), inu);
-                // G_x = gu x t_y, G_y = t_x x gu (zero where the pixel is invalid: kk = inu = 0)
-                const float2 gxa = add(mul(gu1, ty2), neg(mul(gu2, ty1)));
-                const float2 gxb = add(mul(gu2, ty0), neg(mul(gu0, ty2)));
-                const float2 gxc = add(mul(gu0, ty1), neg(mul(gu1, ty0)));
-                const float2 gya = add(mul(tx1, gu2), neg(mul(tx2, gu1)));
-                const float2 gyb = add(mul(tx2, gu0), neg(mul(tx0, gu2)));
-                const float2 gyc = add(mul(tx0, gu1), neg(mul(tx1, gu0)));
-                // selects, not products with zero: an invalid pixel's tangents may hold NaN or inf
-                if (v0) {
-                    gx2[0] = make_float3(gxa.x, gxb.x, gxc.x);
-                    gy2[0] = make_float3(gya.x, gyb.x, gyc.x);
-                }
-                if (v1) {
-                    gx2[1] = make_float3(gxa.y, gxb.y, gxc.y);
-                    gy2[1] = make_float3(gya.y, gyb.y, gyc.y);
+                const float u0 = ty1 * tx2 - ty2 * tx1, u1 = ty2 * tx0 - ty0 * tx2, u2 = ty0 * tx1 - ty1 * tx0;
+                const float uu = u0 * u0 + u1 * u1 + u2 * u2;
+                if (uu > 0.0f) {
+                    // 1/|u| by the hardware reciprocal square root (a value, not a decision)
+                    const float inu = rsqrtf(uu);
+                    const float n0 = u0 * inu, n1 = u1 * inu, n2 = u2 * inu;
+                    const float cc = 1.0f - (n0 * cur.p0 + n1 * cur.p1 + n2 * cur.p2);
+                    if (own_col && y >= y0 && y < yend) acc_item += fabsf(cc);
+                    // -scale sign(c) weights the adjoint (sign(0) = 0)
+                    const float kk = cc > 0.f ? -a.scale : (cc < 0.f ? a.scale : 0.f);
+                    const float gn0 = kk * cur.p0, gn1 = kk * cur.p1, gn2 = kk * cur.p2;
+                    const float pn = n0 * gn0 + n1 * gn1 + n2 * gn2;
+                    const float gu0 = (gn0 - n0 * pn) * inu, gu1 = (gn1 - n1 * pn) * inu, gu2 = (gn2 - n2 * pn) * inu;
+                    // G_x = gu x t_y, G_y = t_x x gu
+                    gx0 = gu1 * ty2 - gu2 * ty1; gx1 = gu2 * ty0 - gu0 * ty2; gx2 = gu0 * ty1 - gu1 * ty0;
+                    gy0 = tx1 * gu2 - tx2 * gu1; gy1 = tx2 * gu0 - tx0 * gu2; gy2 = tx0 * gu1 - tx1 * gu0;
                 }
             }
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                s_g[0][gy_][gx0 + c] = gx2[c].x; s_g[1][gy_][gx0 + c] = gx2[c].y; s_g[2][gy_][gx0 + c] = gx2[c].z;
-                s_g[3][gy_][gx0 + c] = gy2[c].x; s_g[4][gy_][gx0 + c] = gy2[c].y; s_g[5][gy_][gx0 + c] = gy2[c].z;
+            // the row above (y - 1) is complete: + G_x of its left neighbour (t_x there =
+            // P(q) - P(q - 2)), - G_x of its right one, + G_y of the pixel above it, - G_y of this row
+            const float l0 = __shfl_up_sync(0xffffffffu, gxp0, 1), r0 = __shfl_down_sync(0xffffffffu, gxp0, 1);
+            const float l1 = __shfl_up_sync(0xffffffffu, gxp1, 1), r1 = __shfl_down_sync(0xffffffffu, gxp1, 1);
+            const float l2 = __shfl_up_sync(0xffffffffu, gxp2, 1), r2 = __shfl_down_sync(0xffffffffu, gxp2, 1);
+            if (own_col && y > y0 && y <= yend) {
+                const float dP0 = l0 - r0 + gyq0 - gy0, dP1 = l1 - r1 + gyq1 - gy1, dP2 = l2 - r2 + gyq2 - gy2;
+                c.dd[(y - 1) * W] = cur.dd + (rxc * dP0 + ry_up * dP1 + dP2);
             }
+            gyq0 = gyp0; gyq1 = gyp1; gyq2 = gyp2;
+            gyp0 = gy0; gyp1 = gy1; gyp2 = gy2;
+            gxp0 = gx0; gxp1 = gx1; gxp2 = gx2;
+            d_up = d_mid; ok_up = ok_mid; ry_up = ry_mid;
+            d_mid = d_dn; ok_mid = ok_dn; ry_mid = ry_dn;
+            if (y < yend) cur = nxt;
         }
         acc += (double)acc_item;
-        __syncthreads();
-        const int tx_ = threadIdx.x % kNTW, ty_ = threadIdx.x / kNTW;
-        const int x = cx0 + tx_, y = cy0 + ty_;
-        if (x < a.W && y < a.H) {
-            const int gx_ = tx_ + 1, gy_ = ty_ + 1;
-            // + G_x of the left neighbour (t_x there = P(q) - P(q - 2)), - G_x of the right one,
-            // + G_y of the pixel above, - G_y of the pixel below (zero outside the image)
-            float3 dP;
-            dP.x = s_g[0][gy_][gx_ - 1] - s_g[0][gy_][gx_ + 1] + s_g[3][gy_ - 1][gx_] - s_g[3][gy_ + 1][gx_];
-            dP.y = s_g[1][gy_][gx_ - 1] - s_g[1][gy_][gx_ + 1] + s_g[4][gy_ - 1][gx_] - s_g[4][gy_ + 1][gx_];
-            dP.z = s_g[2][gy_][gx_ - 1] - s_g[2][gy_][gx_ + 1] + s_g[5][gy_ - 1][gx_] - s_g[5][gy_ + 1][gx_];
-            const float3 r = make_float3(nm_ray(x, cam.cx, ifx), nm_ray(y, cam.cy, ify), 1.0f);
-            a.d_depth[(long long)cv * HW + (long long)y * a.W + x] = dd_own + nm_dot(r, dP);
-        }
     }
     nm_block_add(acc * (double)a.scale, a.loss);
 }
@@ -248,9 +187,11 @@ int launch_loss_normal(const NormalArgs &a, cudaStream_t s) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_normal, kNormalThreads, 0) != cudaSuccess || b < 1) b = 1;
         return b;
     }();
-    const long long tiles = (long long)a.V * ((a.W + kNTW - 1) / kNTW) * ((a.H + kNTH - 1) / kNTH);
-    if (tiles >= (1LL << 31)) return GS_ERR_INVALID_ARG;   // items are 32-bit
-    const long long grid = std::max<long long>(1, std::min<long long>(tiles, (long long)device_sm_count() * occ));
+    if (3LL * a.H * a.W >= (1LL << 31)) return GS_ERR_INVALID_ARG;   // 32-bit offsets inside a view
+    const long long items = (long long)a.V * ((a.W + kNCols - 1) / kNCols) * ((a.H + kNRows - 1) / kNRows);
+    const long long warps = kNormalThreads / 32;
+    const long long grid = std::max<long long>(1, std::min<long long>((items + warps - 1) / warps,
+                                                                      (long long)device_sm_count() * occ));
     k_normal<<<(unsigned)grid, kNormalThreads, 0, s>>>(a);
     count_launches(1);
     return check_launch();

@@ -1,5 +1,6 @@
 """GPU parity of the normal term of Eq. 4 (gs_loss_normal) against the FP64 oracle, on images that
-are and are not multiples of the kernel's 32 x 8 pixel tile, down to images with no interior pixel."""
+span several of the kernel's 30-column x 16-row items in both directions or less than one, with
+ragged last items, down to images with no interior pixel."""
 import numpy as np
 import pytest
 
