@@ -11,16 +11,17 @@
 // G_y(q+y)).
 //
 // One persistent kernel of independent warps (no CTA barrier until the final loss sum).  A warp
-// takes (view, 16-row strip, 30-column block) items in turn: lane l holds column x0 - 1 + l (lanes
-// 0 and 31 are the block's halo columns) and the warp walks down the strip's rows, one row per
-// step, with the depths of the rows above and below in registers.  A step loads one depth and one
-// prior row (lane 0 and lane 31 one more depth each: the columns beside the halo), computes the
-// normal and the adjoints of its row, and finishes the depth gradient of the row above: the left
-// and right neighbours' G_x come by warp shuffles, G_y of the rows above and below from
-// registers.  Every normal is computed once per item (the two halo columns and the two rows
-// beyond the strip are recomputed by the neighbouring items), and a pixel costs its depth, its
-// prior and a read-modify-write of d_depth.  The next row's loads are issued before the current
-// row's arithmetic.  Values in FP32; the loss in FP32 per item and FP64 per CTA.
+// takes (view, 16-row strip, 60-column block) items in turn: lane l holds the two columns
+// x0 - 2 + 2l and x0 - 1 + 2l as the two components of packed FP32x2 arithmetic (lanes 0 and 31
+// are the block's halo), and the warp walks down the strip's rows, one row per step, with the
+// depths of the rows above and below in registers.  A step loads one depth and one prior row
+// (8-byte pairs when the width is even), computes the normals and the adjoints of its row, and
+// finishes the depth gradient of the row above: the neighbouring columns' depths and G_x come from
+// the lane's other component or by one warp shuffle, G_y of the rows above and below from
+// registers.  Every normal is computed once per item (the halo columns and the two rows beyond the
+// strip are recomputed by the neighbouring items), and a pixel costs its depth, its prior and a
+// read-modify-write of d_depth.  The next row's loads are issued before the current row's
+// arithmetic.  Values in FP32; the loss in FP32 per item and FP64 per CTA.
 #include <algorithm>
 
 #include "gs_kernels.cuh"
@@ -28,7 +29,7 @@
 namespace gs {
 
 constexpr int kNormalThreads = 256;
-constexpr int kNCols = 30;           // output columns of a warp's item (32 lanes less two halo lanes)
+constexpr int kNCols = 60;           // output columns of a warp's item (32 lanes x 2, less two halo lanes)
 constexpr int kNRows = 16;           // output rows of an item
 
 __device__ __forceinline__ bool nm_depth_ok(float d) { return d > 0.0f && d < __int_as_float(0x7f800000); }
@@ -50,129 +51,178 @@ __device__ __forceinline__ void nm_block_add(double v, double *out) {
     }
 }
 
-// The global inputs of one row step: the lane's depth one row below the row being normalised, its
-// extra depth (lane 0: the column left of the halo, lane 31: the one right of it, of the row
-// itself), the prior of its pixel, and d_depth of its pixel one row above (whose gradient the step
-// finishes).  Every load reads a clamped (in-image) address; out-of-image depths then read as -1
-// (invalid), priors and d_depth as 0.
-struct NormalRow {
-    float d_below, d_ext, p0, p1, p2, dd;
+// The global inputs of one row step for the lane's two columns: the depths one row below the row
+// being normalised, the prior of its pixels, and d_depth of its pixels one row above (whose
+// gradient the step finishes).  Every load reads a clamped (in-image) address; out-of-image depths
+// then read as -1 (invalid), priors and d_depth as 0.
+struct NormalRow2 {
+    float2 d_below, p0, p1, p2, dd;
 };
 
-// Per item and lane: the column pointers (clamped into the image) and which of them are real.
-struct NormalCol {
-    const float *d, *de, *p;
-    float *dd;
-    bool xin, xein;
+// Per item and lane: the column indices of its two pixels clamped into the image (consecutive when
+// the width is even, so that a pair is one aligned 8-byte load) and which of them are real.
+struct NormalCols {
+    int ia, ib;
+    bool ina, inb;
 };
 
-__device__ __forceinline__ void nm_fetch_row(const NormalCol &c, int HW, int W, int H, int y, NormalRow &r) {
-    const int yb = min(max(y + 1, 0), H - 1), yc = min(max(y, 0), H - 1), ya = min(max(y - 1, 0), H - 1);
-    const float db = __ldg(c.d + yb * W), de = __ldg(c.de + yc * W);
-    const float p0 = __ldg(c.p + yc * W), p1 = __ldg(c.p + HW + yc * W), p2 = __ldg(c.p + 2 * HW + yc * W);
-    const float dd = c.dd[ya * W];
-    const bool bin = (unsigned)(y + 1) < (unsigned)H, cin = (unsigned)y < (unsigned)H, ain = (unsigned)(y - 1) < (unsigned)H;
-    r.d_below = c.xin && bin ? db : -1.0f;
-    r.d_ext = c.xein && cin ? de : -1.0f;
-    const bool pin = c.xin && cin;
-    r.p0 = pin ? p0 : 0.0f;
-    r.p1 = pin ? p1 : 0.0f;
-    r.p2 = pin ? p2 : 0.0f;
-    r.dd = c.xin && ain ? dd : 0.0f;
+template <bool EVEN>
+__device__ __forceinline__ float2 nm_ld2(const float *row, const NormalCols &c) {
+    if constexpr (EVEN) return __ldg(reinterpret_cast<const float2 *>(row + c.ia));
+    else return make_float2(__ldg(row + c.ia), __ldg(row + c.ib));
 }
 
-__global__ void __launch_bounds__(kNormalThreads, 3) k_normal(NormalArgs a) {
+__device__ __forceinline__ float2 nm_sel2(bool a, bool b, float2 v, float z) {
+    return make_float2(a ? v.x : z, b ? v.y : z);
+}
+
+template <bool EVEN>
+__device__ __forceinline__ void nm_fetch_row(const float *D, const float *Pr, const float *DD, const NormalCols &c,
+                                             int HW, int W, int H, int y, NormalRow2 &r) {
+    const int yb = min(max(y + 1, 0), H - 1), yc = min(max(y, 0), H - 1), ya = min(max(y - 1, 0), H - 1);
+    const float2 db = nm_ld2<EVEN>(D + yb * W, c);
+    const float2 p0 = nm_ld2<EVEN>(Pr + yc * W, c), p1 = nm_ld2<EVEN>(Pr + HW + yc * W, c),
+                 p2 = nm_ld2<EVEN>(Pr + 2 * HW + yc * W, c);
+    float2 dd;
+    if constexpr (EVEN) dd = *reinterpret_cast<const float2 *>(DD + ya * W + c.ia);
+    else dd = make_float2(DD[ya * W + c.ia], DD[ya * W + c.ib]);
+    const bool bin = (unsigned)(y + 1) < (unsigned)H, cin = (unsigned)y < (unsigned)H, ain = (unsigned)(y - 1) < (unsigned)H;
+    r.d_below = nm_sel2(c.ina && bin, c.inb && bin, db, -1.0f);
+    r.p0 = nm_sel2(c.ina && cin, c.inb && cin, p0, 0.0f);
+    r.p1 = nm_sel2(c.ina && cin, c.inb && cin, p1, 0.0f);
+    r.p2 = nm_sel2(c.ina && cin, c.inb && cin, p2, 0.0f);
+    r.dd = nm_sel2(c.ina && ain, c.inb && ain, dd, 0.0f);
+}
+
+template <bool EVEN>
+__global__ void __launch_bounds__(kNormalThreads, 2) k_normal(NormalArgs a) {
+    using namespace fp2;
     const int lane = threadIdx.x & 31;
     const int W = a.W, H = a.H, HW = a.H * a.W;      // the launcher checks 3 H W < 2^31
     const int cblocks = (W + kNCols - 1) / kNCols, strips = (H + kNRows - 1) / kNRows;
     const int per_view = cblocks * strips;
     const long long items = (long long)a.V * per_view;
     const long long nwarps = (long long)gridDim.x * (kNormalThreads / 32);
+    const float2 z2 = splat(0.0f);
     double acc = 0.0;
     for (long long item = (long long)blockIdx.x * (kNormalThreads / 32) + (threadIdx.x >> 5); item < items;
          item += nwarps) {
         const int v = (int)(item / per_view);
         const int t = (int)(item - (long long)v * per_view);
         const int sr = t / cblocks;
-        const int y0 = sr * kNRows, x = (t - sr * cblocks) * kNCols - 1 + lane;
-        // lane 0 also reads the column left of it, lane 31 the one right of it
-        const int xe = lane == 0 ? x - 1 : (lane == 31 ? x + 1 : -1);
-        const bool own_col = lane >= 1 && lane <= kNCols && x < W;
+        const int y0 = sr * kNRows, xa = (t - sr * cblocks) * kNCols - 2 + 2 * lane;   // the lane's first column
+        const bool inner = lane >= 1 && lane <= kNCols / 2;
+        const bool own_a = inner && xa < W, own_b = inner && xa + 1 < W;
         const gs_camera &cam = a.cams[v];
         const float ifx = 1.0f / cam.fx, ify = 1.0f / cam.fy, cy = cam.cy;
-        const float rxl = nm_ray(x - 1, cam.cx, ifx), rxc = nm_ray(x, cam.cx, ifx), rxr = nm_ray(x + 1, cam.cx, ifx);
-        const bool colok = x >= 1 && x <= W - 2;
-        NormalCol c;
-        const int xc = min(max(x, 0), W - 1), xec = min(max(xe, 0), W - 1);
-        c.d = a.depth + (size_t)v * HW + xc;
-        c.de = a.depth + (size_t)v * HW + xec;
-        c.p = a.prior + (size_t)v * 3 * HW + xc;
-        c.dd = a.d_depth + (size_t)v * HW + xc;
-        c.xin = (unsigned)x < (unsigned)W;
-        c.xein = (unsigned)xe < (unsigned)W;
-        // rows y0 - 2 and y0 - 1 of the own column, then the first step's inputs (row y0 - 1)
-        const float dm2 = __ldg(c.d + min(max(y0 - 2, 0), H - 1) * W), dm1 = __ldg(c.d + min(max(y0 - 1, 0), H - 1) * W);
-        float d_up = c.xin && y0 >= 2 ? dm2 : -1.0f;
-        float d_mid = c.xin && y0 >= 1 ? dm1 : -1.0f;
-        bool ok_up = nm_depth_ok(d_up), ok_mid = nm_depth_ok(d_mid);
+        const float r_m = nm_ray(xa - 1, cam.cx, ifx), r_a = nm_ray(xa, cam.cx, ifx), r_b = nm_ray(xa + 1, cam.cx, ifx),
+                    r_p = nm_ray(xa + 2, cam.cx, ifx);
+        const float2 rxl = make_float2(r_m, r_a), rxc = make_float2(r_a, r_b), rxr = make_float2(r_b, r_p);
+        const bool colok_a = xa >= 1 && xa <= W - 2, colok_b = xa + 1 >= 1 && xa + 1 <= W - 2;
+        NormalCols c;
+        c.ina = (unsigned)xa < (unsigned)W;
+        c.inb = (unsigned)(xa + 1) < (unsigned)W;
+        if (EVEN) {   // xa is even: both columns or neither inside the image
+            c.ia = min(max(xa, 0), W - 2);
+            c.ib = c.ia + 1;
+        } else {
+            c.ia = min(max(xa, 0), W - 1);
+            c.ib = min(max(xa + 1, 0), W - 1);
+        }
+        const float *D = a.depth + (size_t)v * HW;
+        const float *Pr = a.prior + (size_t)v * 3 * HW;
+        float *DD = a.d_depth + (size_t)v * HW;
+        // rows y0 - 2 and y0 - 1 of the lane's columns, then the first step's inputs (row y0 - 1)
+        const float2 dm2 = nm_ld2<EVEN>(D + min(max(y0 - 2, 0), H - 1) * W, c);
+        const float2 dm1 = nm_ld2<EVEN>(D + min(max(y0 - 1, 0), H - 1) * W, c);
+        float2 d_up = nm_sel2(c.ina && y0 >= 2, c.inb && y0 >= 2, dm2, -1.0f);
+        float2 d_mid = nm_sel2(c.ina && y0 >= 1, c.inb && y0 >= 1, dm1, -1.0f);
         float ry_up = nm_ray(y0 - 2, cy, ify), ry_mid = nm_ray(y0 - 1, cy, ify);
-        const int yend = min(y0 + kNRows, H);                // the rows y0 .. yend - 1 are this item's
-        NormalRow cur;
-        nm_fetch_row(c, HW, W, H, y0 - 1, cur);
-        float gxp0 = 0.f, gxp1 = 0.f, gxp2 = 0.f;            // G_x of the row above the current one
-        float gyp0 = 0.f, gyp1 = 0.f, gyp2 = 0.f;            // G_y of the row above
-        float gyq0 = 0.f, gyq1 = 0.f, gyq2 = 0.f;            // G_y two rows above
+        NormalRow2 cur;
+        nm_fetch_row<EVEN>(D, Pr, DD, c, HW, W, H, y0 - 1, cur);
+        float2 gxp0 = z2, gxp1 = z2, gxp2 = z2;            // G_x of the row above the current one
+        float2 gyp0 = z2, gyp1 = z2, gyp2 = z2;            // G_y of the row above
+        float2 gyq0 = z2, gyq1 = z2, gyq2 = z2;            // G_y two rows above
         float acc_item = 0.f;
+        const int yend = min(y0 + kNRows, H);              // the rows y0 .. yend - 1 are this item's
         for (int y = y0 - 1; y <= yend; ++y) {
-            NormalRow nxt;
-            if (y < yend) nm_fetch_row(c, HW, W, H, y + 1, nxt);
-            const float d_dn = cur.d_below;
-            const bool ok_dn = nm_depth_ok(d_dn);
+            NormalRow2 nxt;
+            if (y < yend) nm_fetch_row<EVEN>(D, Pr, DD, c, HW, W, H, y + 1, nxt);
+            const float2 d_dn = cur.d_below;
             const float ry_dn = nm_ray(y + 1, cy, ify);
-            // the row's depths left and right of the lane (lanes 0 and 31 from their extra read)
-            const float d_l0 = __shfl_up_sync(0xffffffffu, d_mid, 1), d_r0 = __shfl_down_sync(0xffffffffu, d_mid, 1);
-            const float d_l = lane == 0 ? cur.d_ext : d_l0, d_r = lane == 31 ? cur.d_ext : d_r0;
-            const bool ok = colok && y >= 1 && y <= H - 2 && ok_mid && ok_up && ok_dn && nm_depth_ok(d_l) &&
-                            nm_depth_ok(d_r);
-            float gx0 = 0.f, gx1 = 0.f, gx2 = 0.f, gy0 = 0.f, gy1 = 0.f, gy2 = 0.f;
-            if (ok) {
+            // the row's depths left and right of each column: the lane's other column, or the
+            // neighbouring lane's by one shuffle
+            const float2 d_l = make_float2(__shfl_up_sync(0xffffffffu, d_mid.y, 1), d_mid.x);
+            const float2 d_r = make_float2(d_mid.y, __shfl_down_sync(0xffffffffu, d_mid.x, 1));
+            const bool rowok = y >= 1 && y <= H - 2;
+            const bool ok_a = colok_a && rowok && nm_depth_ok(d_mid.x) && nm_depth_ok(d_up.x) && nm_depth_ok(d_dn.x) &&
+                              nm_depth_ok(d_l.x) && nm_depth_ok(d_r.x);
+            const bool ok_b = colok_b && rowok && nm_depth_ok(d_mid.y) && nm_depth_ok(d_up.y) && nm_depth_ok(d_dn.y) &&
+                              nm_depth_ok(d_l.y) && nm_depth_ok(d_r.y);
+            float2 gx0 = z2, gx1 = z2, gx2 = z2, gy0 = z2, gy1 = z2, gy2 = z2;
+            if (ok_a || ok_b) {
                 // neighbours in a row share the ray's y component, in a column its x component
-                const float dx_ = d_r - d_l, dy_ = d_dn - d_up;
-                const float tx0 = d_r * rxr - d_l * rxl, tx1 = dx_ * ry_mid, tx2 = dx_;
-                const float ty0 = dy_ * rxc, ty1 = d_dn * ry_dn - d_up * ry_up, ty2 = dy_;
+                const float2 dx_ = add(d_r, neg(d_l)), dy_ = add(d_dn, neg(d_up));
+                const float2 tx0 = add(mul(d_r, rxr), neg(mul(d_l, rxl))), tx1 = mul(dx_, splat(ry_mid)), tx2 = dx_;
+                const float2 ty0 = mul(dy_, rxc), ty1 = add(mul(d_dn, splat(ry_dn)), neg(mul(d_up, splat(ry_up)))),
+                             ty2 = dy_;
                 // u = t_y x t_x
-                const float u0 = ty1 * tx2 - ty2 * tx1, u1 = ty2 * tx0 - ty0 * tx2, u2 = ty0 * tx1 - ty1 * tx0;
-                const float uu = u0 * u0 + u1 * u1 + u2 * u2;
-                if (uu > 0.0f) {
-                    // 1/|u| by the hardware reciprocal square root (a value, not a decision)
-                    const float inu = rsqrtf(uu);
-                    const float n0 = u0 * inu, n1 = u1 * inu, n2 = u2 * inu;
-                    const float cc = 1.0f - (n0 * cur.p0 + n1 * cur.p1 + n2 * cur.p2);
-                    if (own_col && y >= y0 && y < yend) acc_item += fabsf(cc);
-                    // -scale sign(c) weights the adjoint (sign(0) = 0)
-                    const float kk = cc > 0.f ? -a.scale : (cc < 0.f ? a.scale : 0.f);
-                    const float gn0 = kk * cur.p0, gn1 = kk * cur.p1, gn2 = kk * cur.p2;
-                    const float pn = n0 * gn0 + n1 * gn1 + n2 * gn2;
-                    const float gu0 = (gn0 - n0 * pn) * inu, gu1 = (gn1 - n1 * pn) * inu, gu2 = (gn2 - n2 * pn) * inu;
-                    // G_x = gu x t_y, G_y = t_x x gu
-                    gx0 = gu1 * ty2 - gu2 * ty1; gx1 = gu2 * ty0 - gu0 * ty2; gx2 = gu0 * ty1 - gu1 * ty0;
-                    gy0 = tx1 * gu2 - tx2 * gu1; gy1 = tx2 * gu0 - tx0 * gu2; gy2 = tx0 * gu1 - tx1 * gu0;
-                }
+                const float2 u0 = add(mul(ty1, tx2), neg(mul(ty2, tx1)));
+                const float2 u1 = add(mul(ty2, tx0), neg(mul(ty0, tx2)));
+                const float2 u2 = add(mul(ty0, tx1), neg(mul(ty1, tx0)));
+                const float2 uu = fma(u0, u0, fma(u1, u1, mul(u2, u2)));
+                const bool va = ok_a && uu.x > 0.0f, vb = ok_b && uu.y > 0.0f;
+                // 1/|u| by the hardware reciprocal square root (a value, not a decision)
+                const float2 inu = make_float2(va ? rsqrtf(uu.x) : 0.f, vb ? rsqrtf(uu.y) : 0.f);
+                const float2 n0 = mul(u0, inu), n1 = mul(u1, inu), n2 = mul(u2, inu);
+                const float2 cc = add(splat(1.0f), neg(fma(n0, cur.p0, fma(n1, cur.p1, mul(n2, cur.p2)))));
+                if (y >= y0 && y < yend)   // the own pixels of the item add their loss (selects: NaN-safe)
+                    acc_item += (own_a && va ? fabsf(cc.x) : 0.f) + (own_b && vb ? fabsf(cc.y) : 0.f);
+                // -scale sign(c) weights the adjoint (sign(0) = 0)
+                const float2 kk = make_float2(!va ? 0.f : (cc.x > 0.f ? -a.scale : (cc.x < 0.f ? a.scale : 0.f)),
+                                              !vb ? 0.f : (cc.y > 0.f ? -a.scale : (cc.y < 0.f ? a.scale : 0.f)));
+                const float2 gn0 = mul(kk, cur.p0), gn1 = mul(kk, cur.p1), gn2 = mul(kk, cur.p2);
+                const float2 pn = fma(n0, gn0, fma(n1, gn1, mul(n2, gn2)));
+                const float2 gu0 = mul(add(gn0, neg(mul(n0, pn))), inu);
+                const float2 gu1 = mul(add(gn1, neg(mul(n1, pn))), inu);
+                const float2 gu2 = mul(add(gn2, neg(mul(n2, pn))), inu);
+                // G_x = gu x t_y, G_y = t_x x gu; selects, not products with zero: an invalid
+                // pixel's tangents may hold NaN or inf
+                gx0 = nm_sel2(va, vb, add(mul(gu1, ty2), neg(mul(gu2, ty1))), 0.f);
+                gx1 = nm_sel2(va, vb, add(mul(gu2, ty0), neg(mul(gu0, ty2))), 0.f);
+                gx2 = nm_sel2(va, vb, add(mul(gu0, ty1), neg(mul(gu1, ty0))), 0.f);
+                gy0 = nm_sel2(va, vb, add(mul(tx1, gu2), neg(mul(tx2, gu1))), 0.f);
+                gy1 = nm_sel2(va, vb, add(mul(tx2, gu0), neg(mul(tx0, gu2))), 0.f);
+                gy2 = nm_sel2(va, vb, add(mul(tx0, gu1), neg(mul(tx1, gu0))), 0.f);
             }
-            // the row above (y - 1) is complete: + G_x of its left neighbour (t_x there =
+            // the row above (y - 1) is complete: + G_x of each pixel's left neighbour (t_x there =
             // P(q) - P(q - 2)), - G_x of its right one, + G_y of the pixel above it, - G_y of this row
-            const float l0 = __shfl_up_sync(0xffffffffu, gxp0, 1), r0 = __shfl_down_sync(0xffffffffu, gxp0, 1);
-            const float l1 = __shfl_up_sync(0xffffffffu, gxp1, 1), r1 = __shfl_down_sync(0xffffffffu, gxp1, 1);
-            const float l2 = __shfl_up_sync(0xffffffffu, gxp2, 1), r2 = __shfl_down_sync(0xffffffffu, gxp2, 1);
-            if (own_col && y > y0 && y <= yend) {
-                const float dP0 = l0 - r0 + gyq0 - gy0, dP1 = l1 - r1 + gyq1 - gy1, dP2 = l2 - r2 + gyq2 - gy2;
-                c.dd[(y - 1) * W] = cur.dd + (rxc * dP0 + ry_up * dP1 + dP2);
+            const float2 l0 = make_float2(__shfl_up_sync(0xffffffffu, gxp0.y, 1), gxp0.x);
+            const float2 l1 = make_float2(__shfl_up_sync(0xffffffffu, gxp1.y, 1), gxp1.x);
+            const float2 l2 = make_float2(__shfl_up_sync(0xffffffffu, gxp2.y, 1), gxp2.x);
+            const float2 r0 = make_float2(gxp0.y, __shfl_down_sync(0xffffffffu, gxp0.x, 1));
+            const float2 r1 = make_float2(gxp1.y, __shfl_down_sync(0xffffffffu, gxp1.x, 1));
+            const float2 r2 = make_float2(gxp2.y, __shfl_down_sync(0xffffffffu, gxp2.x, 1));
+            if ((own_a || own_b) && y > y0 && y <= yend) {
+                const float2 dP0 = add(add(l0, neg(r0)), add(gyq0, neg(gy0)));
+                const float2 dP1 = add(add(l1, neg(r1)), add(gyq1, neg(gy1)));
+                const float2 dP2 = add(add(l2, neg(r2)), add(gyq2, neg(gy2)));
+                const float2 nd = add(cur.dd, fma(rxc, dP0, fma(splat(ry_up), dP1, dP2)));
+                float *row = DD + (y - 1) * W;
+                if (EVEN) {   // xa even and inside: both pixels inside
+                    *reinterpret_cast<float2 *>(row + c.ia) = nd;
+                } else {
+                    if (own_a) row[c.ia] = nd.x;
+                    if (own_b) row[c.ib] = nd.y;
+                }
             }
             gyq0 = gyp0; gyq1 = gyp1; gyq2 = gyp2;
             gyp0 = gy0; gyp1 = gy1; gyp2 = gy2;
             gxp0 = gx0; gxp1 = gx1; gxp2 = gx2;
-            d_up = d_mid; ok_up = ok_mid; ry_up = ry_mid;
-            d_mid = d_dn; ok_mid = ok_dn; ry_mid = ry_dn;
+            d_up = d_mid;
+            ry_up = ry_mid;
+            d_mid = d_dn;
+            ry_mid = ry_dn;
             if (y < yend) cur = nxt;
         }
         acc += (double)acc_item;
@@ -181,18 +231,29 @@ __global__ void __launch_bounds__(kNormalThreads, 3) k_normal(NormalArgs a) {
 }
 
 int launch_loss_normal(const NormalArgs &a, cudaStream_t s) {
-    // persistent: as many CTAs as are resident at once (a second wave would only add a tail)
-    static int occ = [] {
+    if (a.W < 3 || a.H < 3) return check_launch();   // no pixel has four neighbours: L and d_depth unchanged
+    if (3LL * a.H * a.W >= (1LL << 31)) return GS_ERR_INVALID_ARG;   // 32-bit offsets inside a view
+    // an even width keeps every pixel pair 8-byte aligned (given 8-byte aligned planes)
+    const bool even = (a.W % 2 == 0) && (((uintptr_t)a.depth | (uintptr_t)a.prior | (uintptr_t)a.d_depth) % 8 == 0);
+    static int occ_e = [] {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_normal, kNormalThreads, 0) != cudaSuccess || b < 1) b = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_normal<true>, kNormalThreads, 0) != cudaSuccess || b < 1)
+            b = 1;
         return b;
     }();
-    if (3LL * a.H * a.W >= (1LL << 31)) return GS_ERR_INVALID_ARG;   // 32-bit offsets inside a view
+    static int occ_o = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_normal<false>, kNormalThreads, 0) != cudaSuccess || b < 1)
+            b = 1;
+        return b;
+    }();
+    // persistent: as many CTAs as are resident at once (a second wave would only add a tail)
     const long long items = (long long)a.V * ((a.W + kNCols - 1) / kNCols) * ((a.H + kNRows - 1) / kNRows);
     const long long warps = kNormalThreads / 32;
     const long long grid = std::max<long long>(1, std::min<long long>((items + warps - 1) / warps,
-                                                                      (long long)device_sm_count() * occ));
-    k_normal<<<(unsigned)grid, kNormalThreads, 0, s>>>(a);
+                                                                      (long long)device_sm_count() * (even ? occ_e : occ_o)));
+    if (even) k_normal<true><<<(unsigned)grid, kNormalThreads, 0, s>>>(a);
+    else k_normal<false><<<(unsigned)grid, kNormalThreads, 0, s>>>(a);
     count_launches(1);
     return check_launch();
 }

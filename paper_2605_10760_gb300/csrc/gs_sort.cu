@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(BinArgs a) {
         }
         scan_store<kScanIPT>(a, base, y);
         __syncthreads();
+        if (nparts <= (long long)gridDim.x) break;   // every partition was taken by a first claim
     }
 }
 
@@ -319,6 +320,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_scan_emit(BinArgs a) {
             }
         }
         __syncthreads();
+        if (nparts <= (long long)gridDim.x) break;   // every partition was taken by a first claim
     }
     for (int i = threadIdx.x; i < a.passes * 256; i += kEmitThreads) {
         const uint32_t c = (&s_hist[0][0])[i];
@@ -514,6 +516,9 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
                 }
             }
         }
+        // a grid that covers every partition claimed them all with its first claims: leave without
+        // another claim round trip
+        if (nparts <= gridDim.x) break;
         __syncthreads();
         // next partition; the per-warp digit counters start from zero again
         if (threadIdx.x == 0) {

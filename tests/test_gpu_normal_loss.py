@@ -1,6 +1,7 @@
 """GPU parity of the normal term of Eq. 4 (gs_loss_normal) against the FP64 oracle, on images that
-span several of the kernel's 30-column x 16-row items in both directions or less than one, with
-ragged last items, down to images with no interior pixel."""
+span several of the kernel's 60-column x 16-row items in both directions or less than one, with
+ragged last items, of even width (pixel pairs loaded as 8-byte pairs) and odd width, down to
+images with no interior pixel."""
 import numpy as np
 import pytest
 
@@ -41,7 +42,7 @@ def _normal_case(rng, V, H, W):
     return depth.astype(np.float32), prior.astype(np.float32), intr.astype(np.float32).astype(np.float64), cams
 
 
-@pytest.mark.parametrize("V,H,W", [(2, 37, 53), (3, 9, 33), (1, 2, 3), (1, 680, 1200)])
+@pytest.mark.parametrize("V,H,W", [(2, 37, 53), (2, 21, 122), (3, 9, 33), (1, 2, 3), (1, 680, 1200)])
 def test_normal_loss_matches_oracle(R, V, H, W):
     rng = np.random.default_rng(V * H + W)
     depth, prior, intr, cams = _normal_case(rng, V, H, W)
