@@ -20,8 +20,10 @@
 // the lane's other component or by one warp shuffle, G_y of the rows above and below from
 // registers.  Every normal is computed once per item (the halo columns and the two rows beyond the
 // strip are recomputed by the neighbouring items), and a pixel costs its depth, its prior and a
-// read-modify-write of d_depth.  The next row's loads are issued before the current row's
-// arithmetic.  Values in FP32; the loss in FP32 per item and FP64 per CTA.
+// read-modify-write of d_depth.  A row's inputs are copied by cp.async into a per-warp ring of
+// shared-memory rows kNRing - 1 steps before the row is needed (each lane copies and later reads
+// only its own two columns), so every warp keeps several rows of loads in flight without holding
+// them in registers.  Values in FP32; the loss in FP32 per item and FP64 per CTA.
 #include <algorithm>
 
 #include "gs_kernels.cuh"
@@ -31,6 +33,8 @@ namespace gs {
 constexpr int kNormalThreads = 256;
 constexpr int kNCols = 60;           // output columns of a warp's item (32 lanes x 2, less two halo lanes)
 constexpr int kNRows = 16;           // output rows of an item
+constexpr int kNRing = 4;            // rows of inputs per warp in shared memory (kNRing - 1 in flight)
+constexpr int kNPlanes = 5;          // per ring row: depth below, three prior components, d_depth above
 
 __device__ __forceinline__ bool nm_depth_ok(float d) { return d > 0.0f && d < __int_as_float(0x7f800000); }
 
@@ -51,16 +55,8 @@ __device__ __forceinline__ void nm_block_add(double v, double *out) {
     }
 }
 
-// The global inputs of one row step for the lane's two columns: the depths one row below the row
-// being normalised, the prior of its pixels, and d_depth of its pixels one row above (whose
-// gradient the step finishes).  Every load reads a clamped (in-image) address; out-of-image depths
-// then read as -1 (invalid), priors and d_depth as 0.
-struct NormalRow2 {
-    float2 d_below, p0, p1, p2, dd;
-};
-
 // Per item and lane: the column indices of its two pixels clamped into the image (consecutive when
-// the width is even, so that a pair is one aligned 8-byte load) and which of them are real.
+// the width is even, so that a pair is one aligned 8-byte copy) and which of them are real.
 struct NormalCols {
     int ia, ib;
     bool ina, inb;
@@ -76,28 +72,41 @@ __device__ __forceinline__ float2 nm_sel2(bool a, bool b, float2 v, float z) {
     return make_float2(a ? v.x : z, b ? v.y : z);
 }
 
+template <int BYTES>
+__device__ __forceinline__ void nm_cp_async(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void nm_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void nm_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(kNRing - 1) : "memory"); }
+
+// Copies the inputs of the step that normalises row y into ring row `slot` (the lane's two
+// columns of each plane): the depths of row y + 1, the prior of row y, d_depth of row y - 1, every
+// row clamped into the image (the out-of-image values are replaced when the ring row is read).
+// One commit group per step; a step past the item's last row commits an empty group, so that
+// waiting for all but the kNRing - 1 newest groups always completes the step being consumed.
 template <bool EVEN>
-__device__ __forceinline__ void nm_fetch_row(const float *D, const float *Pr, const float *DD, const NormalCols &c,
-                                             int HW, int W, int H, int y, NormalRow2 &r) {
+__device__ __forceinline__ void nm_issue_row(float (*ring)[64], const float *D, const float *Pr, const float *DD,
+                                             const NormalCols &c, int HW, int W, int H, int y, int lane) {
     const int yb = min(max(y + 1, 0), H - 1), yc = min(max(y, 0), H - 1), ya = min(max(y - 1, 0), H - 1);
-    const float2 db = nm_ld2<EVEN>(D + yb * W, c);
-    const float2 p0 = nm_ld2<EVEN>(Pr + yc * W, c), p1 = nm_ld2<EVEN>(Pr + HW + yc * W, c),
-                 p2 = nm_ld2<EVEN>(Pr + 2 * HW + yc * W, c);
-    float2 dd;
-    if constexpr (EVEN) dd = *reinterpret_cast<const float2 *>(DD + ya * W + c.ia);
-    else dd = make_float2(DD[ya * W + c.ia], DD[ya * W + c.ib]);
-    const bool bin = (unsigned)(y + 1) < (unsigned)H, cin = (unsigned)y < (unsigned)H, ain = (unsigned)(y - 1) < (unsigned)H;
-    r.d_below = nm_sel2(c.ina && bin, c.inb && bin, db, -1.0f);
-    r.p0 = nm_sel2(c.ina && cin, c.inb && cin, p0, 0.0f);
-    r.p1 = nm_sel2(c.ina && cin, c.inb && cin, p1, 0.0f);
-    r.p2 = nm_sel2(c.ina && cin, c.inb && cin, p2, 0.0f);
-    r.dd = nm_sel2(c.ina && ain, c.inb && ain, dd, 0.0f);
+    const float *src[kNPlanes] = {D + yb * W, Pr + yc * W, Pr + HW + yc * W, Pr + 2 * HW + yc * W, DD + ya * W};
+#pragma unroll
+    for (int k = 0; k < kNPlanes; ++k) {
+        float *dst = ring[k] + 2 * lane;
+        if constexpr (EVEN) {
+            nm_cp_async<8>(dst, src[k] + c.ia);
+        } else {
+            nm_cp_async<4>(dst, src[k] + c.ia);
+            nm_cp_async<4>(dst + 1, src[k] + c.ib);
+        }
+    }
 }
 
 template <bool EVEN>
 __global__ void __launch_bounds__(kNormalThreads, 2) k_normal(NormalArgs a) {
     using namespace fp2;
+    __shared__ __align__(16) float s_ring[kNormalThreads / 32][kNRing][kNPlanes][64];
     const int lane = threadIdx.x & 31;
+    float (*ring)[kNPlanes][64] = s_ring[threadIdx.x >> 5];
     const int W = a.W, H = a.H, HW = a.H * a.W;      // the launcher checks 3 H W < 2^31
     const int cblocks = (W + kNCols - 1) / kNCols, strips = (H + kNRows - 1) / kNRows;
     const int per_view = cblocks * strips;
@@ -132,23 +141,39 @@ __global__ void __launch_bounds__(kNormalThreads, 2) k_normal(NormalArgs a) {
         const float *D = a.depth + (size_t)v * HW;
         const float *Pr = a.prior + (size_t)v * 3 * HW;
         float *DD = a.d_depth + (size_t)v * HW;
-        // rows y0 - 2 and y0 - 1 of the lane's columns, then the first step's inputs (row y0 - 1)
+        const int yend = min(y0 + kNRows, H);              // the rows y0 .. yend - 1 are this item's
+        const int nsteps = yend - y0 + 2;                  // rows y0 - 1 .. yend are normalised
+        // the first kNRing - 1 steps' inputs in flight, then rows y0 - 2 and y0 - 1 of the lane's
+        // columns (plain loads)
+#pragma unroll
+        for (int q = 0; q < kNRing - 1; ++q) {
+            if (q < nsteps) nm_issue_row<EVEN>(ring[q], D, Pr, DD, c, HW, W, H, y0 - 1 + q, lane);
+            nm_cp_commit();
+        }
         const float2 dm2 = nm_ld2<EVEN>(D + min(max(y0 - 2, 0), H - 1) * W, c);
         const float2 dm1 = nm_ld2<EVEN>(D + min(max(y0 - 1, 0), H - 1) * W, c);
         float2 d_up = nm_sel2(c.ina && y0 >= 2, c.inb && y0 >= 2, dm2, -1.0f);
         float2 d_mid = nm_sel2(c.ina && y0 >= 1, c.inb && y0 >= 1, dm1, -1.0f);
         float ry_up = nm_ray(y0 - 2, cy, ify), ry_mid = nm_ray(y0 - 1, cy, ify);
-        NormalRow2 cur;
-        nm_fetch_row<EVEN>(D, Pr, DD, c, HW, W, H, y0 - 1, cur);
         float2 gxp0 = z2, gxp1 = z2, gxp2 = z2;            // G_x of the row above the current one
         float2 gyp0 = z2, gyp1 = z2, gyp2 = z2;            // G_y of the row above
         float2 gyq0 = z2, gyq1 = z2, gyq2 = z2;            // G_y two rows above
         float acc_item = 0.f;
-        const int yend = min(y0 + kNRows, H);              // the rows y0 .. yend - 1 are this item's
-        for (int y = y0 - 1; y <= yend; ++y) {
-            NormalRow2 nxt;
-            if (y < yend) nm_fetch_row<EVEN>(D, Pr, DD, c, HW, W, H, y + 1, nxt);
-            const float2 d_dn = cur.d_below;
+        for (int st = 0; st < nsteps; ++st) {
+            const int y = y0 - 1 + st;
+            // the inputs kNRing - 1 steps ahead go into the ring row the previous step read
+            const int ahead = st + kNRing - 1;
+            if (ahead < nsteps) nm_issue_row<EVEN>(ring[ahead % kNRing], D, Pr, DD, c, HW, W, H, y0 - 1 + ahead, lane);
+            nm_cp_commit();
+            nm_cp_wait();                                  // this step's group has landed
+            const float(*rr)[64] = ring[st % kNRing];
+            const bool bin = (unsigned)(y + 1) < (unsigned)H, cin = (unsigned)y < (unsigned)H,
+                       ain = (unsigned)(y - 1) < (unsigned)H;
+            const float2 d_dn = nm_sel2(c.ina && bin, c.inb && bin, *reinterpret_cast<const float2 *>(rr[0] + 2 * lane), -1.0f);
+            const float2 p0 = nm_sel2(c.ina && cin, c.inb && cin, *reinterpret_cast<const float2 *>(rr[1] + 2 * lane), 0.0f);
+            const float2 p1 = nm_sel2(c.ina && cin, c.inb && cin, *reinterpret_cast<const float2 *>(rr[2] + 2 * lane), 0.0f);
+            const float2 p2 = nm_sel2(c.ina && cin, c.inb && cin, *reinterpret_cast<const float2 *>(rr[3] + 2 * lane), 0.0f);
+            const float2 ddv = nm_sel2(c.ina && ain, c.inb && ain, *reinterpret_cast<const float2 *>(rr[4] + 2 * lane), 0.0f);
             const float ry_dn = nm_ray(y + 1, cy, ify);
             // the row's depths left and right of each column: the lane's other column, or the
             // neighbouring lane's by one shuffle
@@ -175,13 +200,13 @@ __global__ void __launch_bounds__(kNormalThreads, 2) k_normal(NormalArgs a) {
                 // 1/|u| by the hardware reciprocal square root (a value, not a decision)
                 const float2 inu = make_float2(va ? rsqrtf(uu.x) : 0.f, vb ? rsqrtf(uu.y) : 0.f);
                 const float2 n0 = mul(u0, inu), n1 = mul(u1, inu), n2 = mul(u2, inu);
-                const float2 cc = add(splat(1.0f), neg(fma(n0, cur.p0, fma(n1, cur.p1, mul(n2, cur.p2)))));
+                const float2 cc = add(splat(1.0f), neg(fma(n0, p0, fma(n1, p1, mul(n2, p2)))));
                 if (y >= y0 && y < yend)   // the own pixels of the item add their loss (selects: NaN-safe)
                     acc_item += (own_a && va ? fabsf(cc.x) : 0.f) + (own_b && vb ? fabsf(cc.y) : 0.f);
                 // -scale sign(c) weights the adjoint (sign(0) = 0)
                 const float2 kk = make_float2(!va ? 0.f : (cc.x > 0.f ? -a.scale : (cc.x < 0.f ? a.scale : 0.f)),
                                               !vb ? 0.f : (cc.y > 0.f ? -a.scale : (cc.y < 0.f ? a.scale : 0.f)));
-                const float2 gn0 = mul(kk, cur.p0), gn1 = mul(kk, cur.p1), gn2 = mul(kk, cur.p2);
+                const float2 gn0 = mul(kk, p0), gn1 = mul(kk, p1), gn2 = mul(kk, p2);
                 const float2 pn = fma(n0, gn0, fma(n1, gn1, mul(n2, gn2)));
                 const float2 gu0 = mul(add(gn0, neg(mul(n0, pn))), inu);
                 const float2 gu1 = mul(add(gn1, neg(mul(n1, pn))), inu);
@@ -207,7 +232,7 @@ __global__ void __launch_bounds__(kNormalThreads, 2) k_normal(NormalArgs a) {
                 const float2 dP0 = add(add(l0, neg(r0)), add(gyq0, neg(gy0)));
                 const float2 dP1 = add(add(l1, neg(r1)), add(gyq1, neg(gy1)));
                 const float2 dP2 = add(add(l2, neg(r2)), add(gyq2, neg(gy2)));
-                const float2 nd = add(cur.dd, fma(rxc, dP0, fma(splat(ry_up), dP1, dP2)));
+                const float2 nd = add(ddv, fma(rxc, dP0, fma(splat(ry_up), dP1, dP2)));
                 float *row = DD + (y - 1) * W;
                 if (EVEN) {   // xa even and inside: both pixels inside
                     *reinterpret_cast<float2 *>(row + c.ia) = nd;
@@ -223,7 +248,6 @@ __global__ void __launch_bounds__(kNormalThreads, 2) k_normal(NormalArgs a) {
             ry_up = ry_mid;
             d_mid = d_dn;
             ry_mid = ry_dn;
-            if (y < yend) cur = nxt;
         }
         acc += (double)acc_item;
     }
