@@ -203,18 +203,20 @@ class Pipeline:
             with torch.cuda.graph(gr):
                 fn()
             self.graphs.append(gr)
-        # the whole step: the gradient zeroing runs on a forked branch of the graph, concurrently
-        # with the projection, the sort and the forward (joined before the backward: a zeroing
-        # still running beside the persistent compositing adjoint would wait for free SMs)
+        # the whole step: the gradient zeroing runs on a branch of the graph forked after the
+        # projection, concurrently with the sort (whose passes leave most SMs idle) and the
+        # forward, and joined before the backward (a zeroing still running beside the persistent
+        # compositing adjoint would wait for free SMs)
         self.whole = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
         with torch.cuda.graph(self.whole):
             main = torch.cuda.current_stream()
+            st = self.stages(zero=False)
+            st[0]()
             side.wait_stream(main)
             with torch.cuda.stream(side):
                 self.zero_grads()
-            st = self.stages(zero=False)
-            for fn in st[:3]:
+            for fn in st[1:3]:
                 fn()
             main.wait_stream(side)
             for fn in st[3:]:

@@ -105,12 +105,14 @@ typedef struct gs_params {
 typedef struct gs_problem {
     int32_t num_views;                 /* V, 1..GS_MAX_VIEWS                          */
     int32_t width, height;             /* image size, pixels                          */
-    int32_t visible_capacity;          /* max visible (view, Gaussian) pairs whose projection
-                                          records and 2-D gradients the workspace holds; 0 = the
-                                          pair count (always enough).  More visible pairs record
-                                          GS_ERR_CAPACITY and drop the excess (K is then counted
-                                          without their keys); gs_read_stats reports the visible
-                                          count needed. */
+    int32_t visible_capacity;          /* slots for projection records and 2-D gradients in the
+                                          workspace; 0 = the pair count (always enough).  A slot is
+                                          taken by every (view, Gaussian) pair that the
+                                          projection's conservative pre-test cannot reject: its
+                                          visible pairs and a few it then finds invisible.  Too
+                                          few slots record GS_ERR_CAPACITY and drop the visible
+                                          pairs beyond them (K is then counted without their
+                                          keys); gs_read_stats reports the slots needed. */
     int64_t num_gaussians;             /* N                                           */
     const int64_t *view_gauss_begin;   /* host [V]                                    */
     const int64_t *view_gauss_count;   /* host [V]                                    */
@@ -180,8 +182,10 @@ typedef struct gs_stats {
     int64_t num_keys;                  /* K of the last gs_bin_sort                           */
     int64_t fwd_pairs;                 /* (pixel, list entry) pairs evaluated by the forward  */
     int64_t bwd_pairs;                 /* (pixel, list entry) pairs walked by the backward    */
-    int64_t num_visible;               /* visible pairs of the last gs_project (also beyond
-                                          visible_capacity: the capacity a retry needs)       */
+    int64_t num_visible;               /* slots the last gs_project took: its visible pairs and
+                                          the candidates its pre-test kept but its decision
+                                          chain culled (also beyond visible_capacity: the
+                                          capacity a retry needs)                             */
 } gs_stats;
 
 const char *gs_error_string(int code);

@@ -131,7 +131,7 @@ int compute_layout(const gs_problem *pb, Layout *L) {
     guard();
     L->o_clist = o; o = align256(o + sizeof(uint32_t) * kClaimClasses * (size_t)std::max<long long>(L->G, 1));
     guard();
-    L->o_slane = o; o = align256(o + (size_t)L->vcap);
+    L->o_slane = o; o = align256(o + sizeof(uint16_t) * (size_t)L->vcap);
     guard();
     L->o_blk = o; o = align256(o + sizeof(uint4) * (size_t)std::max<long long>(chunks_total, 1));
     guard();
@@ -380,7 +380,7 @@ int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stre
     a.st = st;
     a.slot = ws_ptr<uint32_t>(ws, L.o_slot);
     a.vcap = L.vcap;
-    a.slane = ws_ptr<uint8_t>(ws, L.o_slane);
+    a.slane = ws_ptr<uint16_t>(ws, L.o_slane);
     a.blk = ws_ptr<uint4>(ws, L.o_blk);
     a.chunks = L.chunks_total;
     a.Txi = L.Tx;
@@ -516,7 +516,7 @@ int gs_project_bwd(const gs_problem *pb, const gs_gaussians *g, void *ws, const 
     b.views = ws_ptr<ViewEntry>(ws, L.o_views);
     b.cams = pb->cameras;
     b.means = g->means; b.log_scales = g->log_scales; b.quats = g->quats;
-    b.slane = ws_ptr<const uint8_t>(ws, L.o_slane);
+    b.slane = ws_ptr<const uint16_t>(ws, L.o_slane);
     b.blk = ws_ptr<const uint4>(ws, L.o_blk);
     b.g2d = ws_ptr<const float4>(ws, L.o_g2d);
     b.g_means = grads->means; b.g_ls = grads->log_scales; b.g_quats = grads->quats;

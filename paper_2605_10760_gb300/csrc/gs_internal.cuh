@@ -73,6 +73,7 @@ struct Layout {
                                        // the claim-class lists, the slot lanes, the block slot ranges
 };
 constexpr uint32_t kNoSlot = 0xffffffffu;   // pair_slot of a culled pair
+constexpr uint16_t kSlotHole = 0x100;        // slot lane flag: a candidate the decision chain culled
 // The compositing kernels claim (view, tile) items class by class: class k lists the items whose
 // list length n has 2 min(floor(log2 n), 15) + (the bit below the leading one) = 31 - k, so class
 // 0 holds the longest lists and class 31 the lists of 0 or 1 entries (k = 0 from 2^16 entries on).

@@ -18,12 +18,12 @@ struct ProjArgs {
     uint32_t *tile_cnt;         // [G] key count per global tile (tile-bucket binning), else null
     int Txi, Ty_i;
     long long P;                // (view, Gaussian) pairs: the length of touched and slot
-    DevStatus *st;              // errors; num_visible is the slot counter
+    DevStatus *st;              // errors; num_visible is the slot counter (slots taken by candidates)
     uint32_t *slot;             // [P] slot of each visible pair in proj (kNoSlot when culled)
     long long vcap;             // slots in proj
-    uint8_t *slane;             // [vcap] thread (pair) of its projection block that holds each slot
-    uint4 *blk;                 // [chunks] first slot and visible-pair count of each projection
-                                //   block's two rounds
+    uint16_t *slane;            // [vcap] the chunk position of each slot's pair, | kSlotHole when the
+                                //   decision chain culled it
+    uint4 *blk;                 // [chunks] first slot and candidate count of each projection block
     long long chunks;           // projection blocks over all views (the length of blk)
 };
 
@@ -31,8 +31,8 @@ struct ProjBwdArgs {
     const ViewEntry *views;
     const gs_camera *cams;
     const float *means, *log_scales, *quats;
-    const uint8_t *slane;           // [vcap] thread of its projection block that holds each slot
-    const uint4 *blk;               // [chunks] first slot and visible count of the block's two rounds
+    const uint16_t *slane;          // [vcap] chunk position of each slot's pair (| kSlotHole: a hole)
+    const uint4 *blk;               // [chunks] first slot and candidate count of each projection block
     const float4 *g2d;              // [vcap,3] float4
     float *g_means, *g_ls, *g_quats, *g_op, *g_col;
     float *pose_part;               // [chunks, 8]

@@ -2,8 +2,8 @@
 //
 // Forward: the FP32 decision chain of gs_internal.cuh, grid (chunk, view), a pre-test per pair and
 // the chain on the block's compacted candidates.
-// Backward: per block, one thread per visible pair of the forward's block (its slot range); the
-// chain rule through the same projection in FP32 value arithmetic, accumulating
+// Backward: per block, one thread per slot of the forward block's candidates (holes, the slots of
+// candidates the chain found invisible, flagged and skipped); the chain rule through the same projection in FP32 value arithmetic, accumulating
 // dL/d(mean, log-scale, quaternion, opacity, colour) with atomics (several views of one scene add
 // into the same Gaussian; a reduction is issued without waiting for a result, which also makes it
 // cheaper than a load and a store where no two views share a Gaussian) and the per-view SE(3) pose
@@ -44,25 +44,25 @@ __device__ __forceinline__ bool may_be_visible(const float *R, const float *t, f
     return x1 > x0 && y1 > y0;
 }
 
-// One block of kProjThreads threads = the 256 pairs (chunk) of one view.  Phase 1: each thread
-// pre-tests two pairs (may_be_visible); the candidates are compacted in pair order.  Phase 2: the
-// candidates run the decision chain on dense lanes, kProjThreads at a time; the visible pairs of
-// each round take consecutive slots (ballot + warp counts; the round's first slot from one atomic
-// on the slot counter).  The block records each round's first slot and count (blk: at most two
-// rounds) and, per slot, the pair's position in the chunk (slane): the adjoint walks exactly these
-// slots.  Slots beyond the capacity record GS_ERR_CAPACITY and their pairs are dropped.
-constexpr int kProjThreads = 128;
-constexpr int kProjRounds = kChunk / kProjThreads;
-static_assert(kProjRounds == 2, "blk holds two slot ranges per chunk");
+// One block of kProjThreads threads = the 256 pairs (chunk) of one view, so that every chunk of a
+// single-view problem is resident at once.  Phase 1: each thread pre-tests kProjPre pairs
+// (may_be_visible); the candidates are compacted in pair order and take consecutive slots, reserved
+// by one atomic per block on the slot counter, issued before the decision chain so that the
+// chain's arithmetic hides its latency.  Phase 2: the candidates run the decision chain
+// kProjThreads at a time; a visible one writes its record into its slot, an invisible one leaves
+// its slot a hole.  The block records its first slot and candidate count (blk) and, per slot, the
+// pair's position in the chunk, flagged kSlotHole for a hole (slane).  Slots beyond the capacity
+// record GS_ERR_CAPACITY for a visible pair and drop it.
+constexpr int kProjThreads = 64;
+constexpr int kProjPre = kChunk / kProjThreads;   // pairs pre-tested per thread
 
 __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
     const int v = blockIdx.y;
     __shared__ ViewEntry s_ve;
     __shared__ float s_cam[19];   // R, t, fx, fy, cx, cy, the clamp limits, then wb2
     __shared__ uint8_t s_cl[kChunk];
-    __shared__ uint32_t s_wcnt[kProjRounds][kProjThreads / 32];
+    __shared__ uint32_t s_wcnt[kProjPre][kProjThreads / 32];
     __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_rng[2 * kProjRounds];
     if (threadIdx.x == 0) s_ve = a.views[v];
     if (threadIdx.x < 16) s_cam[threadIdx.x] = reinterpret_cast<const float *>(a.cams + v)[threadIdx.x];
     if (threadIdx.x == 32) {      // once per view and block, the same operations as the per-pair chain
@@ -77,14 +77,13 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
         const float wx = fabsf(c.fx) * (n0 + fabsf(limx) * n2), wy = fabsf(c.fy) * (n1 + fabsf(limy) * n2);
         s_cam[18] = wx * wx + wy * wy;
     }
-    if (threadIdx.x < 2 * kProjRounds) s_rng[threadIdx.x] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long base_i = (long long)blockIdx.x * kChunk;
     // phase 1: pairs base_i + k kProjThreads + thread
-    unsigned cmask[kProjRounds];
+    unsigned cmask[kProjPre];
 #pragma unroll
-    for (int k = 0; k < kProjRounds; ++k) {
+    for (int k = 0; k < kProjPre; ++k) {
         const int li = k * kProjThreads + threadIdx.x;
         const long long i = base_i + li;
         const bool in = i < s_ve.count;
@@ -97,10 +96,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
             cand = may_be_visible(s_cam, s_cam + 9, s_cam[12], s_cam[13], s_cam[14], s_cam[15], s_cam[18], a.itw,
                                   a.ith, a.Tx, a.Ty, a.near_plane, a.dil, a.sigmas, __ldg(mu), __ldg(mu + 1),
                                   __ldg(mu + 2), a.log_scales + 3 * gi);
-            if (!cand) {
-                a.touched[f] = 0u;
-                a.slot[f] = kNoSlot;
-            }
+            a.slot[f] = kNoSlot;   // a visible candidate overwrites it below
+            if (!cand) a.touched[f] = 0u;
         }
         cmask[k] = __ballot_sync(0xffffffffu, cand);
         if (lane == 0) s_wcnt[k][warp] = (uint32_t)__popc(cmask[k]);
@@ -108,14 +105,17 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
     __syncthreads();
     uint32_t ncand = 0;
 #pragma unroll
-    for (int k = 0; k < kProjRounds; ++k) {
+    for (int k = 0; k < kProjPre; ++k) {
         uint32_t pre = ncand + (uint32_t)__popc(cmask[k] & lanemask_lt());
         for (int w = 0; w < warp; ++w) pre += s_wcnt[k][w];
         if ((cmask[k] >> lane) & 1u) s_cl[pre] = (uint8_t)(k * kProjThreads + threadIdx.x);
 #pragma unroll
         for (int w = 0; w < kProjThreads / 32; ++w) ncand += s_wcnt[k][w];
     }
-    __syncthreads();   // s_cl complete; s_wcnt is reused below
+    __syncthreads();   // s_cl complete
+    // the candidates' slots: one atomic, whose result is needed only after the first round's chain
+    unsigned long long base_reg = 0ull;
+    if (threadIdx.x == 0 && ncand > 0) base_reg = atomicAdd(&a.st->num_visible, (unsigned long long)ncand);
     // phase 2: candidates r kProjThreads + thread through the decision chain
     const int rounds = (int)((ncand + kProjThreads - 1) / kProjThreads);
     for (int r = 0; r < rounds; ++r) {
@@ -128,62 +128,59 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
         SpecProj o;
         o.visible = false;
         o.x0 = o.x1 = o.y0 = o.y1 = 0;
+        float op = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
         if (act) {
             const float *mu = a.means + 3 * gi;
             const float *ls = a.log_scales + 3 * gi;
             const float4 q = __ldg(reinterpret_cast<const float4 *>(a.quats) + gi);
+            // the record's other inputs, in flight during the chain
+            op = __ldg(a.opacities + gi);
+            c0 = __ldg(a.colors + 3 * gi);
+            c1 = __ldg(a.colors + 3 * gi + 1);
+            c2 = __ldg(a.colors + 3 * gi + 2);
             o = spec_project(s_cam, s_cam + 9, s_cam[12], s_cam[13], s_cam[14], s_cam[15], s_cam[16], s_cam[17],
                              a.itw, a.ith, a.Tx, a.Ty, a.near_plane, a.dil, a.sigmas, __ldg(mu), __ldg(mu + 1),
                              __ldg(mu + 2), __ldg(ls), __ldg(ls + 1), __ldg(ls + 2), q.x, q.y, q.z, q.w);
         }
-        const unsigned vmask = __ballot_sync(0xffffffffu, o.visible);
-        if (lane == 0) s_wcnt[r][warp] = (uint32_t)__popc(vmask);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t tot = 0;
-#pragma unroll
-            for (int w = 0; w < kProjThreads / 32; ++w) tot += s_wcnt[r][w];
-            const unsigned long long b0 = tot ? atomicAdd(&a.st->num_visible, (unsigned long long)tot) : 0ull;
-            s_base = b0;
-            s_rng[2 * r] = (uint32_t)min(b0, (unsigned long long)a.vcap);
-            s_rng[2 * r + 1] = tot;
+        if (r == 0) {
+            if (threadIdx.x == 0) s_base = base_reg;
+            __syncthreads();
         }
-        __syncthreads();
-        unsigned long long slot = s_base + (unsigned long long)__popc(vmask & lanemask_lt());
-        for (int w = 0; w < warp; ++w) slot += s_wcnt[r][w];
-        if (o.visible && slot >= (unsigned long long)a.vcap) {
-            record_error(a.st, GS_ERR_CAPACITY, 11);
-            o.visible = false;
-        }
-        if (act) a.slot[f] = o.visible ? (uint32_t)slot : kNoSlot;
-        uint32_t cnt = 0;
-        if (o.visible) {
-            cnt = (uint32_t)((o.x1 - o.x0) * (o.y1 - o.y0));
-            a.slane[slot] = (uint8_t)li;
-            const float *col = a.colors + 3 * gi;
-            float4 *rec = a.proj + 3 * slot;
-            const float op = __ldg(a.opacities + gi);
-            // sigma beyond which alpha < alpha_min is certain (see gs_render.cu); +inf disables the cut
-            float cut = __int_as_float(0x7f800000);
-            if (a.alpha_min > 0.0f) {
-                if (op > 0.0f) cut = logf(op / a.alpha_min) + 1e-3f;
-                else if (op <= 0.0f) cut = -1.0f;
+        const unsigned long long slot = s_base + (unsigned long long)t;
+        if (act) {
+            if (slot < (unsigned long long)a.vcap) {
+                a.slane[slot] = (uint16_t)(li | (o.visible ? 0 : kSlotHole));   // the adjoint skips holes
+            } else if (o.visible) {
+                record_error(a.st, GS_ERR_CAPACITY, 11);
+                o.visible = false;
             }
-            rec[0] = make_float4(o.mx, o.my, o.A, o.B);
-            rec[1] = make_float4(o.C, op, o.z, o.rf);
-            rec[2] = make_float4(__ldg(col), __ldg(col + 1), __ldg(col + 2), cut);
+            uint32_t cnt = 0;
+            if (o.visible) {
+                cnt = (uint32_t)((o.x1 - o.x0) * (o.y1 - o.y0));
+                a.slot[f] = (uint32_t)slot;
+                float4 *rec = a.proj + 3 * slot;
+                // sigma beyond which alpha < alpha_min is certain (see gs_render.cu); +inf disables the cut
+                float cut = __int_as_float(0x7f800000);
+                if (a.alpha_min > 0.0f) {
+                    if (op > 0.0f) cut = logf(op / a.alpha_min) + 1e-3f;
+                    else if (op <= 0.0f) cut = -1.0f;
+                }
+                rec[0] = make_float4(o.mx, o.my, o.A, o.B);
+                rec[1] = make_float4(o.C, op, o.z, o.rf);
+                rec[2] = make_float4(c0, c1, c2, cut);
+            }
+            a.touched[f] = cnt;
         }
         if (a.tile_cnt && o.visible) {   // tile-bucket binning: one key per touched tile of this view
             uint32_t *row = a.tile_cnt + (size_t)v * a.Txi * a.Ty_i;
             for (int ty = o.y0; ty < o.y1; ++ty)
                 for (int tx = o.x0; tx < o.x1; ++tx) atomicAdd(row + ty * a.Txi + tx, 1u);
         }
-        if (act) a.touched[f] = cnt;
     }
     if (threadIdx.x == 0) {
         const long long ch = s_ve.chunk_off + blockIdx.x;
         if (base_i < s_ve.count && gs_guard(a.st, ch < a.chunks, 6))
-            a.blk[ch] = make_uint4(s_rng[0], s_rng[1], s_rng[2], s_rng[3]);
+            a.blk[ch] = make_uint4((uint32_t)min(base_reg, (unsigned long long)a.vcap), ncand, 0u, 0u);
     }
 }
 
@@ -227,17 +224,19 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_project_bwd(ProjBwdArgs a) 
     const long long ch = s_ve.chunk_off + blockIdx.x;
     if (threadIdx.x == 0) s_blk = gs_guard(a.st, ch < a.chunks, 3) ? a.blk[ch] : make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
-    // the chunk's visible pairs hold the slots [b0, b0 + n0) and [b1, b1 + n1) (beyond the capacity:
-    // dropped by the projection)
+    // the chunk's candidates hold the slots [b0, b0 + n0) (beyond the capacity: dropped by the
+    // projection); holes (candidates the decision chain culled) are flagged in their slot lane
     const unsigned long long vc = (unsigned long long)a.vcap;
-    const unsigned long long b0 = s_blk.x, b1 = s_blk.z;
+    const unsigned long long b0 = s_blk.x;
     const unsigned long long n0 = b0 < vc ? min((unsigned long long)s_blk.y, vc - b0) : 0ull;
-    const unsigned long long n1 = b1 < vc ? min((unsigned long long)s_blk.w, vc - b1) : 0ull;
     float pose[6] = {0, 0, 0, 0, 0, 0};
-    for (unsigned long long u = threadIdx.x; u < n0 + n1; u += kProjBwdThreads) {
-        const uint32_t sl = (uint32_t)(u < n0 ? b0 + u : b1 + (u - n0));
-        const long long i = (long long)blockIdx.x * kChunk + a.slane[sl];
-        if (gs_guard(a.st, i < s_ve.count && s_ve.pair_off + i < a.P && s_ve.gauss_begin + i < a.N, 2)) {
+    for (unsigned long long u = threadIdx.x; u < n0; u += kProjBwdThreads) {
+        const uint32_t sl = (uint32_t)(b0 + u);
+        const uint32_t lanev = a.slane[sl];
+        if (lanev & kSlotHole) continue;
+        const long long i = (long long)blockIdx.x * kChunk + (lanev & 0xffu);
+        if (!gs_guard(a.st, i < s_ve.count && s_ve.pair_off + i < a.P && s_ve.gauss_begin + i < a.N, 2)) continue;
+        {
             const long long gi = s_ve.gauss_begin + i;
             const float *R = s_cam, *t = s_cam + 9;
             const float fx = s_cam[12], fy = s_cam[13];

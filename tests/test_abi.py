@@ -69,13 +69,13 @@ def test_workspace_size_and_validation(lib):
     bad.append(neg)
     for b in bad:
         assert lib.gs_workspace_size(C.byref(b), C.byref(n)) == L.GS_ERR_INVALID_ARG
-    # a visible-pair capacity below the pair count shrinks the records, the 2-D gradients and the
-    # slot lanes (48 + 48 + 1 B per slot; each region is rounded up to 256 B)
+    # a slot capacity below the pair count shrinks the records, the 2-D gradients and the slot
+    # lanes (48 + 48 + 2 B per slot; each region is rounded up to 256 B)
     small = _problem()
     small.visible_capacity = 100_000
     m = C.c_size_t()
     assert lib.gs_workspace_size(C.byref(small), C.byref(m)) == 0
-    assert 0 <= n_full.value - m.value - 400_000 * 97 < 3 * 256
+    assert 0 <= n_full.value - m.value - 400_000 * 98 < 3 * 256
     pb = _problem(V=2)
     vc = np.array([10, 20], np.int64)
     vb = np.array([0, 500_000 - 5], np.int64)       # second view overruns the arrays
