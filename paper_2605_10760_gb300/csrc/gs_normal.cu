@@ -23,7 +23,9 @@
 // read-modify-write of d_depth.  A row's inputs are copied by cp.async into a per-warp ring of
 // shared-memory rows kNRing - 1 steps before the row is needed (each lane copies and later reads
 // only its own two columns), so every warp keeps several rows of loads in flight without holding
-// them in registers.  Values in FP32; the loss in FP32 per item and FP64 per CTA.
+// them in registers.  An item away from the image border (every row and column it reads inside,
+// every pixel it normalises off the border) runs a copy of the item loop without index clamps or
+// out-of-image selects.  Values in FP32; the loss in FP32 per item and FP64 per CTA.
 #include <algorithm>
 
 #include "gs_kernels.cuh"
@@ -84,10 +86,12 @@ __device__ __forceinline__ void nm_cp_wait() { asm volatile("cp.async.wait_group
 // row clamped into the image (the out-of-image values are replaced when the ring row is read).
 // One commit group per step; a step past the item's last row commits an empty group, so that
 // waiting for all but the kNRing - 1 newest groups always completes the step being consumed.
-template <bool EVEN>
+template <bool EVEN, bool INTERIOR>
 __device__ __forceinline__ void nm_issue_row(float (*ring)[64], const float *D, const float *Pr, const float *DD,
                                              const NormalCols &c, int HW, int W, int H, int y, int lane) {
-    const int yb = min(max(y + 1, 0), H - 1), yc = min(max(y, 0), H - 1), ya = min(max(y - 1, 0), H - 1);
+    // an interior item's rows y - 1 .. y + 1 are inside the image: no clamping
+    const int yb = INTERIOR ? y + 1 : min(max(y + 1, 0), H - 1), yc = INTERIOR ? y : min(max(y, 0), H - 1),
+              ya = INTERIOR ? y - 1 : min(max(y - 1, 0), H - 1);
     const float *src[kNPlanes] = {D + yb * W, Pr + yc * W, Pr + HW + yc * W, Pr + 2 * HW + yc * W, DD + ya * W};
 #pragma unroll
     for (int k = 0; k < kNPlanes; ++k) {
@@ -101,18 +105,161 @@ __device__ __forceinline__ void nm_issue_row(float (*ring)[64], const float *D, 
     }
 }
 
+// One (view, 16-row strip, 60-column block) item of a warp (lane's first column xa = x0 - 2 + 2 lane);
+// returns the loss of its own pixels.  INTERIOR: every row the item reads (y0 - 2 .. y0 + kNRows +
+// 1) and every column (x0 - 3 .. x0 + kNCols + 2) lies inside the image and every pixel it
+// normalises off the border, so no index is clamped and no value replaced.
+template <bool EVEN, bool INTERIOR>
+__device__ __forceinline__ float nm_run_item(const NormalArgs &a, float (*ring)[kNPlanes][64], int lane, int v,
+                                             int y0, int xa) {
+    using namespace fp2;
+    const int W = a.W, H = a.H, HW = a.H * a.W;
+    const float2 z2 = splat(0.0f);
+    const bool inner = lane >= 1 && lane <= kNCols / 2;
+    const bool own_a = inner && (INTERIOR || xa < W), own_b = inner && (INTERIOR || xa + 1 < W);
+    const gs_camera &cam = a.cams[v];
+    const float ifx = 1.0f / cam.fx, ify = 1.0f / cam.fy, cy = cam.cy;
+    const float r_m = nm_ray(xa - 1, cam.cx, ifx), r_a = nm_ray(xa, cam.cx, ifx), r_b = nm_ray(xa + 1, cam.cx, ifx),
+                r_p = nm_ray(xa + 2, cam.cx, ifx);
+    const float2 rxl = make_float2(r_m, r_a), rxc = make_float2(r_a, r_b), rxr = make_float2(r_b, r_p);
+    const bool colok_a = INTERIOR || (xa >= 1 && xa <= W - 2), colok_b = INTERIOR || (xa + 1 >= 1 && xa + 1 <= W - 2);
+    NormalCols c;
+    c.ina = INTERIOR || (unsigned)xa < (unsigned)W;
+    c.inb = INTERIOR || (unsigned)(xa + 1) < (unsigned)W;
+    if (INTERIOR) {
+        c.ia = xa;
+        c.ib = xa + 1;
+    } else if (EVEN) {   // xa is even: both columns or neither inside the image
+        c.ia = min(max(xa, 0), W - 2);
+        c.ib = c.ia + 1;
+    } else {
+        c.ia = min(max(xa, 0), W - 1);
+        c.ib = min(max(xa + 1, 0), W - 1);
+    }
+    const float *D = a.depth + (size_t)v * HW;
+    const float *Pr = a.prior + (size_t)v * 3 * HW;
+    float *DD = a.d_depth + (size_t)v * HW;
+    const int yend = min(y0 + kNRows, H);              // the rows y0 .. yend - 1 are this item's
+    const int nsteps = yend - y0 + 2;                  // rows y0 - 1 .. yend are normalised
+    // the first kNRing - 1 steps' inputs in flight, then rows y0 - 2 and y0 - 1 of the lane's
+    // columns (plain loads)
+#pragma unroll
+    for (int q = 0; q < kNRing - 1; ++q) {
+        if (q < nsteps) nm_issue_row<EVEN, INTERIOR>(ring[q], D, Pr, DD, c, HW, W, H, y0 - 1 + q, lane);
+        nm_cp_commit();
+    }
+    const float2 dm2 = nm_ld2<EVEN>(D + (INTERIOR ? y0 - 2 : min(max(y0 - 2, 0), H - 1)) * W, c);
+    const float2 dm1 = nm_ld2<EVEN>(D + (INTERIOR ? y0 - 1 : min(max(y0 - 1, 0), H - 1)) * W, c);
+    float2 d_up = nm_sel2(c.ina && (INTERIOR || y0 >= 2), c.inb && (INTERIOR || y0 >= 2), dm2, -1.0f);
+    float2 d_mid = nm_sel2(c.ina && (INTERIOR || y0 >= 1), c.inb && (INTERIOR || y0 >= 1), dm1, -1.0f);
+    float ry_up = nm_ray(y0 - 2, cy, ify), ry_mid = nm_ray(y0 - 1, cy, ify);
+    float2 gxp0 = z2, gxp1 = z2, gxp2 = z2;            // G_x of the row above the current one
+    float2 gyp0 = z2, gyp1 = z2, gyp2 = z2;            // G_y of the row above
+    float2 gyq0 = z2, gyq1 = z2, gyq2 = z2;            // G_y two rows above
+    float acc_item = 0.f;
+    for (int st = 0; st < nsteps; ++st) {
+        const int y = y0 - 1 + st;
+        // the inputs kNRing - 1 steps ahead go into the ring row the previous step read
+        const int ahead = st + kNRing - 1;
+        if (ahead < nsteps) nm_issue_row<EVEN, INTERIOR>(ring[ahead % kNRing], D, Pr, DD, c, HW, W, H, y0 - 1 + ahead, lane);
+        nm_cp_commit();
+        nm_cp_wait();                                  // this step's group has landed
+        const float(*rr)[64] = ring[st % kNRing];
+        const bool bin = INTERIOR || (unsigned)(y + 1) < (unsigned)H, cin = INTERIOR || (unsigned)y < (unsigned)H,
+                   ain = INTERIOR || (unsigned)(y - 1) < (unsigned)H;
+        const float2 d_dn = nm_sel2(c.ina && bin, c.inb && bin, *reinterpret_cast<const float2 *>(rr[0] + 2 * lane), -1.0f);
+        const float2 p0 = nm_sel2(c.ina && cin, c.inb && cin, *reinterpret_cast<const float2 *>(rr[1] + 2 * lane), 0.0f);
+        const float2 p1 = nm_sel2(c.ina && cin, c.inb && cin, *reinterpret_cast<const float2 *>(rr[2] + 2 * lane), 0.0f);
+        const float2 p2 = nm_sel2(c.ina && cin, c.inb && cin, *reinterpret_cast<const float2 *>(rr[3] + 2 * lane), 0.0f);
+        const float2 ddv = nm_sel2(c.ina && ain, c.inb && ain, *reinterpret_cast<const float2 *>(rr[4] + 2 * lane), 0.0f);
+        const float ry_dn = nm_ray(y + 1, cy, ify);
+        // the row's depths left and right of each column: the lane's other column, or the
+        // neighbouring lane's by one shuffle
+        const float2 d_l = make_float2(__shfl_up_sync(0xffffffffu, d_mid.y, 1), d_mid.x);
+        const float2 d_r = make_float2(d_mid.y, __shfl_down_sync(0xffffffffu, d_mid.x, 1));
+        const bool rowok = INTERIOR || (y >= 1 && y <= H - 2);
+        const bool ok_a = colok_a && rowok && nm_depth_ok(d_mid.x) && nm_depth_ok(d_up.x) && nm_depth_ok(d_dn.x) &&
+                          nm_depth_ok(d_l.x) && nm_depth_ok(d_r.x);
+        const bool ok_b = colok_b && rowok && nm_depth_ok(d_mid.y) && nm_depth_ok(d_up.y) && nm_depth_ok(d_dn.y) &&
+                          nm_depth_ok(d_l.y) && nm_depth_ok(d_r.y);
+        float2 gx0 = z2, gx1 = z2, gx2 = z2, gy0 = z2, gy1 = z2, gy2 = z2;
+        if (ok_a || ok_b) {
+            // neighbours in a row share the ray's y component, in a column its x component
+            const float2 dx_ = add(d_r, neg(d_l)), dy_ = add(d_dn, neg(d_up));
+            const float2 tx0 = add(mul(d_r, rxr), neg(mul(d_l, rxl))), tx1 = mul(dx_, splat(ry_mid)), tx2 = dx_;
+            const float2 ty0 = mul(dy_, rxc), ty1 = add(mul(d_dn, splat(ry_dn)), neg(mul(d_up, splat(ry_up)))),
+                         ty2 = dy_;
+            // u = t_y x t_x
+            const float2 u0 = add(mul(ty1, tx2), neg(mul(ty2, tx1)));
+            const float2 u1 = add(mul(ty2, tx0), neg(mul(ty0, tx2)));
+            const float2 u2 = add(mul(ty0, tx1), neg(mul(ty1, tx0)));
+            const float2 uu = fma(u0, u0, fma(u1, u1, mul(u2, u2)));
+            const bool va = ok_a && uu.x > 0.0f, vb = ok_b && uu.y > 0.0f;
+            // 1/|u| by the hardware reciprocal square root (a value, not a decision)
+            const float2 inu = make_float2(va ? rsqrtf(uu.x) : 0.f, vb ? rsqrtf(uu.y) : 0.f);
+            const float2 n0 = mul(u0, inu), n1 = mul(u1, inu), n2 = mul(u2, inu);
+            const float2 cc = add(splat(1.0f), neg(fma(n0, p0, fma(n1, p1, mul(n2, p2)))));
+            if (y >= y0 && y < yend)   // the own pixels of the item add their loss (selects: NaN-safe)
+                acc_item += (own_a && va ? fabsf(cc.x) : 0.f) + (own_b && vb ? fabsf(cc.y) : 0.f);
+            // -scale sign(c) weights the adjoint (sign(0) = 0)
+            const float2 kk = make_float2(!va ? 0.f : (cc.x > 0.f ? -a.scale : (cc.x < 0.f ? a.scale : 0.f)),
+                                          !vb ? 0.f : (cc.y > 0.f ? -a.scale : (cc.y < 0.f ? a.scale : 0.f)));
+            const float2 gn0 = mul(kk, p0), gn1 = mul(kk, p1), gn2 = mul(kk, p2);
+            const float2 pn = fma(n0, gn0, fma(n1, gn1, mul(n2, gn2)));
+            const float2 gu0 = mul(add(gn0, neg(mul(n0, pn))), inu);
+            const float2 gu1 = mul(add(gn1, neg(mul(n1, pn))), inu);
+            const float2 gu2 = mul(add(gn2, neg(mul(n2, pn))), inu);
+            // G_x = gu x t_y, G_y = t_x x gu; selects, not products with zero: an invalid
+            // pixel's tangents may hold NaN or inf
+            gx0 = nm_sel2(va, vb, add(mul(gu1, ty2), neg(mul(gu2, ty1))), 0.f);
+            gx1 = nm_sel2(va, vb, add(mul(gu2, ty0), neg(mul(gu0, ty2))), 0.f);
+            gx2 = nm_sel2(va, vb, add(mul(gu0, ty1), neg(mul(gu1, ty0))), 0.f);
+            gy0 = nm_sel2(va, vb, add(mul(tx1, gu2), neg(mul(tx2, gu1))), 0.f);
+            gy1 = nm_sel2(va, vb, add(mul(tx2, gu0), neg(mul(tx0, gu2))), 0.f);
+            gy2 = nm_sel2(va, vb, add(mul(tx0, gu1), neg(mul(tx1, gu0))), 0.f);
+        }
+        // the row above (y - 1) is complete: + G_x of each pixel's left neighbour (t_x there =
+        // P(q) - P(q - 2)), - G_x of its right one, + G_y of the pixel above it, - G_y of this row
+        const float2 l0 = make_float2(__shfl_up_sync(0xffffffffu, gxp0.y, 1), gxp0.x);
+        const float2 l1 = make_float2(__shfl_up_sync(0xffffffffu, gxp1.y, 1), gxp1.x);
+        const float2 l2 = make_float2(__shfl_up_sync(0xffffffffu, gxp2.y, 1), gxp2.x);
+        const float2 r0 = make_float2(gxp0.y, __shfl_down_sync(0xffffffffu, gxp0.x, 1));
+        const float2 r1 = make_float2(gxp1.y, __shfl_down_sync(0xffffffffu, gxp1.x, 1));
+        const float2 r2 = make_float2(gxp2.y, __shfl_down_sync(0xffffffffu, gxp2.x, 1));
+        if ((own_a || own_b) && y > y0 && y <= yend) {
+            const float2 dP0 = add(add(l0, neg(r0)), add(gyq0, neg(gy0)));
+            const float2 dP1 = add(add(l1, neg(r1)), add(gyq1, neg(gy1)));
+            const float2 dP2 = add(add(l2, neg(r2)), add(gyq2, neg(gy2)));
+            const float2 nd = add(ddv, fma(rxc, dP0, fma(splat(ry_up), dP1, dP2)));
+            float *row = DD + (y - 1) * W;
+            if (EVEN) {   // xa even and inside: both pixels inside
+                *reinterpret_cast<float2 *>(row + c.ia) = nd;
+            } else {
+                if (own_a) row[c.ia] = nd.x;
+                if (own_b) row[c.ib] = nd.y;
+            }
+        }
+        gyq0 = gyp0; gyq1 = gyp1; gyq2 = gyp2;
+        gyp0 = gy0; gyp1 = gy1; gyp2 = gy2;
+        gxp0 = gx0; gxp1 = gx1; gxp2 = gx2;
+        d_up = d_mid;
+        ry_up = ry_mid;
+        d_mid = d_dn;
+        ry_mid = ry_dn;
+    }
+    return acc_item;
+}
+
 template <bool EVEN>
 __global__ void __launch_bounds__(kNormalThreads, 2) k_normal(NormalArgs a) {
-    using namespace fp2;
     __shared__ __align__(16) float s_ring[kNormalThreads / 32][kNRing][kNPlanes][64];
     const int lane = threadIdx.x & 31;
     float (*ring)[kNPlanes][64] = s_ring[threadIdx.x >> 5];
-    const int W = a.W, H = a.H, HW = a.H * a.W;      // the launcher checks 3 H W < 2^31
+    const int W = a.W, H = a.H;                        // the launcher checks 3 H W < 2^31
     const int cblocks = (W + kNCols - 1) / kNCols, strips = (H + kNRows - 1) / kNRows;
     const int per_view = cblocks * strips;
     const long long items = (long long)a.V * per_view;
     const long long nwarps = (long long)gridDim.x * (kNormalThreads / 32);
-    const float2 z2 = splat(0.0f);
     double acc = 0.0;
     for (long long item = (long long)blockIdx.x * (kNormalThreads / 32) + (threadIdx.x >> 5); item < items;
          item += nwarps) {
@@ -120,136 +267,10 @@ __global__ void __launch_bounds__(kNormalThreads, 2) k_normal(NormalArgs a) {
         const int t = (int)(item - (long long)v * per_view);
         const int sr = t / cblocks;
         const int y0 = sr * kNRows, xa = (t - sr * cblocks) * kNCols - 2 + 2 * lane;   // the lane's first column
-        const bool inner = lane >= 1 && lane <= kNCols / 2;
-        const bool own_a = inner && xa < W, own_b = inner && xa + 1 < W;
-        const gs_camera &cam = a.cams[v];
-        const float ifx = 1.0f / cam.fx, ify = 1.0f / cam.fy, cy = cam.cy;
-        const float r_m = nm_ray(xa - 1, cam.cx, ifx), r_a = nm_ray(xa, cam.cx, ifx), r_b = nm_ray(xa + 1, cam.cx, ifx),
-                    r_p = nm_ray(xa + 2, cam.cx, ifx);
-        const float2 rxl = make_float2(r_m, r_a), rxc = make_float2(r_a, r_b), rxr = make_float2(r_b, r_p);
-        const bool colok_a = xa >= 1 && xa <= W - 2, colok_b = xa + 1 >= 1 && xa + 1 <= W - 2;
-        NormalCols c;
-        c.ina = (unsigned)xa < (unsigned)W;
-        c.inb = (unsigned)(xa + 1) < (unsigned)W;
-        if (EVEN) {   // xa is even: both columns or neither inside the image
-            c.ia = min(max(xa, 0), W - 2);
-            c.ib = c.ia + 1;
-        } else {
-            c.ia = min(max(xa, 0), W - 1);
-            c.ib = min(max(xa + 1, 0), W - 1);
-        }
-        const float *D = a.depth + (size_t)v * HW;
-        const float *Pr = a.prior + (size_t)v * 3 * HW;
-        float *DD = a.d_depth + (size_t)v * HW;
-        const int yend = min(y0 + kNRows, H);              // the rows y0 .. yend - 1 are this item's
-        const int nsteps = yend - y0 + 2;                  // rows y0 - 1 .. yend are normalised
-        // the first kNRing - 1 steps' inputs in flight, then rows y0 - 2 and y0 - 1 of the lane's
-        // columns (plain loads)
-#pragma unroll
-        for (int q = 0; q < kNRing - 1; ++q) {
-            if (q < nsteps) nm_issue_row<EVEN>(ring[q], D, Pr, DD, c, HW, W, H, y0 - 1 + q, lane);
-            nm_cp_commit();
-        }
-        const float2 dm2 = nm_ld2<EVEN>(D + min(max(y0 - 2, 0), H - 1) * W, c);
-        const float2 dm1 = nm_ld2<EVEN>(D + min(max(y0 - 1, 0), H - 1) * W, c);
-        float2 d_up = nm_sel2(c.ina && y0 >= 2, c.inb && y0 >= 2, dm2, -1.0f);
-        float2 d_mid = nm_sel2(c.ina && y0 >= 1, c.inb && y0 >= 1, dm1, -1.0f);
-        float ry_up = nm_ray(y0 - 2, cy, ify), ry_mid = nm_ray(y0 - 1, cy, ify);
-        float2 gxp0 = z2, gxp1 = z2, gxp2 = z2;            // G_x of the row above the current one
-        float2 gyp0 = z2, gyp1 = z2, gyp2 = z2;            // G_y of the row above
-        float2 gyq0 = z2, gyq1 = z2, gyq2 = z2;            // G_y two rows above
-        float acc_item = 0.f;
-        for (int st = 0; st < nsteps; ++st) {
-            const int y = y0 - 1 + st;
-            // the inputs kNRing - 1 steps ahead go into the ring row the previous step read
-            const int ahead = st + kNRing - 1;
-            if (ahead < nsteps) nm_issue_row<EVEN>(ring[ahead % kNRing], D, Pr, DD, c, HW, W, H, y0 - 1 + ahead, lane);
-            nm_cp_commit();
-            nm_cp_wait();                                  // this step's group has landed
-            const float(*rr)[64] = ring[st % kNRing];
-            const bool bin = (unsigned)(y + 1) < (unsigned)H, cin = (unsigned)y < (unsigned)H,
-                       ain = (unsigned)(y - 1) < (unsigned)H;
-            const float2 d_dn = nm_sel2(c.ina && bin, c.inb && bin, *reinterpret_cast<const float2 *>(rr[0] + 2 * lane), -1.0f);
-            const float2 p0 = nm_sel2(c.ina && cin, c.inb && cin, *reinterpret_cast<const float2 *>(rr[1] + 2 * lane), 0.0f);
-            const float2 p1 = nm_sel2(c.ina && cin, c.inb && cin, *reinterpret_cast<const float2 *>(rr[2] + 2 * lane), 0.0f);
-            const float2 p2 = nm_sel2(c.ina && cin, c.inb && cin, *reinterpret_cast<const float2 *>(rr[3] + 2 * lane), 0.0f);
-            const float2 ddv = nm_sel2(c.ina && ain, c.inb && ain, *reinterpret_cast<const float2 *>(rr[4] + 2 * lane), 0.0f);
-            const float ry_dn = nm_ray(y + 1, cy, ify);
-            // the row's depths left and right of each column: the lane's other column, or the
-            // neighbouring lane's by one shuffle
-            const float2 d_l = make_float2(__shfl_up_sync(0xffffffffu, d_mid.y, 1), d_mid.x);
-            const float2 d_r = make_float2(d_mid.y, __shfl_down_sync(0xffffffffu, d_mid.x, 1));
-            const bool rowok = y >= 1 && y <= H - 2;
-            const bool ok_a = colok_a && rowok && nm_depth_ok(d_mid.x) && nm_depth_ok(d_up.x) && nm_depth_ok(d_dn.x) &&
-                              nm_depth_ok(d_l.x) && nm_depth_ok(d_r.x);
-            const bool ok_b = colok_b && rowok && nm_depth_ok(d_mid.y) && nm_depth_ok(d_up.y) && nm_depth_ok(d_dn.y) &&
-                              nm_depth_ok(d_l.y) && nm_depth_ok(d_r.y);
-            float2 gx0 = z2, gx1 = z2, gx2 = z2, gy0 = z2, gy1 = z2, gy2 = z2;
-            if (ok_a || ok_b) {
-                // neighbours in a row share the ray's y component, in a column its x component
-                const float2 dx_ = add(d_r, neg(d_l)), dy_ = add(d_dn, neg(d_up));
-                const float2 tx0 = add(mul(d_r, rxr), neg(mul(d_l, rxl))), tx1 = mul(dx_, splat(ry_mid)), tx2 = dx_;
-                const float2 ty0 = mul(dy_, rxc), ty1 = add(mul(d_dn, splat(ry_dn)), neg(mul(d_up, splat(ry_up)))),
-                             ty2 = dy_;
-                // u = t_y x t_x
-                const float2 u0 = add(mul(ty1, tx2), neg(mul(ty2, tx1)));
-                const float2 u1 = add(mul(ty2, tx0), neg(mul(ty0, tx2)));
-                const float2 u2 = add(mul(ty0, tx1), neg(mul(ty1, tx0)));
-                const float2 uu = fma(u0, u0, fma(u1, u1, mul(u2, u2)));
-                const bool va = ok_a && uu.x > 0.0f, vb = ok_b && uu.y > 0.0f;
-                // 1/|u| by the hardware reciprocal square root (a value, not a decision)
-                const float2 inu = make_float2(va ? rsqrtf(uu.x) : 0.f, vb ? rsqrtf(uu.y) : 0.f);
-                const float2 n0 = mul(u0, inu), n1 = mul(u1, inu), n2 = mul(u2, inu);
-                const float2 cc = add(splat(1.0f), neg(fma(n0, p0, fma(n1, p1, mul(n2, p2)))));
-                if (y >= y0 && y < yend)   // the own pixels of the item add their loss (selects: NaN-safe)
-                    acc_item += (own_a && va ? fabsf(cc.x) : 0.f) + (own_b && vb ? fabsf(cc.y) : 0.f);
-                // -scale sign(c) weights the adjoint (sign(0) = 0)
-                const float2 kk = make_float2(!va ? 0.f : (cc.x > 0.f ? -a.scale : (cc.x < 0.f ? a.scale : 0.f)),
-                                              !vb ? 0.f : (cc.y > 0.f ? -a.scale : (cc.y < 0.f ? a.scale : 0.f)));
-                const float2 gn0 = mul(kk, p0), gn1 = mul(kk, p1), gn2 = mul(kk, p2);
-                const float2 pn = fma(n0, gn0, fma(n1, gn1, mul(n2, gn2)));
-                const float2 gu0 = mul(add(gn0, neg(mul(n0, pn))), inu);
-                const float2 gu1 = mul(add(gn1, neg(mul(n1, pn))), inu);
-                const float2 gu2 = mul(add(gn2, neg(mul(n2, pn))), inu);
-                // G_x = gu x t_y, G_y = t_x x gu; selects, not products with zero: an invalid
-                // pixel's tangents may hold NaN or inf
-                gx0 = nm_sel2(va, vb, add(mul(gu1, ty2), neg(mul(gu2, ty1))), 0.f);
-                gx1 = nm_sel2(va, vb, add(mul(gu2, ty0), neg(mul(gu0, ty2))), 0.f);
-                gx2 = nm_sel2(va, vb, add(mul(gu0, ty1), neg(mul(gu1, ty0))), 0.f);
-                gy0 = nm_sel2(va, vb, add(mul(tx1, gu2), neg(mul(tx2, gu1))), 0.f);
-                gy1 = nm_sel2(va, vb, add(mul(tx2, gu0), neg(mul(tx0, gu2))), 0.f);
-                gy2 = nm_sel2(va, vb, add(mul(tx0, gu1), neg(mul(tx1, gu0))), 0.f);
-            }
-            // the row above (y - 1) is complete: + G_x of each pixel's left neighbour (t_x there =
-            // P(q) - P(q - 2)), - G_x of its right one, + G_y of the pixel above it, - G_y of this row
-            const float2 l0 = make_float2(__shfl_up_sync(0xffffffffu, gxp0.y, 1), gxp0.x);
-            const float2 l1 = make_float2(__shfl_up_sync(0xffffffffu, gxp1.y, 1), gxp1.x);
-            const float2 l2 = make_float2(__shfl_up_sync(0xffffffffu, gxp2.y, 1), gxp2.x);
-            const float2 r0 = make_float2(gxp0.y, __shfl_down_sync(0xffffffffu, gxp0.x, 1));
-            const float2 r1 = make_float2(gxp1.y, __shfl_down_sync(0xffffffffu, gxp1.x, 1));
-            const float2 r2 = make_float2(gxp2.y, __shfl_down_sync(0xffffffffu, gxp2.x, 1));
-            if ((own_a || own_b) && y > y0 && y <= yend) {
-                const float2 dP0 = add(add(l0, neg(r0)), add(gyq0, neg(gy0)));
-                const float2 dP1 = add(add(l1, neg(r1)), add(gyq1, neg(gy1)));
-                const float2 dP2 = add(add(l2, neg(r2)), add(gyq2, neg(gy2)));
-                const float2 nd = add(ddv, fma(rxc, dP0, fma(splat(ry_up), dP1, dP2)));
-                float *row = DD + (y - 1) * W;
-                if (EVEN) {   // xa even and inside: both pixels inside
-                    *reinterpret_cast<float2 *>(row + c.ia) = nd;
-                } else {
-                    if (own_a) row[c.ia] = nd.x;
-                    if (own_b) row[c.ib] = nd.y;
-                }
-            }
-            gyq0 = gyp0; gyq1 = gyp1; gyq2 = gyp2;
-            gyp0 = gy0; gyp1 = gy1; gyp2 = gy2;
-            gxp0 = gx0; gxp1 = gx1; gxp2 = gx2;
-            d_up = d_mid;
-            ry_up = ry_mid;
-            d_mid = d_dn;
-            ry_mid = ry_dn;
-        }
-        acc += (double)acc_item;
+        const int x0 = xa + 2 - 2 * lane;
+        const bool interior = x0 >= 3 && x0 + kNCols + 2 <= W - 1 && y0 >= 2 && y0 + kNRows + 1 <= H - 1;
+        acc += (double)(interior ? nm_run_item<EVEN, true>(a, ring, lane, v, y0, xa)
+                                 : nm_run_item<EVEN, false>(a, ring, lane, v, y0, xa));
     }
     nm_block_add(acc * (double)a.scale, a.loss);
 }
