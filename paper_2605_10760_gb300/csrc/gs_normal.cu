@@ -25,7 +25,8 @@
 // only its own two columns), so every warp keeps several rows of loads in flight without holding
 // them in registers.  An item away from the image border (every row and column it reads inside,
 // every pixel it normalises off the border) runs a copy of the item loop without index clamps or
-// out-of-image selects.  Values in FP32; the loss in FP32 per item and FP64 per CTA.
+// out-of-image selects.  Each depth's validity is tested once, when its row arrives, and rolled
+// down with it.  Values in FP32; the loss in FP32 per item and FP64 per CTA.
 #include <algorithm>
 
 #include "gs_kernels.cuh"
@@ -39,6 +40,9 @@ constexpr int kNRing = 4;            // rows of inputs per warp in shared memory
 constexpr int kNPlanes = 5;          // per ring row: depth below, three prior components, d_depth above
 
 __device__ __forceinline__ bool nm_depth_ok(float d) { return d > 0.0f && d < __int_as_float(0x7f800000); }
+__device__ __forceinline__ uint32_t nm_ok2(float2 d) {
+    return (nm_depth_ok(d.x) ? 1u : 0u) | (nm_depth_ok(d.y) ? 2u : 0u);
+}
 
 // the pixel ray of column x / row y (one expression for the normal and for its adjoint)
 __device__ __forceinline__ float nm_ray(int x, float c, float inv_f) { return ((float)x + 0.5f - c) * inv_f; }
@@ -152,6 +156,9 @@ __device__ __forceinline__ float nm_run_item(const NormalArgs &a, float (*ring)[
     const float2 dm1 = nm_ld2<EVEN>(D + (INTERIOR ? y0 - 1 : min(max(y0 - 1, 0), H - 1)) * W, c);
     float2 d_up = nm_sel2(c.ina && (INTERIOR || y0 >= 2), c.inb && (INTERIOR || y0 >= 2), dm2, -1.0f);
     float2 d_mid = nm_sel2(c.ina && (INTERIOR || y0 >= 1), c.inb && (INTERIOR || y0 >= 1), dm1, -1.0f);
+    // which of the lane's two depths are usable (bit 0: first column, bit 1: second), per row,
+    // rolled down with the depths
+    uint32_t ok_up = nm_ok2(d_up), ok_mid = nm_ok2(d_mid);
     float ry_up = nm_ray(y0 - 2, cy, ify), ry_mid = nm_ray(y0 - 1, cy, ify);
     float2 gxp0 = z2, gxp1 = z2, gxp2 = z2;            // G_x of the row above the current one
     float2 gyp0 = z2, gyp1 = z2, gyp2 = z2;            // G_y of the row above
@@ -178,10 +185,13 @@ __device__ __forceinline__ float nm_run_item(const NormalArgs &a, float (*ring)[
         const float2 d_l = make_float2(__shfl_up_sync(0xffffffffu, d_mid.y, 1), d_mid.x);
         const float2 d_r = make_float2(d_mid.y, __shfl_down_sync(0xffffffffu, d_mid.x, 1));
         const bool rowok = INTERIOR || (y >= 1 && y <= H - 2);
-        const bool ok_a = colok_a && rowok && nm_depth_ok(d_mid.x) && nm_depth_ok(d_up.x) && nm_depth_ok(d_dn.x) &&
-                          nm_depth_ok(d_l.x) && nm_depth_ok(d_r.x);
-        const bool ok_b = colok_b && rowok && nm_depth_ok(d_mid.y) && nm_depth_ok(d_up.y) && nm_depth_ok(d_dn.y) &&
-                          nm_depth_ok(d_l.y) && nm_depth_ok(d_r.y);
+        // the flags of d_l and d_r: the lane's other column, or the neighbouring lane's flag (the
+        // same shuffles as the depths, so each flag belongs to the depth it stands for)
+        const uint32_t ok_dn = nm_ok2(d_dn);
+        const uint32_t ok_l = ((__shfl_up_sync(0xffffffffu, ok_mid, 1) >> 1) & 1u) | ((ok_mid & 1u) << 1);
+        const uint32_t ok_r = ((ok_mid >> 1) & 1u) | ((__shfl_down_sync(0xffffffffu, ok_mid, 1) & 1u) << 1);
+        const uint32_t ok5 = ok_mid & ok_up & ok_dn & ok_l & ok_r;
+        const bool ok_a = colok_a && rowok && (ok5 & 1u), ok_b = colok_b && rowok && (ok5 & 2u);
         float2 gx0 = z2, gx1 = z2, gx2 = z2, gy0 = z2, gy1 = z2, gy2 = z2;
         if (ok_a || ok_b) {
             // neighbours in a row share the ray's y component, in a column its x component
@@ -243,8 +253,10 @@ __device__ __forceinline__ float nm_run_item(const NormalArgs &a, float (*ring)[
         gyp0 = gy0; gyp1 = gy1; gyp2 = gy2;
         gxp0 = gx0; gxp1 = gx1; gxp2 = gx2;
         d_up = d_mid;
+        ok_up = ok_mid;
         ry_up = ry_mid;
         d_mid = d_dn;
+        ok_mid = ok_dn;
         ry_mid = ry_dn;
     }
     return acc_item;
