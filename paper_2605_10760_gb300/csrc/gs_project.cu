@@ -3,11 +3,11 @@
 // Forward: the FP32 decision chain of gs_internal.cuh, grid (chunk, view), a pre-test per pair and
 // the chain on the block's compacted candidates.
 // Backward: per block, one thread per slot of the forward block's candidates (holes, the slots of
-// candidates the chain found invisible, flagged and skipped); the chain rule through the same projection in FP32 value arithmetic, accumulating
-// dL/d(mean, log-scale, quaternion, opacity, colour) with atomics (several views of one scene add
-// into the same Gaussian; a reduction is issued without waiting for a result, which also makes it
-// cheaper than a load and a store where no two views share a Gaussian) and the per-view SE(3) pose
-// gradient as one partial sum per block.
+// candidates the chain found invisible, flagged and skipped); the chain rule through the same
+// projection in FP32 value arithmetic, accumulating dL/d(mean, log-scale, quaternion, opacity,
+// colour) with atomics (several views of one scene add into the same Gaussian; a reduction is
+// issued without waiting for a result, which also makes it cheaper than a load and a store where
+// no two views share a Gaussian) and the per-view SE(3) pose gradient as one partial sum per block.
 #include "gs_kernels.cuh"
 
 namespace gs {
