@@ -57,10 +57,12 @@ struct ScanShared {
 // the thread's counts (threads in order).  Block scan of the per-thread sums; warp 0 publishes the
 // partition total, looks back over the predecessors (a warp reads 32 at a time, the nearest
 // inclusive word ends it; bounded spins) and publishes the inclusive prefix; the last partition
-// writes K and checks the capacity.  sh.prefix holds the partition's prefix on return.
-template <int THREADS>
+// writes K and checks the capacity.  Every thread runs `overlap` (work that needs no prefix) before
+// the closing barrier, warp 0 after its look-back.  sh.prefix holds the partition's prefix on
+// return.
+template <int THREADS, class Overlap>
 __device__ unsigned long long scan_partition(const BinArgs &a, ScanShared<THREADS> &sh, long long part,
-                                             long long nparts, unsigned long long tsum) {
+                                             long long nparts, unsigned long long tsum, Overlap &&overlap) {
     static_assert(THREADS / 32 <= 32, "warp 0 scans the warp sums");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long incl = tsum;
@@ -128,6 +130,7 @@ __device__ unsigned long long scan_partition(const BinArgs &a, ScanShared<THREAD
             }
         }
     }
+    overlap();   // work that needs no prefix: warps 1.. while warp 0 looks back, warp 0 after it
     __syncthreads();
     return sh.prefix + sh.wsum[warp] + (incl - tsum);
 }
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(BinArgs a) {
         unsigned long long tsum = 0;
 #pragma unroll
         for (int k = 0; k < kScanIPT; ++k) tsum += x[k];
-        unsigned long long run = scan_partition<kScanThreads>(a, sh, part, nparts, tsum);
+        unsigned long long run = scan_partition<kScanThreads>(a, sh, part, nparts, tsum, [] {});
         uint32_t y[kScanIPT];
 #pragma unroll
         for (int k = 0; k < kScanIPT; ++k) {
@@ -242,54 +245,58 @@ __global__ void __launch_bounds__(kEmitThreads) k_scan_emit(BinArgs a) {
         if (part >= nparts) break;
         const long long pbase = part * kScanTile;
         const long long base = pbase + (long long)threadIdx.x * kEmitIPT;
-        // (1) scan
-        {
-            uint32_t x[kEmitIPT];
-            scan_load<kEmitIPT>(a, base, x);
-            unsigned long long tsum = 0;
-#pragma unroll
-            for (int k = 0; k < kEmitIPT; ++k) tsum += x[k];
-            unsigned long long run = scan_partition<kEmitThreads>(a, sh, part, nparts, tsum);
-            uint32_t y[kEmitIPT];
-#pragma unroll
-            for (int k = 0; k < kEmitIPT; ++k) {
-                run += x[k];
-                y[k] = sat32(run);
-                es.inc[threadIdx.x * kEmitIPT + k] = y[k];
-            }
-            scan_store<kEmitIPT>(a, base, y);
-        }
-        const uint32_t pstart = sat32(sh.prefix);
         const int np = (int)min((long long)kScanTile, a.P - pbase);   // pairs in this partition
+        // (1) scan; the counts also go to shared memory for (2)
+        uint32_t x[kEmitIPT];
+        scan_load<kEmitIPT>(a, base, x);
+        unsigned long long tsum = 0;
+#pragma unroll
+        for (int k = 0; k < kEmitIPT; ++k) {
+            tsum += x[k];
+            es.inc[threadIdx.x * kEmitIPT + k] = x[k];
+        }
+        // (2) per pair with keys, its rectangle and depth bits: needs no prefix, so it runs while
+        // warp 0 looks back over the predecessor partitions
+        auto rects = [&] {
+#pragma unroll
+            for (int j = 0; j < kEmitIPT; ++j) {
+                const int li = j * kEmitThreads + threadIdx.x;
+                if (li >= np) break;
+                const uint32_t cnt = es.inc[li];
+                if (cnt == 0) continue;
+                const long long f = pbase + li;
+                const uint32_t sl = a.slot[f];      // a pair with keys is visible and holds a slot
+                if (sl >= (unsigned long long)a.vcap) {   // only after an earlier recorded failure
+                    record_error(a.st, GS_ERR_DEVICE_FAULT, 7);
+                    continue;
+                }
+                const float4 r0 = a.proj[3 * (size_t)sl], r1 = a.proj[3 * (size_t)sl + 1];
+                int x0, x1, y0, y1;
+                spec_rect(r0.x, r0.y, r1.w, a.itw, a.ith, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
+                const int v = view_of_pair(a.views, a.V, f);
+                if ((uint32_t)((x1 - x0) * (y1 - y0)) != cnt || x1 <= x0) record_error(a.st, GS_ERR_DEVICE_FAULT, 3);
+                es.g0[li] = (uint32_t)((unsigned long long)v * a.Tx * a.Ty + (unsigned long long)(y0 * a.Tx + x0));
+                es.wr[li] = (uint32_t)max(x1 - x0, 1);
+                es.z[li] = __float_as_uint(r1.z);
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                a.g2d[3 * (size_t)sl] = z4;
+                a.g2d[3 * (size_t)sl + 1] = z4;
+                a.g2d[3 * (size_t)sl + 2] = z4;
+            }
+        };
+        unsigned long long run = scan_partition<kEmitThreads>(a, sh, part, nparts, tsum, rects);
+        // the counts in shared memory become inclusive sums (every read of them in (2) is done)
+        uint32_t y[kEmitIPT];
+#pragma unroll
+        for (int k = 0; k < kEmitIPT; ++k) {
+            run += x[k];
+            y[k] = sat32(run);
+            es.inc[threadIdx.x * kEmitIPT + k] = y[k];
+        }
+        scan_store<kEmitIPT>(a, base, y);
+        const uint32_t pstart = sat32(sh.prefix);
         __syncthreads();
         const uint32_t pend = es.inc[np - 1];
-        // (2) per pair: rectangle and depth bits
-#pragma unroll
-        for (int j = 0; j < kEmitIPT; ++j) {
-            const int li = j * kEmitThreads + threadIdx.x;
-            if (li >= np) break;
-            const uint32_t b1 = es.inc[li], b0 = li ? es.inc[li - 1] : pstart;
-            if (b1 == b0) continue;
-            const long long f = pbase + li;
-            const uint32_t sl = a.slot[f];      // a pair with keys is visible and holds a slot
-            if (sl >= (unsigned long long)a.vcap) {   // only after an earlier recorded failure
-                record_error(a.st, GS_ERR_DEVICE_FAULT, 7);
-                continue;
-            }
-            const float4 r0 = a.proj[3 * (size_t)sl], r1 = a.proj[3 * (size_t)sl + 1];
-            int x0, x1, y0, y1;
-            spec_rect(r0.x, r0.y, r1.w, a.itw, a.ith, (float)a.Tx, (float)a.Ty, x0, x1, y0, y1);
-            const int v = view_of_pair(a.views, a.V, f);
-            if ((uint32_t)((x1 - x0) * (y1 - y0)) != b1 - b0 || x1 <= x0) record_error(a.st, GS_ERR_DEVICE_FAULT, 3);
-            es.g0[li] = (uint32_t)((unsigned long long)v * a.Tx * a.Ty + (unsigned long long)(y0 * a.Tx + x0));
-            es.wr[li] = (uint32_t)max(x1 - x0, 1);
-            es.z[li] = __float_as_uint(r1.z);
-            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            a.g2d[3 * (size_t)sl] = z4;
-            a.g2d[3 * (size_t)sl + 1] = z4;
-            a.g2d[3 * (size_t)sl + 2] = z4;
-        }
-        __syncthreads();
         // (3) per key, up to the capacity (< 2^30, so the counter cannot wrap even when the sums
         // saturated); keys at or beyond it are neither written nor counted
         const uint32_t kend = (uint32_t)min((unsigned long long)pend, cap);
