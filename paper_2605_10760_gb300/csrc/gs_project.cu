@@ -391,31 +391,40 @@ void launch_project_bwd(const Layout &L, const ProjBwdArgs &a, cudaStream_t s) {
     count_launches(1);
 }
 
-// deterministic per-view sum of the pose partials: one 256-thread block per (view, component),
-// fixed per-thread strides and a fixed reduction tree
+// deterministic per-view sum of the pose partials: one 256-thread block per view, each thread
+// reading its chunks' 8-float partials as two 16-byte loads; fixed per-thread strides and a fixed
+// reduction tree per component
 __global__ void __launch_bounds__(256) k_pose_reduce(const ViewEntry *views, const float *pose_part, float *out,
                                                      long long total_chunks, DevStatus *st) {
-    __shared__ float s_w[8];
-    const int v = blockIdx.x, k = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ float s_w[8][6];
+    const int v = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const ViewEntry ve = views[v];
     const long long chunks = (ve.count + kChunk - 1) / kChunk;
-    float acc = 0.f;
-    for (long long c = threadIdx.x; c < chunks; c += 256)
-        if (gs_guard(st, ve.chunk_off + c < total_chunks, 4)) acc += pose_part[(ve.chunk_off + c) * 8 + k];
-    acc = warp_sum(acc);
-    if (lane == 0) s_w[warp] = acc;
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float4 *part4 = reinterpret_cast<const float4 *>(pose_part);
+    for (long long c = threadIdx.x; c < chunks; c += 256) {
+        if (gs_guard(st, ve.chunk_off + c < total_chunks, 4)) {
+            const float4 p0 = part4[2 * (ve.chunk_off + c)], p1 = part4[2 * (ve.chunk_off + c) + 1];
+            acc[0] += p0.x; acc[1] += p0.y; acc[2] += p0.z; acc[3] += p0.w; acc[4] += p1.x; acc[5] += p1.y;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float r = warp_sum(acc[k]);
+        if (lane == 0) s_w[warp][k] = r;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 6) {
         float r = 0.f;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) r += s_w[w];
-        out[6 * v + k] = r;
+        for (int w = 0; w < 8; ++w) r += s_w[w][threadIdx.x];
+        out[6 * v + threadIdx.x] = r;
     }
 }
 
 void launch_pose_reduce(const Layout &L, const ViewEntry *views, const float *part, float *out, DevStatus *st,
                         cudaStream_t s) {
-    k_pose_reduce<<<dim3(L.V, 6), 256, 0, s>>>(views, part, out, std::max<long long>(L.chunks_total, 1), st);
+    k_pose_reduce<<<L.V, 256, 0, s>>>(views, part, out, std::max<long long>(L.chunks_total, 1), st);
     count_launches(1);
 }
 
