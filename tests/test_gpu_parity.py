@@ -334,3 +334,36 @@ def test_autograd_function_matches_direct_calls(R):
     for leaf, k in zip(leaves, ("means", "log_scales", "quats", "opacities", "colors")):
         assert rel_l2(leaf.grad.cpu().numpy(), orc["bwd"][k]) <= TOL_GRAD, k
     assert rel_l2(pose.grad.cpu().numpy(), orc["bwd"]["pose"]) <= TOL_GRAD
+
+
+def test_repeated_launches_need_no_clearing(R):
+    """The compositing launches return their work counters to zero themselves (no clearing between
+    calls): forwards repeated on one binning give the same images, last indices and pair counts
+    every time; a second backward walks the same pairs and adds the same 2-D gradients again (they
+    accumulate until the next binning zeroes them)."""
+    wl = S.workload("cloud10k", scale=0.3)
+    pb, g = gpu_problem(wl)
+    pb.project(g)
+    pb.bin_sort()
+    imgs, fwd_pairs = [], []
+    for _ in range(3):
+        img = pb.render_fwd()
+        torch.cuda.synchronize()
+        imgs.append({k: v.cpu().numpy().copy() for k, v in img.items()})
+        fwd_pairs.append(pb.stats()["fwd_pairs"])
+    for i in (1, 2):
+        for k in imgs[0]:
+            np.testing.assert_array_equal(imgs[i][k], imgs[0][k])
+    assert fwd_pairs[0] == fwd_pairs[1] == fwd_pairs[2] > 0
+    d_rgb, d_depth, d_alpha = upstream(wl, pb.V, 7)
+    dev = lambda a: torch.from_numpy(a).cuda()
+    g2d, bwd_pairs = [], []
+    for _ in range(2):
+        pb.render_bwd(g, img, dev(d_rgb), dev(d_depth), dev(d_alpha))
+        torch.cuda.synchronize()
+        g2d.append(pb.workspace()["grad2d"].cpu().numpy())
+        bwd_pairs.append(pb.stats()["bwd_pairs"])
+    assert bwd_pairs[0] == bwd_pairs[1] > 0
+    np.testing.assert_allclose(g2d[1], 2.0 * g2d[0], rtol=1e-5, atol=1e-9)
+    rc, _ = pb.check_status()
+    assert rc == 0
