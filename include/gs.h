@@ -180,8 +180,10 @@ typedef struct gs_ws_view {
 /* Statistics of the last calls, read by gs_read_stats (synchronises the stream). */
 typedef struct gs_stats {
     int64_t num_keys;                  /* K of the last gs_bin_sort                           */
-    int64_t fwd_pairs;                 /* (pixel, list entry) pairs evaluated by the forward  */
-    int64_t bwd_pairs;                 /* (pixel, list entry) pairs walked by the backward    */
+    int64_t fwd_pairs;                 /* (pixel, list entry) pairs evaluated by the forward
+                                          launches since the last gs_bin_sort                 */
+    int64_t bwd_pairs;                 /* (pixel, list entry) pairs walked by the backward
+                                          launches since the last gs_bin_sort                 */
     int64_t num_visible;               /* slots the last gs_project took: its visible pairs and
                                           the candidates its pre-test kept but its decision
                                           chain culled (also beyond visible_capacity: the

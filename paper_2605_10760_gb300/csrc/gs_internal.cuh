@@ -37,8 +37,9 @@ struct DevStatus {
     int32_t where;                // stage tag of that error
     unsigned long long required_keys;
     unsigned long long num_keys;  // K written by the scan
-    // each compositing kernel's pair counter and work-queue counter sit in one 16-byte block,
-    // cleared together by one memset before the launch
+    // the compositing kernels' work-queue counters return to zero at the end of every launch (the
+    // CTA drawing a launch's last claim resets it); their pair counts are cleared by each binning
+    // and count the (pixel, entry) pairs of the launches since
     unsigned long long fwd_pairs;
     uint32_t fwd_items, fwd_pad;
     unsigned long long bwd_pairs;

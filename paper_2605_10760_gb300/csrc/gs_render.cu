@@ -142,13 +142,19 @@ __device__ __forceinline__ void claim_offsets(const DevStatus *st, uint32_t *cof
     }
 }
 
-// Next work item of a persistent compositing CTA (thread 0), -1 when all are taken.  Class lists
-// inconsistent with G (only after an earlier binning failure) record a device fault; the claim then
-// falls back to the counter's own value.
-__device__ __forceinline__ long long claim_item(DevStatus *st, unsigned int *ctr, const uint32_t *coff,
+// Next work item of a persistent compositing CTA (thread 0), -1 when all are taken.  Every CTA
+// makes exactly one claim past the last item; the CTA that draws the last of those (every other
+// claim of the launch is made by then) returns the counter to zero for the next launch.  Class
+// lists inconsistent with G (only after an earlier binning failure) record a device fault; the
+// claim then falls back to the counter's own value.
+__device__ __forceinline__ long long claim_item(DevStatus *st, uint32_t *ctr, const uint32_t *coff,
                                                 const uint32_t *clist, long long G) {
     const long long c = (long long)atomicAdd(ctr, 1u);
-    if (c >= min((long long)coff[kClaimClasses], G)) return -1;
+    const long long total = min((long long)coff[kClaimClasses], G);
+    if (c >= total) {
+        if (c == total + (long long)gridDim.x - 1) *ctr = 0u;
+        return -1;
+    }
     int k = 0;   // the largest k with coff[k] <= c (coff[0] = 0)
 #pragma unroll
     for (int step = kClaimClasses / 2; step > 0; step >>= 1)
@@ -160,6 +166,20 @@ __device__ __forceinline__ long long claim_item(DevStatus *st, unsigned int *ctr
         return c;
     }
     return (long long)g;
+}
+
+// A CTA leaving early (after a failed wait, an error already recorded) claims until it draws a
+// value past the items, skipping the items it draws, so that every CTA still makes exactly one
+// claim past them and the launch's last claim returns the counter to zero.
+__device__ __forceinline__ void claim_exit(uint32_t *ctr, const uint32_t *coff, long long G) {
+    if (threadIdx.x == 0) {
+        const long long total = min((long long)coff[kClaimClasses], G);
+        long long c;
+        do {
+            c = (long long)atomicAdd(ctr, 1u);
+        } while (c < total);
+        if (c == total + (long long)gridDim.x - 1) *ctr = 0u;
+    }
 }
 
 // Shared memory of one render CTA: two batches of records (double buffer filled by TMA), the
@@ -252,6 +272,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
             if (__syncthreads_or(!ok)) {
                 const bool pending[2] = {buf == 0 || bi + 1 < nb, buf == 1 || bi + 1 < nb};
                 drain_after_timeout<NB>(sm, parity, pending, a.st);
+                claim_exit(&a.st->fwd_items, sm.coff, a.G);
                 return;
             }
             parity[buf] ^= 1u;
@@ -314,6 +335,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_fwd(FwdArgs a) {
                     if (__syncthreads_or(!ok2)) {
                         const bool pending[2] = {buf == 1, buf == 0};
                         drain_after_timeout<NB>(sm, parity, pending, a.st);
+                        claim_exit(&a.st->fwd_items, sm.coff, a.G);
                         return;
                     }
                     parity[buf ^ 1] ^= 1u;
@@ -504,6 +526,7 @@ __global__ void __launch_bounds__(TW *TH / kPPT) k_render_bwd(BwdArgs a) {
             if (__syncthreads_or(!ok)) {
                 const bool pending[2] = {buf == 0 || bi + 1 < nb, buf == 1 || bi + 1 < nb};
                 drain_after_timeout<NB>(sm, parity, pending, a.st);
+                claim_exit(&a.st->bwd_items, sm.coff, a.G);
                 return;
             }
             parity[buf] ^= 1u;
@@ -614,7 +637,6 @@ template <int TW, int TH, int NB>
 static int fwd_t(const FwdArgs &a, cudaStream_t s) {
     constexpr int NT = TW * TH / kPPT;
     static int grid = persistent_grid(k_render_fwd<TW, TH, NB>, NT);
-    if (cudaMemsetAsync(&a.st->fwd_pairs, 0, 16, s) != cudaSuccess) return GS_ERR_CUDA;   // pairs + items
     if (a.rgb_t && cudaMemsetAsync(a.loss, 0, sizeof(double), s) != cudaSuccess) return GS_ERR_CUDA;
     const long long g = std::min<long long>(grid, std::max<long long>(1, a.G));
     k_render_fwd<TW, TH, NB><<<(unsigned)g, NT, 0, s>>>(a);
@@ -626,7 +648,6 @@ template <int TW, int TH, int NB>
 static int bwd_t(const BwdArgs &a, cudaStream_t s) {
     constexpr int NT = TW * TH / kPPT;
     static int grid = persistent_grid(k_render_bwd<TW, TH, NB>, NT);
-    if (cudaMemsetAsync(&a.st->bwd_pairs, 0, 16, s) != cudaSuccess) return GS_ERR_CUDA;   // pairs + items
     const long long g = std::min<long long>(grid, std::max<long long>(1, a.G));
     k_render_bwd<TW, TH, NB><<<(unsigned)g, NT, 0, s>>>(a);
     count_launches(1);

@@ -576,6 +576,10 @@ __global__ void __launch_bounds__(kRangesThreads) k_ranges(const uint64_t *keys,
                                                            long long P, uint32_t *ranges, unsigned long long *tword,
                                                            uint32_t *clist) {
     const unsigned long long K = min(st->num_keys, (unsigned long long)cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // the compositing launches on this binning count anew
+        st->fwd_pairs = 0ull;
+        st->bwd_pairs = 0ull;
+    }
     if (K == 0) {   // every tile empty: all in the last claim class, in tile order
         for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x)
             clist[(size_t)(kClaimClasses - 1) * G + g] = (uint32_t)g;
@@ -786,6 +790,10 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(BinArgs a) {
     uint64_t *kout = a.keys[a.passes & 1];
     uint32_t *vout = a.vals[a.passes & 1];
     const unsigned long long *words = reinterpret_cast<const unsigned long long *>(a.keys[0]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // the compositing launches on this binning count anew
+        a.st->fwd_pairs = 0ull;
+        a.st->bwd_pairs = 0ull;
+    }
     for (;;) {
         long long g = 0;
         if (lane == 0) g = (long long)atomicAdd(&a.st->ctr[kCtrTileSort], 1u);
