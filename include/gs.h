@@ -201,7 +201,9 @@ void gs_default_params(gs_params *out);
 int gs_workspace_size(const gs_problem *pb, size_t *bytes);
 
 /* Writes the per-view tables into the workspace and clears its status block.  Call once after
- * allocating the workspace and again whenever view_gauss_begin / view_gauss_count change. */
+ * allocating the workspace and again whenever view_gauss_begin / view_gauss_count change.  The
+ * work counters in the status block return to zero at the end of every launch that uses them, so
+ * calls need no clearing in between; one workspace serves one stream of calls at a time. */
 int gs_workspace_init(const gs_problem *pb, void *ws, void *stream);
 
 /* Fills *out with device pointers into the workspace (host only). */

@@ -361,9 +361,9 @@ int gs_project(const gs_problem *pb, const gs_gaussians *g, void *ws, void *stre
                         (cudaStream_t)stream) != cudaSuccess)
         return GS_ERR_CUDA;
     DevStatus *st = ws_ptr<DevStatus>(ws, L.o_status);
-    if (cudaMemsetAsync(&st->num_visible, 0, sizeof(st->num_visible), (cudaStream_t)stream) != cudaSuccess)
-        return GS_ERR_CUDA;
-    if (L.P == 0) return GS_OK;
+    if (L.P == 0)   // no projection launch: no slots taken
+        return cudaMemsetAsync(&st->num_visible, 0, sizeof(st->num_visible), (cudaStream_t)stream) == cudaSuccess
+                   ? GS_OK : GS_ERR_CUDA;
     ProjArgs a;
     a.views = ws_ptr<ViewEntry>(ws, L.o_views);
     a.cams = pb->cameras;

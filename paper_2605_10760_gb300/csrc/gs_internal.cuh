@@ -48,7 +48,10 @@ struct DevStatus {
     uint32_t claim_cnt[32];       // items in each claim class (cleared with ctr by gs_bin_sort)
     int32_t guard_bad;            // gs_check_guards: index of the first changed guard block
     int32_t guard_pad;
-    unsigned long long num_visible;   // visible pairs of the last projection (slot counter)
+    unsigned long long num_visible;   // slots the last projection took (its visible pairs and holes)
+    // the projection's slot counter: blocks that have reserved << 40 | slots reserved; the block
+    // arriving last publishes num_visible and returns it to zero
+    unsigned long long slot_ctr;
 };
 
 struct ViewEntry {                // per-view table in the workspace (32 bytes)

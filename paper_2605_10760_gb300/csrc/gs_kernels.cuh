@@ -18,7 +18,7 @@ struct ProjArgs {
     uint32_t *tile_cnt;         // [G] key count per global tile (tile-bucket binning), else null
     int Txi, Ty_i;
     long long P;                // (view, Gaussian) pairs: the length of touched and slot
-    DevStatus *st;              // errors; num_visible is the slot counter (slots taken by candidates)
+    DevStatus *st;              // errors; slot_ctr hands out the slots, num_visible their count
     uint32_t *slot;             // [P] slot of each visible pair in proj (kNoSlot when culled)
     long long vcap;             // slots in proj
     uint16_t *slane;            // [vcap] the chunk position of each slot's pair, | kSlotHole when the

@@ -48,7 +48,7 @@ __device__ __forceinline__ bool may_be_visible(const float *R, const float *t, f
 // single-view problem is resident at once.  Phase 1: each thread pre-tests kProjPre pairs
 // (may_be_visible); the candidates are compacted in pair order and take consecutive slots, reserved
 // by one atomic per block on the slot counter, issued before the decision chain so that the
-// chain's arithmetic hides its latency.  Phase 2: the candidates run the decision chain
+// chain's arithmetic hides its latency (the last block to reserve returns the counter to zero).  Phase 2: the candidates run the decision chain
 // kProjThreads at a time; a visible one writes its record into its slot, an invisible one leaves
 // its slot a hole.  The block records its first slot and candidate count (blk) and, per slot, the
 // pair's position in the chunk, flagged kSlotHole for a hole (slane).  Slots beyond the capacity
@@ -113,9 +113,18 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
         for (int w = 0; w < kProjThreads / 32; ++w) ncand += s_wcnt[k][w];
     }
     __syncthreads();   // s_cl complete
-    // the candidates' slots: one atomic, whose result is needed only after the first round's chain
+    // the candidates' slots: one atomic, whose result is needed only after the first round's chain.
+    // Every block takes part (also with no candidate) and counts itself in the high bits; the block
+    // arriving last publishes the slot total and returns the counter to zero for the next launch
     unsigned long long base_reg = 0ull;
-    if (threadIdx.x == 0 && ncand > 0) base_reg = atomicAdd(&a.st->num_visible, (unsigned long long)ncand);
+    if (threadIdx.x == 0) {
+        const unsigned long long old = atomicAdd(&a.st->slot_ctr, (1ull << 40) + (unsigned long long)ncand);
+        base_reg = old & ((1ull << 40) - 1ull);
+        if ((old >> 40) == (unsigned long long)gridDim.x * gridDim.y - 1ull) {
+            a.st->num_visible = base_reg + ncand;
+            a.st->slot_ctr = 0ull;
+        }
+    }
     // phase 2: candidates r kProjThreads + thread through the decision chain
     const int rounds = (int)((ncand + kProjThreads - 1) / kProjThreads);
     for (int r = 0; r < rounds; ++r) {

@@ -167,13 +167,24 @@ __device__ __forceinline__ void scan_store(const BinArgs &a, long long base, con
     }
 }
 
+// Next partition of a scan or onesweep CTA (thread 0), in claim order.  A CTA whose grid covers
+// every partition claims once; otherwise every CTA ends with one claim past the partitions.  The
+// launch's last claim returns the counter to zero for the next launch, so the counters need no
+// clearing between launches (gs_workspace_init leaves them zero).
+__device__ __forceinline__ uint32_t claim_part(uint32_t *ctr, long long nparts) {
+    const uint32_t c = atomicAdd(ctr, 1u);
+    const long long last = nparts <= (long long)gridDim.x ? (long long)gridDim.x - 1 : nparts + gridDim.x - 1;
+    if ((long long)c == last) *ctr = 0u;
+    return c;
+}
+
 // Scan alone: counts -> inclusive sums in place (tile-bucket binning and the bounded-wait test).
 __global__ void __launch_bounds__(kScanThreads) k_scan(BinArgs a) {
     __shared__ uint32_t s_part;
     __shared__ ScanShared<kScanThreads> sh;
     const long long nparts = (a.P + kScanTile - 1) / kScanTile;
     for (;;) {
-        if (threadIdx.x == 0) s_part = atomicAdd(&a.st->ctr[kCtrScan], 1u);
+        if (threadIdx.x == 0) s_part = claim_part(&a.st->ctr[kCtrScan], nparts);
         __syncthreads();
         const long long part = s_part;
         if (part >= nparts) break;
@@ -238,8 +249,11 @@ __global__ void __launch_bounds__(kEmitThreads) k_scan_emit(BinArgs a) {
     const long long nparts = (a.P + kScanTile - 1) / kScanTile;
     const unsigned long long cap = (unsigned long long)a.cap;
     const int lane = threadIdx.x & 31;
+    // the claim classes of this binning start empty (k_ranges fills them; the compositing launches
+    // of the previous binning, which read them, are complete)
+    if (blockIdx.x == 0 && threadIdx.x < kClaimClasses) a.st->claim_cnt[threadIdx.x] = 0u;
     for (;;) {
-        if (threadIdx.x == 0) s_part = atomicAdd(&a.st->ctr[kCtrScan], 1u);
+        if (threadIdx.x == 0) s_part = claim_part(&a.st->ctr[kCtrScan], nparts);
         __syncthreads();
         const long long part = s_part;
         if (part >= nparts) break;
@@ -404,6 +418,11 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
     const uint32_t K = (uint32_t)Kll;
     const uint32_t nparts = (K + kSortTile - 1) / kSortTile;
     const unsigned lt_mask = lanemask_lt();
+    {   // the first claim, made before nparts was known, may be the launch's last one (claim_part)
+        const long long last =
+            (long long)nparts <= (long long)gridDim.x ? (long long)gridDim.x - 1 : (long long)nparts + gridDim.x - 1;
+        if (threadIdx.x == 0 && (long long)s_part == last) *a.ctr = 0u;
+    }
     for (;;) {
         const uint32_t part = s_part;
         if (part >= nparts) break;
@@ -529,7 +548,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SweepArgs a) {
         __syncthreads();
         // next partition; the per-warp digit counters start from zero again
         if (threadIdx.x == 0) {
-            s_part = atomicAdd(a.ctr, 1u);
+            s_part = claim_part(a.ctr, (long long)nparts);
             s_bad = 0;
         }
 #pragma unroll
@@ -889,6 +908,11 @@ static int occupancy(const void *fn, int threads, size_t dyn);
 static int run_scan(const BinArgs &a, cudaStream_t s, bool counter_cleared);
 
 static int run_bucket(const BinArgs &a, cudaStream_t s) {
+    // counters of the scan and of the per-tile sort, and the claim-class counts
+    static_assert(offsetof(DevStatus, claim_cnt) == offsetof(DevStatus, ctr) + sizeof(uint32_t) * kNumCounters,
+                  "the claim-class counts follow the counters");
+    if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t) * (kNumCounters + kClaimClasses), s) != cudaSuccess)
+        return GS_ERR_CUDA;
     // inclusive scan of the G tile counts (K and the capacity check come with it)
     BinArgs sa = a;
     sa.touched = a.tile_cnt;
@@ -969,11 +993,8 @@ static int sweep_passes(const BinArgs &a, cudaStream_t s) {
 }
 
 int run_bin_sort(const BinArgs &a, cudaStream_t s) {
-    // counters of the scan, of every sort pass and of the per-tile sort, and the claim-class counts
-    static_assert(offsetof(DevStatus, claim_cnt) == offsetof(DevStatus, ctr) + sizeof(uint32_t) * kNumCounters,
-                  "the claim-class counts follow the counters");
-    if (cudaMemsetAsync(&a.st->ctr[kCtrScan], 0, sizeof(uint32_t) * (kNumCounters + kClaimClasses), s) != cudaSuccess)
-        return GS_ERR_CUDA;
+    // (the onesweep path's claim counters return to zero at the end of every launch and k_scan_emit
+    // clears the claim-class counts: no memset for them)
     if (a.sort_mode == GS_SORT_TILE_BUCKET) return run_bucket(a, s);
     // look-back words of the scan and of every pass, digit histograms and tile ranges
     if (cudaMemsetAsync(a.clear_begin, 0, a.clear_bytes, s) != cudaSuccess) return GS_ERR_CUDA;
