@@ -1008,8 +1008,10 @@ int run_bin_sort(const BinArgs &a, cudaStream_t s) {
         const long long grid = std::min<long long>(parts, (long long)sms * occ);
         k_scan_emit<<<(unsigned)grid, kEmitThreads, kEmitDynSmem, s>>>(a);
         count_launches(1);
-    } else if (cudaMemsetAsync(&a.st->num_keys, 0, sizeof(unsigned long long), s) != cudaSuccess) {
-        return GS_ERR_CUDA;   // no pairs: K = 0
+    } else {   // no pairs: K = 0, and the claim classes start empty (k_scan_emit clears them otherwise)
+        if (cudaMemsetAsync(&a.st->num_keys, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+            cudaMemsetAsync(a.st->claim_cnt, 0, sizeof(uint32_t) * kClaimClasses, s) != cudaSuccess)
+            return GS_ERR_CUDA;
     }
     const int rc2 = sweep_passes<kSortIPT>(a, s);
     if (rc2) return rc2;

@@ -368,3 +368,18 @@ def test_repeated_launches_need_no_clearing(R):
     np.testing.assert_allclose(g2d[1], 2.0 * g2d[0], rtol=1e-5, atol=1e-9)
     rc, _ = pb.check_status()
     assert rc == 0
+
+
+def test_views_without_gaussians(R):
+    """A problem with no (view, Gaussian) pair at all: no projection or scan launch, an empty
+    binning, the background everywhere, zero pose gradient, and the same again on a second call."""
+    sc = S.random_cloud(0, seed=5)
+    wl = S.Workload("empty", sc, np.array([0, 0], np.int64), [S.identity_camera(40, 30, 30, 30)],
+                    np.zeros(1, np.int32), 40, 30)
+    for _ in range(2):
+        gpu = run_gpu(R, wl, params=R.default_params(bg=(0.25, 0.5, 0.75)))
+        assert gpu["rc"] == 0 and gpu["rc_end"] == 0 and gpu["K"] == 0
+        assert gpu["stats"]["num_visible"] == 0 and gpu["stats"]["fwd_pairs"] == 0
+        assert np.all(gpu["img"]["final_T"] == 1.0) and np.all(gpu["img"]["last_idx"] == 0)
+        np.testing.assert_array_equal(gpu["img"]["rgb"][0, 2], np.full((30, 40), 0.75, np.float32))
+        assert np.all(gpu["pose"] == 0)
